@@ -1,0 +1,408 @@
+/*
+ * tgp_oracle.c -- plain, slow CPU oracle for GP population evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA path and includes nothing from it.
+ *
+ * What it computes (the plain definition the method must reach):
+ *   for every tree t and every grid point (row, col), evaluate the expression
+ *   tree recursively, then reduce each tree to its root-mean-squared error
+ *   against the target:  RMSE_t = sqrt( (1/N) * sum_p (f_t(p) - P(p))^2 ).
+ *
+ * Passages followed (TensorGP, arXiv 2103.07512):
+ *   - tensor phenotype over a fixed rank-2 grid of fitness cases: Sec. 3.1;
+ *   - operator semantics and protections: Table 1 (add, sub, mult, div with
+ *     0 on a zero denominator, sin, cos, neg, abs, min, max);
+ *   - trigonometric operators take the argument multiplied by pi: Sec. 3.2;
+ *   - Pagie polynomial target: Eq. 1;
+ *   - RMSE fitness against the target: Sec. 4.1 and Table 2.
+ *
+ * Readings where the paper is silent or garbled (each listed in the design doc):
+ *   - Table 1 prints sin and cos swapped; the prose of Sec. 3.2 is followed:
+ *     sin(a) := sin(pi*a), cos(a) := cos(pi*a).
+ *   - The grid placement is not printed: inclusive linspace, x along columns,
+ *     y along rows, flat index p = row*W + col, coordinates formed in IEEE
+ *     binary32 as xlo + (float)col * ((xhi - xlo) / (float)(W - 1)) with no
+ *     fused multiply-add; W == 1 gives x = xlo.  The oracle evaluates on these
+ *     same float values widened to double.
+ *   - Eq. 1 is undefined at 0 (x^-4); it is evaluated as x^4 / (1 + x^4), the
+ *     continuous extension, which is 0 at x = 0.
+ *   - RMSE divides by N.  A non-finite squared-error sum gives +inf.
+ *   - Protected division returns 0 when the denominator equals 0 (either
+ *     sign), otherwise the IEEE quotient.
+ *   - min / max follow C fmin / fmax (a NaN operand yields the other one).
+ *
+ * Two evaluation modes run side by side on every node:
+ *   - FP64: every node in binary64;
+ *   - FP32-faithful: every node computed in binary64 from binary32 operands and
+ *     rounded to binary32 before its parent uses it.  For + - * / this is the
+ *     correctly rounded binary32 result; for sin/cos it is the (almost always)
+ *     correctly rounded value of sin(pi*a).
+ * Per element the oracle flags near-singular division: some div node of the
+ * tree saw a denominator with |b| < 1e-6 in either mode.
+ *
+ * Build: gcc -O2 -fPIC -shared -ffp-contract=off -o liboracle.so tgp_oracle.c -lm
+ * (-ffp-contract=off keeps a*b+c from being fused, which some targets do by
+ * default and which would change the binary32 grid coordinates.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* pi to binary64 precision */
+#define ORACLE_PI 3.14159265358979323846
+
+/* Opcodes of the token stream (the 10 functions of the configured set plus
+ * the three terminals x, y and an ephemeral constant). */
+enum {
+    O_X = 0, O_Y = 1, O_CONST = 2,
+    O_ADD = 3, O_SUB = 4, O_MUL = 5, O_DIV = 6,
+    O_SIN = 7, O_COS = 8, O_NEG = 9, O_ABS = 10, O_MIN = 11, O_MAX = 12,
+    O_COUNT = 13
+};
+
+enum { ORD_PREFIX = 0, ORD_POSTFIX = 1 };
+
+/* error codes returned by the oracle */
+enum { OR_OK = 0, OR_BAD_OPCODE = -1, OR_MALFORMED = -2, OR_IMM = -3, OR_ARG = -4, OR_NOMEM = -5 };
+
+static int arity_of(int op)
+{
+    switch (op) {
+    case O_X: case O_Y: case O_CONST: return 0;
+    case O_SIN: case O_COS: case O_NEG: case O_ABS: return 1;
+    case O_ADD: case O_SUB: case O_MUL: case O_DIV: case O_MIN: case O_MAX: return 2;
+    default: return -1;
+    }
+}
+
+/* one parsed tree node */
+typedef struct {
+    int op;
+    int kid[2];     /* indices into the same node array, -1 if absent */
+    double imm;     /* the constant, as the binary32 value widened */
+} onode;
+
+/* ---------------------------------------------------------------- parsing */
+
+/* Prefix: the operator precedes its operands (recursive descent). */
+static int parse_prefix(const int32_t* ops, int64_t n_tok, const float* imm, int64_t n_imm,
+                        int64_t* tok_pos, int64_t* imm_pos, onode* nodes, int* n_nodes, int* out)
+{
+    if (*tok_pos >= n_tok) return OR_MALFORMED;
+    int op = ops[(*tok_pos)++];
+    int ar = arity_of(op);
+    if (ar < 0) return OR_BAD_OPCODE;
+    int me = (*n_nodes)++;
+    nodes[me].op = op;
+    nodes[me].kid[0] = nodes[me].kid[1] = -1;
+    nodes[me].imm = 0.0;
+    if (op == O_CONST) {
+        if (*imm_pos >= n_imm) return OR_IMM;
+        nodes[me].imm = (double)imm[(*imm_pos)++];
+    }
+    for (int c = 0; c < ar; c++) {
+        int k;
+        int rc = parse_prefix(ops, n_tok, imm, n_imm, tok_pos, imm_pos, nodes, n_nodes, &k);
+        if (rc) return rc;
+        nodes[me].kid[c] = k;
+    }
+    *out = me;
+    return OR_OK;
+}
+
+/* Postfix: operands precede their operator (explicit stack). */
+static int parse_postfix(const int32_t* ops, int64_t n_tok, const float* imm, int64_t n_imm,
+                         int64_t* imm_pos, onode* nodes, int* out)
+{
+    int* stack = (int*)malloc(sizeof(int) * (size_t)(n_tok + 1));
+    if (!stack) return OR_NOMEM;
+    int sp = 0, n = 0, rc = OR_OK;
+    for (int64_t i = 0; i < n_tok; i++) {
+        int op = ops[i];
+        int ar = arity_of(op);
+        if (ar < 0) { rc = OR_BAD_OPCODE; break; }
+        if (sp < ar) { rc = OR_MALFORMED; break; }
+        int me = n++;
+        nodes[me].op = op;
+        nodes[me].kid[0] = nodes[me].kid[1] = -1;
+        nodes[me].imm = 0.0;
+        if (op == O_CONST) {
+            if (*imm_pos >= n_imm) { rc = OR_IMM; break; }
+            nodes[me].imm = (double)imm[(*imm_pos)++];
+        }
+        for (int c = ar - 1; c >= 0; c--) nodes[me].kid[c] = stack[--sp];
+        stack[sp++] = me;
+    }
+    if (rc == OR_OK && sp != 1) rc = OR_MALFORMED;
+    if (rc == OR_OK) *out = stack[0];
+    free(stack);
+    return rc;
+}
+
+typedef struct {
+    onode* nodes;
+    int root;
+} otree;
+
+/* Parses every tree of a population.  imm is consumed in stream order across
+ * all trees.  On success trees[t] holds malloc'ed node arrays. */
+static int parse_population(const int32_t* ops, const float* imm, int64_t n_imm,
+                            const int64_t* tree_off, int32_t n_trees, int32_t order, otree* trees)
+{
+    int64_t imm_pos = 0;
+    for (int32_t t = 0; t < n_trees; t++) trees[t].nodes = NULL;
+    for (int32_t t = 0; t < n_trees; t++) {
+        int64_t n_tok = tree_off[t + 1] - tree_off[t];
+        if (n_tok <= 0) return OR_MALFORMED;
+        trees[t].nodes = (onode*)malloc(sizeof(onode) * (size_t)n_tok);
+        if (!trees[t].nodes) return OR_NOMEM;
+        const int32_t* tk = ops + tree_off[t];
+        int rc;
+        if (order == ORD_PREFIX) {
+            int64_t pos = 0;
+            int n = 0;
+            rc = parse_prefix(tk, n_tok, imm, n_imm, &pos, &imm_pos, trees[t].nodes, &n, &trees[t].root);
+            if (rc == OR_OK && pos != n_tok) rc = OR_MALFORMED;
+        } else if (order == ORD_POSTFIX) {
+            rc = parse_postfix(tk, n_tok, imm, n_imm, &imm_pos, trees[t].nodes, &trees[t].root);
+        } else {
+            rc = OR_ARG;
+        }
+        if (rc) return rc;
+    }
+    if (imm_pos != n_imm) return OR_IMM;
+    return OR_OK;
+}
+
+static void free_population(otree* trees, int32_t n_trees)
+{
+    for (int32_t t = 0; t < n_trees; t++) free(trees[t].nodes);
+}
+
+/* ------------------------------------------------------------ arithmetic */
+
+/* sin(pi*a) for a binary64 a.  The argument is reduced exactly: r = a mod 2,
+ * n = nearest integer to 2r, f = r - n/2 in [-1/4, 1/4] (both steps are exact
+ * in binary64), then the quadrant identity picks sin or cos of pi*f.  This
+ * gives exact zeros at integers and exact +-1 at half-integers. */
+double oracle_sinpi(double a)
+{
+    if (!isfinite(a)) return NAN;
+    double r = fmod(a, 2.0);
+    double n = nearbyint(2.0 * r);
+    double f = r - 0.5 * n;
+    int q = (int)fmod(n, 4.0);
+    if (q < 0) q += 4;
+    double pf = ORACLE_PI * f, v;
+    switch (q) {
+    case 0: v = sin(pf); break;
+    case 1: v = cos(pf); break;
+    case 2: v = -sin(pf); break;
+    default: v = -cos(pf); break;
+    }
+    return v == 0.0 ? 0.0 : v;   /* zeros are returned as +0 */
+}
+
+/* cos(pi*a), same reduction. */
+double oracle_cospi(double a)
+{
+    if (!isfinite(a)) return NAN;
+    double r = fmod(a, 2.0);
+    double n = nearbyint(2.0 * r);
+    double f = r - 0.5 * n;
+    int q = (int)fmod(n, 4.0);
+    if (q < 0) q += 4;
+    double pf = ORACLE_PI * f, v;
+    switch (q) {
+    case 0: v = cos(pf); break;
+    case 1: v = -sin(pf); break;
+    case 2: v = -cos(pf); break;
+    default: v = sin(pf); break;
+    }
+    return v == 0.0 ? 0.0 : v;   /* zeros are returned as +0 */
+}
+
+/* Table 1, div: x/y, and 0 when the denominator is 0. */
+static double pdiv(double a, double b)
+{
+    if (b == 0.0) return 0.0;
+    return a / b;
+}
+
+/* One operator of Table 1 applied in binary64. */
+static double apply64(int op, double a, double b)
+{
+    switch (op) {
+    case O_ADD: return a + b;
+    case O_SUB: return a - b;
+    case O_MUL: return a * b;
+    case O_DIV: return pdiv(a, b);
+    case O_SIN: return oracle_sinpi(a);
+    case O_COS: return oracle_cospi(a);
+    case O_NEG: return -a;
+    case O_ABS: return fabs(a);
+    case O_MIN: return fmin(a, b);
+    case O_MAX: return fmax(a, b);
+    default: return NAN;
+    }
+}
+
+#define NEAR_SINGULAR 1e-6
+
+typedef struct {
+    double x64, y64;   /* coordinates (binary32 values widened) */
+    int flag;          /* near-singular division seen */
+} opoint;
+
+/* Recursive tree walk in both modes at once. */
+static void eval_node(const onode* nodes, int i, opoint* pt, double* v64, float* v32)
+{
+    const onode* n = &nodes[i];
+    switch (n->op) {
+    case O_X: *v64 = pt->x64; *v32 = (float)pt->x64; return;
+    case O_Y: *v64 = pt->y64; *v32 = (float)pt->y64; return;
+    case O_CONST: *v64 = n->imm; *v32 = (float)n->imm; return;
+    default: break;
+    }
+    double a64 = 0.0, b64 = 0.0;
+    float a32 = 0.0f, b32 = 0.0f;
+    eval_node(nodes, n->kid[0], pt, &a64, &a32);
+    if (n->kid[1] >= 0) eval_node(nodes, n->kid[1], pt, &b64, &b32);
+    if (n->op == O_DIV) {
+        if (fabs(b64) < NEAR_SINGULAR || fabs((double)b32) < NEAR_SINGULAR) pt->flag = 1;
+    }
+    *v64 = apply64(n->op, a64, b64);
+    *v32 = (float)apply64(n->op, (double)a32, (double)b32);
+}
+
+/* ------------------------------------------------------------------ grid */
+
+/* Coordinate of column col (or row) on an inclusive linspace of n points,
+ * formed in binary32 exactly as the grid reading states. */
+static float grid_coord(float lo, float hi, int32_t n, int64_t i)
+{
+    if (n <= 1) return lo;
+    float step = (hi - lo) / (float)(n - 1);
+    float prod = (float)i * step;
+    return lo + prod;
+}
+
+void oracle_grid_point(int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                       int64_t p, float* x, float* y)
+{
+    int64_t row = p / W, col = p % W;
+    *x = grid_coord(xlo, xhi, W, col);
+    *y = grid_coord(ylo, yhi, H, row);
+}
+
+/* Eq. 1, Pagie polynomial, written as x^4/(1+x^4) + y^4/(1+y^4) (continuous
+ * extension at 0). */
+double oracle_pagie(double x, double y)
+{
+    double x4 = x * x * x * x;
+    double y4 = y * y * y * y;
+    return x4 / (1.0 + x4) + y4 / (1.0 + y4);
+}
+
+/* ------------------------------------------------------------ public API */
+
+/*
+ * Evaluates every tree of a population at n_pts grid points (flat indices in
+ * pts, or all H*W points in order when pts == NULL).
+ *   out64 [n_trees][n_pts]  binary64 values (required)
+ *   out32 [n_trees][n_pts]  FP32-faithful values (may be NULL)
+ *   flags [n_trees][n_pts]  1 where a division saw |denominator| < 1e-6 (may be NULL)
+ * Returns 0 or a negative error code (malformed tokens, bad opcode, imm count).
+ */
+int oracle_eval(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                int32_t n_trees, int32_t order,
+                int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                int64_t n_pts, const int64_t* pts,
+                double* out64, float* out32, uint8_t* flags)
+{
+    if (n_trees < 0 || W <= 0 || H <= 0 || n_pts < 0) return OR_ARG;
+    otree* trees = (otree*)calloc((size_t)(n_trees > 0 ? n_trees : 1), sizeof(otree));
+    if (!trees) return OR_NOMEM;
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, trees);
+    if (rc) { free_population(trees, n_trees); free(trees); return rc; }
+    for (int32_t t = 0; t < n_trees; t++) {
+        for (int64_t i = 0; i < n_pts; i++) {
+            int64_t p = pts ? pts[i] : i;
+            float xf, yf;
+            oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
+            opoint pt = { (double)xf, (double)yf, 0 };
+            double v64;
+            float v32;
+            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32);
+            out64[(size_t)t * n_pts + i] = v64;
+            if (out32) out32[(size_t)t * n_pts + i] = v32;
+            if (flags) flags[(size_t)t * n_pts + i] = (uint8_t)pt.flag;
+        }
+    }
+    free_population(trees, n_trees);
+    free(trees);
+    return OR_OK;
+}
+
+/* target kinds */
+enum { TG_PAGIE = 0, TG_VALUES = 1 };
+
+/*
+ * RMSE of every tree against the target over all H*W points (or over the
+ * n_pts points listed in pts, dividing by n_pts).
+ *   target_kind 0: Pagie polynomial (Eq. 1) at the grid's coordinates;
+ *   target_kind 1: target_vals[p] (binary64, indexed by flat point index).
+ *   rmse64 [n_trees]: RMSE of the binary64 phenotype;
+ *   rmse32 [n_trees]: RMSE of the FP32-faithful phenotype (may be NULL);
+ *   n_flagged [n_trees]: points with a near-singular division (may be NULL).
+ * A non-finite sum gives +inf.
+ */
+int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                   int32_t n_trees, int32_t order,
+                   int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                   int32_t target_kind, const double* target_vals,
+                   int64_t n_pts, const int64_t* pts,
+                   double* rmse64, double* rmse32, int64_t* n_flagged)
+{
+    if (n_trees < 0 || W <= 0 || H <= 0) return OR_ARG;
+    if (target_kind == TG_VALUES && !target_vals) return OR_ARG;
+    if (target_kind != TG_PAGIE && target_kind != TG_VALUES) return OR_ARG;
+    int64_t N = pts ? n_pts : (int64_t)W * (int64_t)H;
+    otree* trees = (otree*)calloc((size_t)(n_trees > 0 ? n_trees : 1), sizeof(otree));
+    if (!trees) return OR_NOMEM;
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, trees);
+    if (rc) { free_population(trees, n_trees); free(trees); return rc; }
+    for (int32_t t = 0; t < n_trees; t++) {
+        double s64 = 0.0, s32 = 0.0;
+        int64_t nf = 0;
+        for (int64_t i = 0; i < N; i++) {
+            int64_t p = pts ? pts[i] : i;
+            float xf, yf;
+            oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
+            double tv = target_kind == TG_PAGIE ? oracle_pagie((double)xf, (double)yf) : target_vals[p];
+            opoint pt = { (double)xf, (double)yf, 0 };
+            double v64;
+            float v32;
+            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32);
+            double d64 = v64 - tv;
+            double d32 = (double)v32 - tv;
+            s64 += d64 * d64;
+            s32 += d32 * d32;
+            nf += pt.flag;
+        }
+        double r64 = sqrt(s64 / (double)N);
+        double r32 = sqrt(s32 / (double)N);
+        rmse64[t] = isfinite(r64) ? r64 : INFINITY;
+        if (rmse32) rmse32[t] = isfinite(r32) ? r32 : INFINITY;
+        if (n_flagged) n_flagged[t] = nf;
+    }
+    free_population(trees, n_trees);
+    free(trees);
+    return OR_OK;
+}
+
+/* Arity of an opcode (-1 if unknown); exported for the tests' brute force. */
+int oracle_arity(int32_t op) { return arity_of(op); }

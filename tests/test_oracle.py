@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value is a closed
+form, an exact rational derived from Eq. 1, an independent numpy restatement of
+a single operator, or brute force written separately in this file.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07512_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def toks(*exprs, order=I.PREFIX):
+    return I.to_tokens([I.parse_string(e) for e in exprs], order)
+
+
+def ev(exprs, W, H, lo=-5.0, hi=5.0, order=I.PREFIX):
+    t = toks(*exprs, order=order)
+    return oracle.evaluate(t.ops, t.imm, t.tree_off, order, W, H, lo, hi, lo, hi)
+
+
+def np_grid(W, H, lo=-5.0, hi=5.0):
+    """Independent restatement of the binary32 grid reading: inclusive
+    linspace, x along columns, y along rows, flat index row*W + col."""
+    f = np.float32
+    sx = (f(hi) - f(lo)) / f(W - 1) if W > 1 else f(0)
+    sy = (f(hi) - f(lo)) / f(H - 1) if H > 1 else f(0)
+    cols = np.arange(W, dtype=np.float32)
+    rows = np.arange(H, dtype=np.float32)
+    xs = f(lo) + cols * sx
+    ys = f(lo) + rows * sy
+    X = np.tile(xs, H).astype(np.float64)
+    Y = np.repeat(ys, W).astype(np.float64)
+    return X, Y
+
+
+# ---------------------------------------------------------------- Eq. 1
+
+def test_pagie_golden_points():
+    rows = [l.split() for l in open(os.path.join(GOLD, "pagie_points.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 8
+    for x, y, num, den in rows:
+        exp = float(Fraction(int(num), int(den)))
+        got = oracle.pagie(float(x), float(y))
+        assert got == pytest.approx(exp, rel=1e-15, abs=1e-15), (x, y)
+
+
+def test_pagie_symmetry_and_limit():
+    for x, y in [(0.3, -2.0), (4.0, 1.5)]:
+        assert oracle.pagie(x, y) == oracle.pagie(-x, y) == oracle.pagie(y, x)
+    assert oracle.pagie(1e6, 1e6) == pytest.approx(2.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- grid
+
+@pytest.mark.parametrize("W,H", [(1, 1), (2, 3), (7, 5), (64, 64), (33, 17)])
+def test_grid_matches_binary32_linspace(W, H):
+    X, Y = np_grid(W, H)
+    for p in range(W * H):
+        x, y = oracle.grid_point(W, H, -5.0, 5.0, -5.0, 5.0, p)
+        assert (x, y) == (X[p], Y[p])
+    # endpoints: first column / row is exactly lo
+    assert oracle.grid_point(W, H, -5.0, 5.0, -5.0, 5.0, 0) == (-5.0, -5.0)
+
+
+def test_grid_endpoints_close_to_hi():
+    x, y = oracle.grid_point(64, 64, -5.0, 5.0, -5.0, 5.0, 64 * 64 - 1)
+    assert abs(x - 5.0) < 1e-5 and abs(y - 5.0) < 1e-5
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_x_plus_y_and_x_times_x():
+    W, H = 7, 5
+    X, Y = np_grid(W, H)
+    v64, v32, fl = ev(["add(x, y)", "mult(x, x)", "x", "y", "sub(x, y)"], W, H)
+    assert np.array_equal(v64[0], X + Y)
+    assert np.array_equal(v64[1], X * X)
+    assert np.array_equal(v64[2], X)
+    assert np.array_equal(v64[3], Y)
+    assert np.array_equal(v64[4], X - Y)
+    assert not fl.any()
+    # FP32-faithful values are the binary32 roundings of single IEEE ops
+    f = np.float32
+    assert np.array_equal(v32[0], (X.astype(f) + Y.astype(f)))
+    assert np.array_equal(v32[1], (X.astype(f) * X.astype(f)))
+
+
+PAGIE_TREE = ("add(div(mult(mult(x, x), mult(x, x)), add(1.0, mult(mult(x, x), mult(x, x)))),"
+              " div(mult(mult(y, y), mult(y, y)), add(1.0, mult(mult(y, y), mult(y, y)))))")
+
+
+def test_pagie_as_tree_has_zero_rmse():
+    t = toks(PAGIE_TREE)
+    r64, r32, nf = oracle.fitness(t.ops, t.imm, t.tree_off, 0, 64, 64, -5, 5, -5, 5)
+    assert r64[0] < 1e-15
+    assert r32[0] < 1e-6  # binary32 roundoff only
+    assert nf[0] == 0
+
+
+def test_rmse_of_zero_tree_is_rms_of_target():
+    W, H = 33, 17
+    t = toks("sub(x, x)")
+    r64, _, _ = oracle.fitness(t.ops, t.imm, t.tree_off, 0, W, H, -5, 5, -5, 5)
+    X, Y = np_grid(W, H)
+    P = X ** 4 / (1 + X ** 4) + Y ** 4 / (1 + Y ** 4)
+    assert r64[0] == pytest.approx(math.sqrt(np.mean(P ** 2)), rel=1e-14)
+
+
+def test_rmse_by_hand_on_2x2_grid():
+    # grid 2x2 over [-5,5]: points (+-5, +-5); P = 2*625/626 at all four
+    a = Fraction(625, 313)
+    t = toks("x", "add(x, y)", "0.5")
+    r64, _, _ = oracle.fitness(t.ops, t.imm, t.tree_off, 0, 2, 2, -5, 5, -5, 5)
+    ex = math.sqrt(float(((Fraction(-5) - a) ** 2 + (Fraction(5) - a) ** 2) / 2))
+    exy = math.sqrt(float(((Fraction(-10) - a) ** 2 + 2 * a ** 2 + (Fraction(10) - a) ** 2) / 4))
+    ec = math.sqrt(float((Fraction(1, 2) - a) ** 2))
+    assert r64[0] == pytest.approx(ex, rel=1e-15)
+    assert r64[1] == pytest.approx(exy, rel=1e-15)
+    assert r64[2] == pytest.approx(ec, rel=1e-15)
+
+
+def test_rmse_against_given_values_divides_by_n():
+    W, H = 3, 2
+    target = np.arange(6, dtype=np.float64)
+    t = toks("0.0")
+    r64, _, _ = oracle.fitness(t.ops, t.imm, t.tree_off, 0, W, H, -5, 5, -5, 5, target=target)
+    assert r64[0] == pytest.approx(math.sqrt(sum(v * v for v in range(6)) / 6), rel=1e-15)
+
+
+def test_nonfinite_fitness_is_inf():
+    # x^1024 by repeated squaring: 5^1024 overflows binary64 (and binary32)
+    e = "0.9"
+    big = "mult(mult(x, x), mult(x, x))"
+    for _ in range(8):
+        big = f"mult({big}, {big})"
+    t = toks(big, e, f"sin({big})")
+    r64, r32, _ = oracle.fitness(t.ops, t.imm, t.tree_off, 0, 4, 4, -5, 5, -5, 5)
+    assert math.isinf(r64[0]) and math.isinf(r32[0])
+    assert math.isfinite(r64[1])
+    # sin(pi * inf) is NaN; a NaN phenotype also gives fitness +inf
+    assert r64[2] == math.inf and r32[2] == math.inf
+
+
+# ---------------------------------------------------------------- operators
+
+def test_trig_is_pi_scaled_special_values():
+    # Sec. 3.2: argument multiplied by pi
+    assert oracle.sinpi(0.5) == 1.0
+    assert oracle.cospi(1.0) == -1.0
+    assert oracle.sinpi(1.0) == 0.0
+    assert oracle.cospi(0.5) == 0.0
+    assert oracle.sinpi(-0.5) == -1.0
+    assert oracle.sinpi(2.5) == 1.0
+    assert oracle.cospi(-3.0) == -1.0
+    assert oracle.sinpi(1e7 + 0.5) == 1.0
+
+
+def test_trig_against_numpy_for_moderate_arguments():
+    a = np.linspace(-7.3, 7.3, 1001)
+    s = np.array([oracle.sinpi(v) for v in a])
+    c = np.array([oracle.cospi(v) for v in a])
+    assert np.allclose(s, np.sin(np.pi * a), rtol=0, atol=1e-14)
+    assert np.allclose(c, np.cos(np.pi * a), rtol=0, atol=1e-14)
+    # not the unscaled (radian) functions, and not swapped (Table 1 typo)
+    assert not np.allclose(s, np.sin(a), atol=1e-3)
+    assert not np.allclose(s, np.cos(np.pi * a), atol=1e-3)
+
+
+def test_trig_periodicity_and_parity():
+    for a in [0.1, 0.37, 1.9, 3.25]:
+        assert oracle.sinpi(a + 2) == pytest.approx(oracle.sinpi(a), abs=1e-14)
+        assert oracle.sinpi(-a) == -oracle.sinpi(a)
+        assert oracle.cospi(-a) == oracle.cospi(a)
+        assert oracle.sinpi(a) ** 2 + oracle.cospi(a) ** 2 == pytest.approx(1.0, abs=1e-15)
+
+
+def test_special_trees():
+    W, H = 7, 5
+    X, Y = np_grid(W, H)
+    v64, _, fl = ev(["sin(0.5)", "cos(1.0)", "div(x, sub(y, y))", "neg(neg(x))", "abs(neg(x))",
+                     "min(x, y)", "max(x, y)", "div(x, y)", "neg(x)", "cos(x)"], W, H)
+    assert np.all(v64[0] == 1.0)
+    assert np.all(v64[1] == -1.0)
+    assert np.all(v64[2] == 0.0)        # protected division
+    assert fl[2].all()                   # denominator 0 is flagged near-singular
+    assert np.array_equal(v64[3], X)
+    assert np.array_equal(v64[4], np.abs(X))
+    assert np.array_equal(v64[5], np.minimum(X, Y))
+    assert np.array_equal(v64[6], np.maximum(X, Y))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(Y == 0, 0.0, X / Y)
+    assert np.array_equal(v64[7], q)
+    assert np.array_equal(v64[8], -X)
+    assert np.allclose(v64[9], np.cos(np.pi * X), atol=2e-15, rtol=0)
+
+
+def test_protected_division_negative_zero():
+    # sub(x, x) is +0; neg of it is -0: both are zero denominators
+    v64, v32, _ = ev(["div(1.0, neg(sub(x, x)))", "div(0.25, mult(x, 0.0))"], 3, 3)
+    assert np.all(v64 == 0.0) and np.all(v32 == 0.0)
+
+
+def test_near_singular_flag():
+    # denominator x - c where c is 1e-7 away from a grid coordinate
+    W, H = 3, 1   # x in {-5, 0, 5}
+    v64, _, fl = ev(["div(1.0, sub(x, 1e-7))", "div(1.0, sub(x, 1e-3))", "add(x, 1e-9)"], W, H)
+    assert fl[0].tolist() == [False, True, False]
+    assert not fl[1].any() and not fl[2].any()
+
+
+# ---------------------------------------------------------------- FP32-faithful
+
+def test_fp32_faithful_single_ops_equal_numpy_binary32():
+    rng = np.random.default_rng(5)
+    W, H = 16, 8
+    X, Y = np_grid(W, H)
+    f = np.float32
+    x32, y32 = X.astype(f), Y.astype(f)
+    c = f(rng.uniform(-1, 1))
+    cs = repr(float(c))
+    v64, v32, _ = ev([f"add(x, {cs})", f"sub({cs}, y)", f"mult(x, y)", f"div(x, {cs})",
+                      "min(x, y)", "max(x, neg(y))", "abs(sub(x, y))"], W, H)
+    with np.errstate(all="ignore"):
+        exp = [x32 + c, c - y32, x32 * y32, x32 / c, np.minimum(x32, y32),
+               np.maximum(x32, -y32), np.abs(x32 - y32)]
+    for i, e in enumerate(exp):
+        assert np.array_equal(v32[i], e), i
+
+
+def test_fp32_faithful_rounds_every_node():
+    # (x*c1)*c2 in binary32 differs from x*(c1*c2) rounded once for some x
+    W, H = 64, 1
+    v64, v32, _ = ev(["mult(mult(x, 0.1), 0.3)"], W, H)
+    X, _ = np_grid(W, H)
+    f = np.float32
+    assert np.array_equal(v32[0], (X.astype(f) * f(0.1)) * f(0.3))
+
+
+# ---------------------------------------------------------------- encodings
+
+def test_prefix_equals_postfix_on_random_population():
+    tok, g = I.small_population(seed=0)
+    post = I.convert_order(tok, I.POSTFIX)
+    assert not np.array_equal(tok.ops, post.ops)
+    a = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, I.PREFIX, 9, 7, -5, 5, -5, 5)
+    b = oracle.evaluate(post.ops, post.imm, post.tree_off, I.POSTFIX, 9, 7, -5, 5, -5, 5)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v, equal_nan=True)
+
+
+def test_duplicate_and_permuted_trees_keep_fitness():
+    tok, g = I.small_population(seed=3)
+    trees = I.from_tokens(tok)
+    perm = list(reversed(trees)) + trees[:5]
+    t2 = I.to_tokens(perm)
+    r1, _, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, 16, 16, -5, 5, -5, 5)
+    r2, _, _ = oracle.fitness(t2.ops, t2.imm, t2.tree_off, 0, 16, 16, -5, 5, -5, 5)
+    assert np.array_equal(r2[:len(trees)], r1[::-1])
+    assert np.array_equal(r2[len(trees):], r1[:5])
+
+
+def test_malformed_tokens_are_rejected():
+    cases = [
+        ([3, 0], [], [0, 2]),            # add with one operand
+        ([0, 1], [], [0, 2]),            # two terminals
+        ([42], [], [0, 1]),              # unknown opcode
+        ([2], [], [0, 1]),               # CONST without imm
+        ([0], [1.0], [0, 1]),            # imm left over
+    ]
+    for ops, imm, off in cases:
+        with pytest.raises(oracle.OracleError):
+            oracle.evaluate(np.array(ops), np.array(imm, np.float32), np.array(off), 0, 2, 2, -1, 1, -1, 1)
+
+
+# ---------------------------------------------------------------- brute force
+
+def _all_trees(depth):
+    """Every tree of depth <= depth over {x, y, 0.5} and the 10 functions."""
+    leaves = ["x", "y", "0.5"]
+    if depth == 0:
+        return leaves
+    sub = _all_trees(depth - 1)
+    out = list(leaves)
+    for f in ["sin", "cos", "neg", "abs"]:
+        out += [f"{f}({a})" for a in sub]
+    for f in ["add", "sub", "mult", "div", "min", "max"]:
+        out += [f"{f}({a}, {b})" for a in sub for b in sub]
+    return out
+
+
+def _np_eval(tree, X, Y, sing):
+    """Direct numpy binary64 evaluation of a tuple tree (independent of the
+    oracle: numpy ufuncs, pi-scaled trig through np.sin(np.pi * a)).  sing is
+    OR-ed with the points where a division saw |denominator| < 1e-6 (there the
+    inexact numpy trig may turn an exact zero denominator into a tiny one)."""
+    op, v, kids = tree
+    if op == I.X:
+        return X
+    if op == I.Y:
+        return Y
+    if op == I.CONST:
+        return np.full_like(X, float(v))
+    a = _np_eval(kids[0], X, Y, sing)
+    b = _np_eval(kids[1], X, Y, sing) if len(kids) > 1 else None
+    if op == I.DIV:
+        sing |= np.abs(b) < 1e-6
+    with np.errstate(all="ignore"):
+        return {
+            I.ADD: lambda: a + b, I.SUB: lambda: a - b, I.MUL: lambda: a * b,
+            I.DIV: lambda: np.where(b == 0, 0.0, a / np.where(b == 0, 1.0, b)),
+            I.SIN: lambda: np.sin(np.pi * a), I.COS: lambda: np.cos(np.pi * a),
+            I.NEG: lambda: -a, I.ABS: lambda: np.abs(a),
+            I.MIN: lambda: np.fmin(a, b), I.MAX: lambda: np.fmax(a, b),
+        }[op]()
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (2, 2), (3, 5)])
+def test_brute_force_depth2_trees(W, H):
+    exprs = _all_trees(2)
+    assert len(exprs) > 1000
+    trees = [I.parse_string(e) for e in exprs]
+    tok = I.to_tokens(trees)
+    v64, _, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, W, H, -5, 5, -5, 5)
+    X, Y = np_grid(W, H)
+    sing = np.zeros((len(trees), W * H), bool)
+    exp = np.stack([_np_eval(t, X, Y, sing[i]) for i, t in enumerate(trees)])
+    ok = ~(sing | fl)
+    assert ok.mean() > 0.9
+    # trig: numpy's sin(pi*a) carries ~1e-15 absolute error that the exact
+    # reduction avoids; everything else is identical
+    assert np.allclose(v64[ok], exp[ok], rtol=1e-13, atol=1e-13, equal_nan=True)
+    # trees without any division agree on every point
+    nodiv = np.array(["div" not in e for e in exprs])
+    assert np.allclose(v64[nodiv], exp[nodiv], rtol=1e-13, atol=1e-13, equal_nan=True)
+    r64, _, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, W, H, -5, 5, -5, 5)
+    P = X ** 4 / (1 + X ** 4) + Y ** 4 / (1 + Y ** 4)
+    with np.errstate(all="ignore"):
+        re = np.sqrt(np.mean((exp - P) ** 2, axis=1))
+    re = np.where(np.isfinite(re), re, np.inf)
+    clean = ok.all(axis=1)
+    assert np.allclose(r64[clean], re[clean], rtol=1e-12, atol=1e-13)
+
+
+def test_golden_regression_small_population():
+    """Config-1 fitness written by tests/golden/make_golden.py (oracle only);
+    guards the oracle against unintended changes."""
+    path = os.path.join(GOLD, "small_population_rmse.txt")
+    exp = np.loadtxt(path)
+    tok, g = I.small_population(seed=0)
+    r64, _, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    assert np.allclose(r64, exp, rtol=1e-12, atol=0, equal_nan=False)

@@ -1,0 +1,57 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case copies oracle/tgp_oracle.c to a temporary directory, plants one
+mistake (a swapped operand, a dropped term, a wrong index, ...), builds the
+copy and runs tests/test_oracle.py against it in a subprocess.  The pin suite
+must fail for every mutant.  Nothing here runs on a GPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "tgp_oracle.c")
+
+MUTANTS = {
+    "sub_operands_swapped": ("case O_SUB: return a - b;", "case O_SUB: return b - a;"),
+    "div_protection_value": ("if (b == 0.0) return 0.0;", "if (b == 0.0) return 1.0;"),
+    "trig_not_pi_scaled": ("double pf = ORACLE_PI * f, v;", "double pf = f, v;"),
+    "sin_cos_swapped": ("case O_SIN: return oracle_sinpi(a);\n    case O_COS: return oracle_cospi(a);",
+                        "case O_SIN: return oracle_cospi(a);\n    case O_COS: return oracle_sinpi(a);"),
+    "pagie_wrong_index": ("y4 / (1.0 + y4)", "x4 / (1.0 + y4)"),
+    "pagie_dropped_term": ("return x4 / (1.0 + x4) + y4 / (1.0 + y4);", "return x4 / (1.0 + x4);"),
+    "linspace_off_by_one": ("float step = (hi - lo) / (float)(n - 1);", "float step = (hi - lo) / (float)n;"),
+    "rmse_divides_by_n_minus_1": ("double r64 = sqrt(s64 / (double)N);", "double r64 = sqrt(s64 / (double)(N - 1));"),
+    "postfix_operands_transposed": ("for (int c = ar - 1; c >= 0; c--) nodes[me].kid[c] = stack[--sp];",
+                                    "for (int c = 0; c < ar; c++) nodes[me].kid[c] = stack[--sp];"),
+    "grid_row_col_swapped": ("int64_t row = p / W, col = p % W;", "int64_t col = p / W, row = p % W;"),
+    "min_is_max": ("case O_MIN: return fmin(a, b);", "case O_MIN: return fmax(a, b);"),
+    "fp32_mode_not_rounded_per_node": ("*v32 = (float)apply64(n->op, (double)a32, (double)b32);",
+                                       "*v32 = (float)apply64(n->op, a64, b64);"),
+    "near_singular_threshold": ("#define NEAR_SINGULAR 1e-6", "#define NEAR_SINGULAR 1e-9"),
+    "nan_fitness_not_inf": ("rmse64[t] = isfinite(r64) ? r64 : INFINITY;", "rmse64[t] = r64;"),
+    "abs_dropped": ("case O_ABS: return fabs(a);", "case O_ABS: return a;"),
+    "const_imm_order": ("nodes[me].imm = (double)imm[(*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {",
+                        "nodes[me].imm = (double)imm[n_imm - 1 - (*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new)
+    c = tmp_path / "mut.c"
+    so = tmp_path / "libmut.so"
+    c.write_text(mutated)
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+                           "-o", str(so), str(c), "-lm"])
+    env = dict(os.environ, TGP_ORACLE_LIB_OVERRIDE=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the oracle pins:\n{r.stdout[-2000:]}"

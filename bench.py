@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: node-evaluations/s of the fused population evaluator on GB300.
+
+Workload (the single-GPU configuration the headline metric is quoted on):
+100 ramped half-and-half trees (depth 2-8, functions add sub mul div sin cos
+neg abs min max, terminals x, y, const ~ U[-1,1], seed 1) over a 1024x1024
+binary32 grid on [-5,5]^2, RMSE against the Pagie polynomial, population-wide
+subtree DAG on.  One step = one fitness pass over the population.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line.  `value` times the device-resident path (bytecode
+already uploaded, CUDA events around each step, L2 flushed between steps);
+`e2e` times the public API from host tokens (compile -> upload -> kernels ->
+fitness on the host) per step.  --impl reference times the CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_2103_07512_gb300 import inputs as I  # noqa: E402
+
+METRIC = "node-evals/s (tree nodes x fitness cases)"
+UNIT = "node-evals/s"
+WORKLOAD = "population_at_scale: 100 RHH trees depth 2-8, 1024x1024 grid, Pagie target, seed 1"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+PROFILE = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
+KERNEL_SRC = os.path.join(HERE, "paper_2103_07512_gb300", "csrc", "kernels.cu")
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload():
+    tok, g = I.population_at_scale(seed=1)
+    return tok, g
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+        smi = shutil.which("nvidia-smi")
+        if smi:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen([smi, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(device_index), "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append({"sm": float(parts[2]), "max": float(parts[3]),
+                             "power": float(parts[4]) if parts[4] not in ("[N/A]", "N/A") else 0.0,
+                             "hw_slowdown": parts[6], "hw_thermal": parts[7], "sw_thermal": parts[8],
+                             "sw_power_cap": parts[9]})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 0.3 * max(r["power"] for r in rows)] or rows
+        reasons = set()
+        for r in load:
+            for k in ("hw_slowdown", "hw_thermal", "sw_thermal", "sw_power_cap"):
+                if r[k].lower().startswith("active"):
+                    reasons.add({"hw_thermal": "hw_thermal_slowdown", "sw_thermal": "sw_thermal_slowdown"}.get(k, k))
+        return {"sm_mhz": float(np.median([r["sm"] for r in load])), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load), "power_w_max": max(r["power"] for r in rows)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def profile_traffic():
+    """dram bytes per launch of the interpreter from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if cur != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def weighted_work(tok, costs):
+    """sum over tree nodes of the calibrated issue cost of their operator."""
+    counts = np.bincount(tok.ops, minlength=len(costs))
+    return float(np.dot(counts[:len(costs)], costs))
+
+
+def cpu_oracle_rate(tok, g, target_seconds=12.0):
+    """The oracle as it stands, single thread, on a bounded sample of rows."""
+    import oracle
+    oracle.build()
+    nodes = int(tok.ops.size)
+    rows = 8
+    while True:
+        pts = np.arange(rows * g.W, dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
+        dt = time.perf_counter() - t0
+        if dt >= target_seconds / 4 or rows >= g.H:
+            break
+        rows = min(g.H, rows * max(2, int(target_seconds / 4 / max(dt, 1e-3))))
+    return nodes * pts.size / dt, {"rows": rows, "points": int(pts.size), "seconds": dt}
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    tok, g = workload()
+    nodes = int(tok.ops.size)
+    rows = max(1, min(g.H, args.ref_rows))
+    pts = np.arange(rows * g.W, dtype=np.int64)
+    for _ in range(args.warmup):
+        oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = nodes * pts.size / dt
+    sample = f"{rows} of {g.H} grid rows ({pts.size} points) per step, all {tok.n_trees} trees, binary64 + FP32-faithful walk"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2103_07512_gb300 as tgp
+    from paper_2103_07512_gb300.perop import PerOpEvaluator
+
+    rank, local, world = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tok, g = workload()
+    T = tok.n_trees
+    nodes = int(tok.ops.size)
+    units = nodes * g.N                                   # node-evals per step
+
+    ctx = tgp.Context(device=local, time_kernels=True)
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    pop = ctx.compile_tokens(tok)
+    st = ctx.stats()
+    dag_internal = st["dag_internal"]
+    costs = ctx.calibrate_op_costs()
+    work = weighted_work(tok, costs) * g.N               # lane-instructions per step
+    rmse = torch.empty(T, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    # keep the GPU busy ~1.5 s before the timed region so the clock record sees load
+    t_heat = time.perf_counter()
+    while time.perf_counter() - t_heat < 1.5:
+        for _ in range(20):
+            ctx.fitness_dev(pop, dom, rmse, stream=stream)
+        torch.cuda.synchronize()
+    s0 = ctx.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))                               # evict L2 between steps (untimed)
+        evs[i][0].record(stream)
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    s1 = ctx.stats()
+    step_ms = float(np.sum([a.elapsed_time(b) for a, b in evs])) / args.steps
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    kern_ms = (s1["eval_ms_sum"] - s0["eval_ms_sum"]) / max(1, s1["eval_timed"] - s0["eval_timed"])
+    launches = int(s1["launches"] - s0["launches"])
+    value = world * units / (step_ms * 1e-3)
+
+    # -------- end to end through the public API from host tokens
+    e2e_steps = max(3, min(args.steps, 20))
+    h2d = d2h = 0
+    e2e_times = []
+    for i in range(e2e_steps + 1):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = ctx.compile_population(tok.ops, tok.imm, tok.tree_off, tok.order)
+        fit = ctx.fitness(p2, dom, T, blocking=True)
+        t1 = time.perf_counter()
+        s = ctx.stats()
+        ctx.release_population(p2)
+        if i > 0:                                          # first one warms the allocator
+            e2e_times.append(t1 - t0)
+        h2d = (s["code_instrs"] + 1) * 8 + (s["n_groups"] + 1) * 8 + s["n_groups"] * 4
+        d2h = 8 * T
+    e2e_s = float(np.mean(e2e_times))
+    e2e_value = world * units / e2e_s
+
+    # -------- per-operator materialising baseline on the same GPU
+    per = PerOpEvaluator(g, device=dev)
+    trees = I.from_tokens(tok)
+    for _ in range(2):
+        per.fitness(trees)
+    torch.cuda.synchronize()
+    pe = []
+    for i in range(3):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pr = per.fitness(trees)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pe.append(a.elapsed_time(b))
+    perop_ms = float(np.median(pe))
+    perop_value = units / (perop_ms * 1e-3)
+    fit_dev = rmse.cpu().numpy()
+    pr = pr.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(fit_dev) & np.isfinite(pr)
+    perop_agree = float(np.mean(np.abs(fit_dev[fin] - pr[fin]) <= 1e-3 * np.abs(fit_dev[fin]) + 1e-5)) if fin.any() else None
+
+    if rank != 0:
+        return 0
+
+    # -------- CPU oracle baseline (rank 0, bounded sample)
+    cpu_value, cpu_info = cpu_oracle_rate(tok, g, target_seconds=args.cpu_seconds)
+
+    peak_tops = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved_tops = work / (kern_ms * 1e-3) / 1e12
+    traffic = profile_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "trees": T, "tree_nodes": nodes, "dag_internal_nodes": int(dag_internal),
+                   "points": g.N, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "points_per_thread": int(s1["points_per_thread"]),
+                   "threads_per_block": int(s1["threads_per_block"]), "groups": int(s1["n_groups"])},
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
+                     "unit": "TOP/s (binary32 lane-instructions)", "frac": achieved_tops / peak_tops,
+                     "traffic": traffic, "kernel_ms": kern_ms,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal unit counts and max clock)",
+                     "op_costs": {I.NAMES[i]: round(float(costs[i]), 3) for i in range(len(costs))},
+                     "frac_one_op_per_node": (units / (kern_ms * 1e-3) / 1e12) / peak_tops},
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{cpu_info['rows']} of {g.H} rows ({cpu_info['points']} points), all trees, "
+                                   f"{cpu_info['seconds']:.1f} s"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_s * 1e3},
+        "perop_baseline": {"value": perop_value, "unit": UNIT, "ms_per_step": perop_ms,
+                           "speedup": value / perop_value, "fitness_agreement": perop_agree,
+                           "launches_per_step": per.launches // 5},
+        "dag_node_evals_per_s": world * int(dag_internal) * g.N / (step_ms * 1e-3),
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

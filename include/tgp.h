@@ -1,0 +1,247 @@
+/*
+ * tgp.h -- C ABI of libtgp: GPU evaluation of a population of GP expression
+ * trees over every point of a regular 2-D grid, with structurally identical
+ * subtrees deduplicated into a population DAG, reduced to per-tree RMSE.
+ *
+ * Method: TensorGP (Baeta, Correia, Martins, Machado; arXiv 2103.07512).
+ *   - tensor phenotype: each individual evaluates to a tensor over the whole
+ *     fixed domain of fitness cases (Sec. 3.1);
+ *   - caching of intermediate subtree results and a population DAG that does
+ *     not duplicate identical subtrees (Sec. 2, Handley; Sec. 3.1);
+ *   - fixed-size cache with update and flush (Sec. 2, Keijzer);
+ *   - operators and protections of Table 1, trigonometry on pi*x (Sec. 3.2);
+ *   - Pagie target, Eq. 1; RMSE fitness (Sec. 4.1, Table 2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: TGP_OK (0) or a negative tgp_status.  Nothing aborts or
+ *     exits the process.  tgp_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ *   - Ownership: the caller owns every pointer it passes; arrays are read (or
+ *     copied) during the call unless stated otherwise.  The library owns the
+ *     objects behind handles until the matching release call.
+ *   - Streams: `stream` is a cudaStream_t (e.g. torch.cuda.Stream.cuda_stream)
+ *     or NULL for the legacy default stream.  Device work is enqueued on it.
+ *   - Thread safety: calls on one context may come from several threads; host
+ *     state is serialised by a per-context lock.  Two concurrent evaluations of
+ *     the same (population, domain) pair on different streams are not allowed
+ *     (they share device scratch); distinct pairs may overlap freely.
+ *   - Device memory: allocated by the library on the context's device with
+ *     cudaMalloc; TGP_E_NOMEM when an allocation fails.
+ */
+#ifndef TGP_H
+#define TGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tgp_ctx tgp_ctx;
+typedef int64_t tgp_handle;
+
+typedef enum tgp_status {
+    TGP_OK = 0,
+    TGP_E_INVALID = -1,       /* bad argument or handle */
+    TGP_E_TOKENS = -2,        /* malformed token stream (arity, opcode, imm, limits) */
+    TGP_E_NOMEM = -3,         /* host or device allocation failed */
+    TGP_E_BUDGET = -4,        /* request does not fit the context's HBM budget */
+    TGP_E_CUDA = -5,          /* a CUDA runtime call failed (message has the name) */
+    TGP_E_TIMEOUT = -6,       /* a bounded wait ran out */
+    TGP_E_DEVICE_CHECK = -7,  /* a device-side check recorded a violation */
+    TGP_E_BUSY = -8           /* object in use (e.g. releasing a pinned cache entry) */
+} tgp_status;
+
+/* Token order of a population (Sec. 3.1: genotype as an expression tree). */
+enum { TGP_PREFIX = 0, TGP_POSTFIX = 1 };
+
+/* Target of the fitness (Sec. 4.1). */
+enum {
+    TGP_TARGET_PAGIE = 0,   /* Eq. 1, computed inline from the coordinates */
+    TGP_TARGET_TENSOR = 1,  /* float[H*W], host or device pointer */
+    TGP_TARGET_TOKENS = 2   /* one expression tree (tgp_target_tokens*) evaluated on the grid */
+};
+
+/* Opcodes of the token stream: the terminals and the Table 1 functions used
+ * by the configured function set.  Arity: X, Y, CONST 0; SIN, COS, NEG, ABS 1;
+ * ADD, SUB, MUL, DIV, MIN, MAX 2.  CONST takes the next value of `imm`. */
+enum {
+    TGP_OP_X = 0, TGP_OP_Y = 1, TGP_OP_CONST = 2,
+    TGP_OP_ADD = 3,  /* a + b                                  (Table 1, add)  */
+    TGP_OP_SUB = 4,  /* a - b                                  (Table 1, sub)  */
+    TGP_OP_MUL = 5,  /* a * b                                  (Table 1, mult) */
+    TGP_OP_DIV = 6,  /* a / b, 0 when b == 0                   (Table 1, div)  */
+    TGP_OP_SIN = 7,  /* sin(pi * a)                            (Sec. 3.2)      */
+    TGP_OP_COS = 8,  /* cos(pi * a)                            (Sec. 3.2)      */
+    TGP_OP_NEG = 9,  /* -a                                     (Table 1, neg)  */
+    TGP_OP_ABS = 10, /* |a|                                    (Table 1, abs)  */
+    TGP_OP_MIN = 11, /* fminf(a, b)                            (Table 1, min)  */
+    TGP_OP_MAX = 12, /* fmaxf(a, b)                            (Table 1, max)  */
+    TGP_N_OPS = 13
+};
+
+/* Limits checked by tgp_compile_population (TGP_E_TOKENS beyond them). */
+#define TGP_MAX_DEPTH 1024              /* root alone has depth 0 */
+#define TGP_MAX_TREE_TOKENS (1 << 24)
+#define TGP_MAX_TREES (1 << 24)
+
+/* tgp_config.flags */
+#define TGP_F_HOST_ONLY 1     /* no device: compile and inspect plans only (for
+                                 machines without a GPU); device calls fail with
+                                 TGP_E_INVALID.  Plans assume 152 SMs. */
+#define TGP_F_NO_DEDUP 2      /* evaluate every tree as a tree: a shared subtree
+                                 is recomputed at each use instead of being held
+                                 (the uncached reference; results are bitwise
+                                 equal to the deduplicated evaluation) */
+#define TGP_F_TIME_KERNELS 4  /* record CUDA events around every interpreter
+                                 launch on its stream; tgp_stats_get reports the
+                                 summed kernel time */
+
+/* Context configuration.  Zero-initialise, then set what you need. */
+typedef struct tgp_config {
+    int32_t device;              /* CUDA device ordinal */
+    int32_t flags;               /* TGP_F_* */
+    int64_t cache_budget_bytes;  /* HBM budget of the cross-call subtree cache; 0 disables it */
+    int32_t points_per_thread;   /* 0 = automatic (autotuned); else 1, 2, 4 or 8 */
+    int32_t threads_per_block;   /* 0 = automatic; else 32, 64 or 128 */
+    int32_t n_groups;            /* 0 = automatic; else trees are split into this many groups */
+    int32_t reserved[5];
+} tgp_config;
+
+/* A target given as one expression tree (TGP_TARGET_TOKENS). */
+typedef struct tgp_target_tokens {
+    const int32_t* ops;   /* opcodes of one tree */
+    const float* imm;     /* one value per CONST token, in stream order */
+    int64_t n_ops;
+    int64_t n_imm;
+    int32_t order;        /* TGP_PREFIX or TGP_POSTFIX */
+} tgp_target_tokens;
+
+/* Counters, reset by tgp_create only. */
+typedef struct tgp_stats {
+    int64_t tree_nodes;       /* sum of tree sizes of the last compiled population */
+    int64_t dag_nodes;        /* unique nodes of its population DAG (terminals included) */
+    int64_t dag_internal;     /* unique function nodes */
+    int64_t code_instrs;      /* bytecode instructions of the last plan used */
+    int64_t n_groups;         /* tree groups of the last plan */
+    int64_t n_items;          /* (group, tile) work items of the last launch */
+    int32_t points_per_thread, threads_per_block;
+    int32_t spill_slots;      /* shared-memory spill slots of the last plan */
+    int32_t reserved0;
+    int64_t cache_entries;    /* live cache entries */
+    int64_t cache_bytes;      /* HBM held by the cache */
+    int64_t cache_hits;       /* subtree loads served from the cache */
+    int64_t cache_inserts;
+    int64_t cache_evictions;
+    int64_t launches;         /* kernels launched by the library so far */
+    double eval_ms_sum;       /* TGP_F_TIME_KERNELS: summed interpreter kernel time */
+    int64_t eval_timed;       /* TGP_F_TIME_KERNELS: launches summed in eval_ms_sum */
+    int64_t reserved[6];
+} tgp_stats;
+
+/* Creates a context on cfg->device (cfg may be NULL: device 0, defaults). */
+int tgp_create(tgp_ctx** out, const tgp_config* cfg);
+
+/* Frees the context and everything it owns (domains, populations, cache). */
+int tgp_destroy(tgp_ctx* ctx);
+
+/* Message of the calling thread's last failed call ("" if none).  The string
+ * stays valid until the next call on this thread. */
+const char* tgp_last_error(const tgp_ctx* ctx);
+
+/*
+ * Loads a domain: a W x H grid of fitness cases (Sec. 3.1; Table 2 uses square
+ * grids of 2^(2n) points) and the target.  Points are an inclusive linspace:
+ * x = xlo + col*((xhi-xlo)/(W-1)), y = ylo + row*((yhi-ylo)/(H-1)) in binary32
+ * (x = xlo when W == 1), flat index p = row*W + col.  Coordinates are never
+ * stored: kernels form them from the thread index.
+ *   target_kind TGP_TARGET_PAGIE: target must be NULL.
+ *   TGP_TARGET_TENSOR: target is float[H*W] in host or device memory (copied).
+ *   TGP_TARGET_TOKENS: target is a tgp_target_tokens*; the tree is evaluated
+ *     once on the device into the domain's target tensor.
+ * W, H >= 1 and W*H <= 2^31 - 1.
+ */
+int tgp_load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                    int32_t target_kind, const void* target, tgp_handle* domain_out);
+
+/* Releases a domain and the device memory it holds. */
+int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain);
+
+/*
+ * Compiles a population from token arrays (host memory, copied):
+ *   ops[tree_off[t] .. tree_off[t+1]) is tree t, in `order`;
+ *   imm holds one binary32 value per CONST token of the whole stream, in
+ *   stream order (n_imm values); every value must be finite.
+ * Host work only: validation, hash-consing of identical subtrees into the
+ * population DAG (Sec. 2: Handley's DAG), and per-tree statistics.  Bytecode
+ * for a given grid size is planned and uploaded lazily by the first
+ * tgp_evaluate / tgp_fitness on a domain of that size.
+ * Errors: TGP_E_TOKENS with a message naming the tree and token.
+ */
+int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, int64_t n_imm,
+                           const int64_t* tree_off, int32_t n_trees, int32_t order,
+                           tgp_handle* pop_out);
+
+/* Releases a population, its plans and device buffers. */
+int tgp_release_population(tgp_ctx* ctx, tgp_handle pop);
+
+/*
+ * Tensor phenotypes (Sec. 3.1): writes out_dev[t*H*W + p] = value of tree t at
+ * point p, binary32, for every tree and point.  out_dev is a device pointer
+ * to n_trees*H*W floats owned by the caller.  Asynchronous on `stream`.
+ */
+int tgp_evaluate(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, float* out_dev);
+
+/*
+ * RMSE fitness of every tree against the domain's target (Sec. 4.1):
+ *   rmse[t] = sqrt( sum_p (f_t(p) - target(p))^2 / (H*W) ),
+ * +inf when the sum is not finite.  Residuals are formed and squared in
+ * binary32; per-warp partial sums are added in binary64 in a fixed order, so
+ * results are bitwise reproducible.
+ * rmse_host: host array of n_trees doubles.  blocking != 0: returns after the
+ * values are in rmse_host.  blocking == 0: the copy is enqueued on `stream`
+ * and rmse_host is valid once the stream has synchronised (pass pinned memory
+ * for a truly asynchronous copy).
+ */
+int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream,
+                double* rmse_host, int32_t blocking);
+
+/* As tgp_fitness, but writes the n_trees doubles to device memory rmse_dev
+ * and never synchronises (suitable for CUDA graph capture). */
+int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
+
+/* Copies the context's counters.  With TGP_F_TIME_KERNELS it first waits for
+ * the timing events of launches not yet summed. */
+int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out);
+
+/*
+ * Host-only inspection of the bytecode plan the library would run for a grid
+ * of n_points points (used by CPU tests of the compiler; no device needed).
+ * Fills up to `cap` decoded instructions into ins_out[i*6 .. i*6+5] as
+ * (form, fn, operand1, operand2, aux, imm_bits) and the group boundaries
+ * into group_off_out[0..n_groups] (cap_groups entries at most).
+ * *n_ins and *n_groups receive the full sizes.  Forms and operand numbering
+ * are listed in tgp_debug_layout.
+ */
+int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points,
+                   int32_t* ins_out, int64_t cap, int64_t* n_ins,
+                   int64_t* group_off_out, int64_t cap_groups, int32_t* n_groups);
+
+/* Layout constants of the decoded bytecode: out[0] = number of register
+ * slots M; operands are 0 = x, 1 = y, 2 = immediate, 3..3+M-1 = register
+ * slot j, 3+M = fill buffer.  out[1] = number of forms. */
+int tgp_debug_layout(int32_t* out, int32_t n);
+
+/*
+ * Measures, with a straight-line kernel per operator, the issue cost of each
+ * opcode relative to one binary32 add (cost[TGP_OP_ADD] == 1; terminals 0).
+ * cost_out: host array of TGP_N_OPS doubles.  Synchronous; for roofline
+ * accounting only.
+ */
+int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TGP_H */

@@ -1,0 +1,263 @@
+"""tgp: GB300-native evaluation of GP expression-tree populations.
+
+Thin ctypes binding of libtgp (C ABI in include/tgp.h): argument marshalling
+only -- every step of the evaluation runs in the library's host compiler and
+CUDA kernels.  The entry points keep the C names without the ``tgp_`` prefix.
+PyTorch is used only for device memory and streams.
+
+Importing this package does not load the library; the first call does, and
+raises if libtgp.so is missing or fails to load (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtgp.so")
+
+OK = 0
+E_INVALID, E_TOKENS, E_NOMEM, E_BUDGET, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_BUSY = range(-1, -9, -1)
+PREFIX, POSTFIX = 0, 1
+TARGET_PAGIE, TARGET_TENSOR, TARGET_TOKENS = 0, 1, 2
+F_HOST_ONLY, F_NO_DEDUP, F_TIME_KERNELS = 1, 2, 4
+N_OPS = 13
+
+EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
+           "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",
+           "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
+           "tgp_calibrate_op_costs"]
+
+
+class TgpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tgp error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("cache_budget_bytes", ctypes.c_int64),
+                ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class TargetTokens(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_void_p), ("imm", ctypes.c_void_p), ("n_ops", ctypes.c_int64),
+                ("n_imm", ctypes.c_int64), ("order", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("tree_nodes", ctypes.c_int64), ("dag_nodes", ctypes.c_int64),
+                ("dag_internal", ctypes.c_int64), ("code_instrs", ctypes.c_int64),
+                ("n_groups", ctypes.c_int64), ("n_items", ctypes.c_int64),
+                ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("spill_slots", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("cache_entries", ctypes.c_int64), ("cache_bytes", ctypes.c_int64),
+                ("cache_hits", ctypes.c_int64), ("cache_inserts", ctypes.c_int64),
+                ("cache_evictions", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("eval_ms_sum", ctypes.c_double), ("eval_timed", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+_lib = None
+
+
+def lib():
+    """Loads libtgp.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        if _build.stale():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtgp.so not found at {LIB_PATH}")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        sig = {
+            "tgp_create": [P, P],
+            "tgp_destroy": [P],
+            "tgp_load_domain": [P, i32, i32, f32, f32, f32, f32, i32, P, P],
+            "tgp_release_domain": [P, i64],
+            "tgp_compile_population": [P, P, P, i64, P, i32, i32, P],
+            "tgp_release_population": [P, i64],
+            "tgp_evaluate": [P, i64, i64, P, P],
+            "tgp_fitness": [P, i64, i64, P, P, i32],
+            "tgp_fitness_dev": [P, i64, i64, P, P],
+            "tgp_stats_get": [P, P],
+            "tgp_debug_plan": [P, i64, i64, P, i64, P, P, i64, P],
+            "tgp_debug_layout": [P, i32],
+            "tgp_calibrate_op_costs": [P, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.tgp_last_error.argtypes = [P]
+        L.tgp_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    if hasattr(a, "data_ptr"):      # torch tensor
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)   # torch.cuda.Stream
+
+
+class Context:
+    """A libtgp context on one CUDA device (or host-only for plan inspection)."""
+
+    def __init__(self, device=0, host_only=False, cache_budget_bytes=0, points_per_thread=0,
+                 threads_per_block=0, n_groups=0, dedup=True, time_kernels=False):
+        self._L = lib()
+        cfg = Config()
+        cfg.device = device
+        cfg.flags = ((F_HOST_ONLY if host_only else 0) | (0 if dedup else F_NO_DEDUP)
+                     | (F_TIME_KERNELS if time_kernels else 0))
+        cfg.cache_budget_bytes = cache_budget_bytes
+        cfg.points_per_thread = points_per_thread
+        cfg.threads_per_block = threads_per_block
+        cfg.n_groups = n_groups
+        h = ctypes.c_void_p()
+        self._h = None
+        self._check(self._L.tgp_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self._L.tgp_last_error(None).decode(errors="replace")
+            raise TgpError(rc, msg)
+
+    def close(self):
+        if self._h is not None:
+            self._L.tgp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- ABI
+
+    def load_domain(self, W, H, xlo=-5.0, xhi=5.0, ylo=-5.0, yhi=5.0, target=None,
+                    target_tokens=None):
+        """tgp_load_domain: Pagie target by default; `target` = float32 [H*W]
+        array (numpy or torch, host or device); `target_tokens` = (ops, imm, order)."""
+        out = ctypes.c_int64()
+        keep = None
+        if target_tokens is not None:
+            ops, imm, order = target_tokens
+            ops = np.ascontiguousarray(ops, np.int32)
+            imm = np.ascontiguousarray(imm, np.float32)
+            tt = TargetTokens(ops.ctypes.data, imm.ctypes.data if imm.size else None,
+                              ops.size, imm.size, order)
+            keep = (ops, imm, tt)
+            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_TOKENS,
+                                         ctypes.byref(tt), ctypes.byref(out))
+        elif target is not None:
+            if isinstance(target, np.ndarray):
+                target = np.ascontiguousarray(target, np.float32)
+                if target.size != W * H:
+                    raise ValueError("target must hold H*W values")
+            keep = target
+            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_TENSOR,
+                                         _ptr(target), ctypes.byref(out))
+        else:
+            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_PAGIE, None,
+                                         ctypes.byref(out))
+        del keep
+        self._check(rc)
+        return out.value
+
+    def release_domain(self, dom):
+        self._check(self._L.tgp_release_domain(self._h, dom))
+
+    def compile_population(self, ops, imm, tree_off, order=PREFIX):
+        """tgp_compile_population from token arrays (or an inputs.Tokens)."""
+        ops = np.ascontiguousarray(ops, np.int32)
+        imm = np.ascontiguousarray(imm, np.float32)
+        tree_off = np.ascontiguousarray(tree_off, np.int64)
+        out = ctypes.c_int64()
+        self._check(self._L.tgp_compile_population(
+            self._h, _ptr(ops), _ptr(imm) if imm.size else None, imm.size, _ptr(tree_off),
+            tree_off.size - 1, order, ctypes.byref(out)))
+        return out.value
+
+    def compile_tokens(self, tok):
+        return self.compile_population(tok.ops, tok.imm, tok.tree_off, tok.order)
+
+    def release_population(self, pop):
+        self._check(self._L.tgp_release_population(self._h, pop))
+
+    def evaluate(self, pop, dom, out, stream=None):
+        """tgp_evaluate into a device float32 buffer [n_trees, H*W] (torch tensor)."""
+        self._check(self._L.tgp_evaluate(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def fitness(self, pop, dom, n_trees, stream=None, blocking=True, out=None):
+        """tgp_fitness: returns a float64 numpy array of n_trees RMSE values."""
+        if out is None:
+            out = np.empty(n_trees, np.float64)
+        self._check(self._L.tgp_fitness(self._h, pop, dom, _stream(stream), _ptr(out), int(blocking)))
+        return out
+
+    def fitness_dev(self, pop, dom, out, stream=None):
+        """tgp_fitness_dev: RMSE into a device float64 buffer (torch tensor)."""
+        self._check(self._L.tgp_fitness_dev(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def stats(self):
+        s = Stats()
+        self._check(self._L.tgp_stats_get(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def debug_plan(self, pop, n_points):
+        """tgp_debug_plan: decoded bytecode [n, 6] int32 and group offsets."""
+        n = ctypes.c_int64()
+        g = ctypes.c_int32()
+        self._check(self._L.tgp_debug_plan(self._h, pop, n_points, None, 0, ctypes.byref(n), None, 0,
+                                           ctypes.byref(g)))
+        ins = np.zeros((n.value, 6), np.int32)
+        off = np.zeros(g.value + 1, np.int64)
+        self._check(self._L.tgp_debug_plan(self._h, pop, n_points, _ptr(ins), n.value, ctypes.byref(n),
+                                           _ptr(off), off.size, ctypes.byref(g)))
+        return ins, off
+
+    def calibrate_op_costs(self):
+        c = np.zeros(N_OPS, np.float64)
+        self._check(self._L.tgp_calibrate_op_costs(self._h, _ptr(c)))
+        return c
+
+
+def debug_layout():
+    out = np.zeros(2, np.int32)
+    rc = lib().tgp_debug_layout(_ptr(out), 2)
+    if rc != OK:
+        raise TgpError(rc, "debug_layout")
+    return {"n_reg": int(out[0]), "n_forms": int(out[1])}

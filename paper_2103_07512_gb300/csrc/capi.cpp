@@ -1,0 +1,578 @@
+// capi.cpp -- the C ABI of libtgp (declared in include/tgp.h).
+//
+// Holds the context, its domains and populations, plans their bytecode per
+// grid size, uploads it, and launches the kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tgp.h"
+#include "compiler.h"
+#include "kernels.h"
+
+using namespace tgp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(TGP_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t ensure(size_t count) {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        size_t c = std::max<size_t>(count, 1);
+        cudaError_t e = cudaMalloc(&p, c * sizeof(T));
+        if (e == cudaSuccess) n = c;
+        else p = nullptr;
+        return e;
+    }
+};
+
+struct Domain {
+    int32_t W = 0, H = 0;
+    float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
+    int32_t kind = TGP_TARGET_PAGIE;
+    DevBuf<float> target;
+    int64_t N() const { return (int64_t)W * H; }
+};
+
+struct Plan {
+    HostPlan hp;
+    DevBuf<Ins> code;
+    DevBuf<int64_t> group_off;
+    DevBuf<int32_t> group_order;
+    DevBuf<float> partial;
+    DevBuf<double> rmse;
+    DevBuf<int32_t> counter;
+    double* h_rmse = nullptr;   // pinned staging
+    size_t h_rmse_n = 0;
+    int grid = 0;
+    size_t smem = 0;
+    ~Plan() {
+        if (h_rmse) cudaFreeHost(h_rmse);
+    }
+};
+
+struct Population {
+    PopIR ir;
+    std::map<PlanShape, std::unique_ptr<Plan>> plans;
+};
+
+}  // namespace
+
+struct tgp_ctx {
+    int device = 0;
+    bool host_only = false;
+    tgp_config cfg{};
+    std::mutex mu;
+    int64_t next_handle = 1;
+    std::map<int64_t, std::unique_ptr<Domain>> domains;
+    std::map<int64_t, std::unique_ptr<Population>> pops;
+    tgp_stats stats{};
+    int sms = 0;
+    std::map<std::tuple<int, int, int, size_t>, int> occ;   // (K, pheno, threads, smem) -> blocks/SM
+    // TGP_F_TIME_KERNELS: event pairs around interpreter launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+    ~tgp_ctx() {
+        for (auto& e : ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        for (auto& e : ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+};
+
+namespace {
+
+int set_device(tgp_ctx* c) {
+    if (c->host_only) return fail(TGP_E_INVALID, "context was created with TGP_F_HOST_ONLY (no device)");
+    CUDA_TRY(cudaSetDevice(c->device));
+    return TGP_OK;
+}
+
+// Sums the kernel time of finished timed launches (waits for them).
+int drain_events(tgp_ctx* c) {
+    for (auto& e : c->ev_pending) {
+        CUDA_TRY(cudaEventSynchronize(e.second));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e.first, e.second));
+        c->stats.eval_ms_sum += ms;
+        c->stats.eval_timed++;
+        c->ev_free.push_back(e);
+    }
+    c->ev_pending.clear();
+    return TGP_OK;
+}
+
+PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
+    PlanShape s = default_shape(ir, N, c->sms);
+    s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
+    if (c->cfg.points_per_thread > 0) s.K = c->cfg.points_per_thread;
+    if (c->cfg.threads_per_block > 0) s.threads = c->cfg.threads_per_block;
+    if (c->cfg.n_groups > 0) s.n_groups = c->cfg.n_groups;
+    if (c->cfg.points_per_thread > 0 || c->cfg.threads_per_block > 0) {
+        if (c->cfg.n_groups <= 0) {   // redo the group count for the forced tile
+            int64_t tile = (int64_t)s.K * s.threads;
+            int64_t n_tiles = (N + tile - 1) / tile;
+            int64_t slots = (int64_t)std::max(c->sms, 1) * 4;
+            int64_t g = (4 * slots + n_tiles - 1) / n_tiles;
+            s.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<size_t>(ir.roots.size(), 1)));
+        }
+    }
+    return s;
+}
+
+int occupancy(tgp_ctx* c, int K, bool pheno, int threads, size_t smem, int* out) {
+    auto key = std::make_tuple(K, (int)pheno, threads, smem);
+    auto it = c->occ.find(key);
+    if (it != c->occ.end()) { *out = it->second; return TGP_OK; }
+    int b = 0;
+    CUDA_TRY(eval_occupancy(K, pheno, threads, smem, &b));
+    if (b <= 0) return fail(TGP_E_INVALID, "kernel cannot be resident with %d threads and %zu bytes of shared memory", threads, smem);
+    c->occ[key] = b;
+    *out = b;
+    return TGP_OK;
+}
+
+// Builds (once) and uploads the plan of `pop` for a grid of N points.
+int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s, Plan** out) {
+    PlanShape shape = choose_shape(c, pop->ir, N);
+    if (shape.K != 1 && shape.K != 2 && shape.K != 4 && shape.K != 8)
+        return fail(TGP_E_INVALID, "points_per_thread must be 1, 2, 4 or 8 (got %d)", shape.K);
+    if (shape.threads != 32 && shape.threads != 64 && shape.threads != 128)
+        return fail(TGP_E_INVALID, "threads_per_block must be 32, 64 or 128 (got %d)", shape.threads);
+    auto it = pop->plans.find(shape);
+    Plan* pl;
+    if (it == pop->plans.end()) {
+        auto up = std::make_unique<Plan>();
+        pl = up.get();
+        build_plan(pop->ir, shape, pl->hp);
+        const HostPlan& hp = pl->hp;
+        const int64_t T = (int64_t)pop->ir.roots.size();
+        const int warps = shape.threads / 32;
+        CUDA_TRY(pl->code.ensure(hp.code.size()));
+        CUDA_TRY(pl->group_off.ensure(hp.group_off.size()));
+        CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
+        CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
+        CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
+        CUDA_TRY(pl->counter.ensure(1));
+        CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * std::max<int64_t>(T, 1)));
+        pl->h_rmse_n = (size_t)std::max<int64_t>(T, 1);
+        CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins),
+                                 cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(),
+                                 hp.group_order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        // host vectors stay alive with the plan, so the async copies are safe
+        pl->smem = (size_t)(1 + hp.spill_slots) * shape.K * shape.threads * sizeof(float);
+        pop->plans[shape] = std::move(up);
+    } else {
+        pl = it->second.get();
+    }
+    int bps = 0;
+    int rc = occupancy(c, shape.K, pheno, shape.threads, pl->smem, &bps);
+    if (rc) return rc;
+    int64_t slots = (int64_t)bps * std::max(c->sms, 1);
+    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl->hp.n_items, slots));
+    *out = pl;
+    return TGP_OK;
+}
+
+int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, cudaStream_t s) {
+    const HostPlan& hp = pl->hp;
+    EvalParams p{};
+    p.code = pl->code.p;
+    p.group_off = pl->group_off.p;
+    p.item_group = pl->group_order.p;
+    p.n_items = hp.n_items;
+    p.n_tiles = hp.n_tiles;
+    p.warps_per_tile = hp.shape.threads / 32;
+    p.N = d->N();
+    p.W = d->W;
+    p.H = d->H;
+    p.xlo = d->xlo;
+    p.xhi = d->xhi;
+    p.ylo = d->ylo;
+    p.yhi = d->yhi;
+    p.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+    p.partial = pl->partial.p;
+    p.out = out;
+    p.cache = nullptr;
+    p.counter = pl->counter.p;
+    p.spill_slots = hp.spill_slots;
+    p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
+    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
+    const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (timed) {
+        if (c->ev_pending.size() >= 4096) {
+            int rc = drain_events(c);
+            if (rc) return rc;
+        }
+        if (c->ev_free.empty()) {
+            CUDA_TRY(cudaEventCreate(&ev.first));
+            CUDA_TRY(cudaEventCreate(&ev.second));
+        } else {
+            ev = c->ev_free.back();
+            c->ev_free.pop_back();
+        }
+        CUDA_TRY(cudaEventRecord(ev.first, s));
+    }
+    CUDA_TRY(launch_eval(p, hp.shape.K, pheno, pl->grid, hp.shape.threads, pl->smem, s));
+    if (timed) {
+        CUDA_TRY(cudaEventRecord(ev.second, s));
+        c->ev_pending.push_back(ev);
+    }
+    c->stats.launches++;
+    c->stats.code_instrs = (int64_t)hp.ir.size();
+    c->stats.n_groups = hp.shape.n_groups;
+    c->stats.n_items = hp.n_items;
+    c->stats.points_per_thread = hp.shape.K;
+    c->stats.threads_per_block = hp.shape.threads;
+    c->stats.spill_slots = hp.spill_slots;
+    return TGP_OK;
+}
+
+int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out) {
+    Plan* pl = nullptr;
+    int rc = get_plan(c, pop, d->N(), false, s, &pl);
+    if (rc) return rc;
+    rc = launch_plan(c, pl, d, false, nullptr, s);
+    if (rc) return rc;
+    FinalizeParams f{};
+    f.partial = pl->partial.p;
+    f.per_tree = (int64_t)pl->hp.n_tiles * (pl->hp.shape.threads / 32);
+    f.n_trees = (int32_t)pop->ir.roots.size();
+    f.n_points = (double)d->N();
+    f.rmse = rmse_dev ? rmse_dev : pl->rmse.p;
+    CUDA_TRY(launch_finalize(f, s));
+    c->stats.launches++;
+    if (plan_out) *plan_out = pl;
+    return TGP_OK;
+}
+
+template <class M>
+typename M::mapped_type::element_type* find(M& m, int64_t h) {
+    auto it = m.find(h);
+    return it == m.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+int tgp_create(tgp_ctx** out, const tgp_config* cfg) {
+    if (!out) return fail(TGP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<tgp_ctx> c(new (std::nothrow) tgp_ctx());
+    if (!c) return fail(TGP_E_NOMEM, "out of host memory");
+    if (cfg) c->cfg = *cfg;
+    c->device = c->cfg.device;
+    if (c->cfg.flags & TGP_F_HOST_ONLY) {
+        c->host_only = true;
+        c->sms = 152;
+        *out = c.release();
+        return TGP_OK;
+    }
+    int n = 0;
+    CUDA_TRY(cudaGetDeviceCount(&n));
+    if (c->device < 0 || c->device >= n)
+        return fail(TGP_E_INVALID, "device %d does not exist (%d devices)", c->device, n);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    *out = c.release();
+    return TGP_OK;
+}
+
+int tgp_destroy(tgp_ctx* ctx) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!ctx->host_only) {
+            cudaSetDevice(ctx->device);
+            cudaDeviceSynchronize();
+        }
+        ctx->pops.clear();
+        ctx->domains.clear();
+    }
+    delete ctx;
+    return TGP_OK;
+}
+
+const char* tgp_last_error(const tgp_ctx*) { return g_err.c_str(); }
+
+int tgp_load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                    int32_t target_kind, const void* target, tgp_handle* domain_out) {
+    if (!ctx || !domain_out) return fail(TGP_E_INVALID, "ctx / domain_out is NULL");
+    if (W < 1 || H < 1 || (int64_t)W * H > INT32_MAX)
+        return fail(TGP_E_INVALID, "grid %d x %d: need W, H >= 1 and W*H <= 2^31-1", W, H);
+    if (!std::isfinite(xlo) || !std::isfinite(xhi) || !std::isfinite(ylo) || !std::isfinite(yhi))
+        return fail(TGP_E_INVALID, "domain bounds must be finite");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    auto d = std::make_unique<Domain>();
+    d->W = W; d->H = H; d->xlo = xlo; d->xhi = xhi; d->ylo = ylo; d->yhi = yhi;
+    d->kind = target_kind;
+    const int64_t N = d->N();
+    if (target_kind == TGP_TARGET_PAGIE) {
+        if (target) return fail(TGP_E_INVALID, "target must be NULL for the Pagie target");
+    } else if (target_kind == TGP_TARGET_TENSOR) {
+        if (!target) return fail(TGP_E_INVALID, "target tensor is NULL");
+        CUDA_TRY(d->target.ensure((size_t)N));
+        cudaPointerAttributes attr{};
+        cudaError_t e = cudaPointerGetAttributes(&attr, target);
+        if (e != cudaSuccess) cudaGetLastError();
+        bool dev = e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+        CUDA_TRY(cudaMemcpy(d->target.p, target, (size_t)N * sizeof(float),
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    } else if (target_kind == TGP_TARGET_TOKENS) {
+        if (!target) return fail(TGP_E_INVALID, "target tokens are NULL");
+        const tgp_target_tokens* tt = (const tgp_target_tokens*)target;
+        int64_t off[2] = {0, tt->n_ops};
+        Population tp;
+        std::string err;
+        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, tp.ir, err);
+        if (prc) return fail(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
+        CUDA_TRY(d->target.ensure((size_t)N));
+        Plan* pl = nullptr;
+        rc = get_plan(ctx, &tp, N, true, 0, &pl);
+        if (rc) return rc;
+        rc = launch_plan(ctx, pl, d.get(), true, d->target.p, 0);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(0));
+    } else {
+        return fail(TGP_E_INVALID, "unknown target kind %d", target_kind);
+    }
+    int64_t h = ctx->next_handle++;
+    ctx->domains[h] = std::move(d);
+    *domain_out = h;
+    return TGP_OK;
+}
+
+int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->domains.find(domain);
+    if (it == ctx->domains.end()) return fail(TGP_E_INVALID, "unknown domain handle %lld", (long long)domain);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());
+    ctx->domains.erase(it);
+    return TGP_OK;
+}
+
+int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, int64_t n_imm,
+                           const int64_t* tree_off, int32_t n_trees, int32_t order, tgp_handle* pop_out) {
+    if (!ctx || !pop_out) return fail(TGP_E_INVALID, "ctx / pop_out is NULL");
+    auto pop = std::make_unique<Population>();
+    std::string err;
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err);
+    if (rc) return fail(rc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->stats.tree_nodes = pop->ir.tree_nodes;
+    ctx->stats.dag_nodes = (int64_t)pop->ir.dag.size();
+    int64_t internal = 0;
+    for (const DagNode& n : pop->ir.dag.nodes) internal += !is_leaf(n.op);
+    ctx->stats.dag_internal = internal;
+    int64_t h = ctx->next_handle++;
+    ctx->pops[h] = std::move(pop);
+    *pop_out = h;
+    return TGP_OK;
+}
+
+int tgp_release_population(tgp_ctx* ctx, tgp_handle pop) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->pops.find(pop);
+    if (it == ctx->pops.end()) return fail(TGP_E_INVALID, "unknown population handle %lld", (long long)pop);
+    if (!ctx->host_only) {
+        cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+    }
+    ctx->pops.erase(it);
+    return TGP_OK;
+}
+
+int tgp_evaluate(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, float* out_dev) {
+    if (!ctx || !out_dev) return fail(TGP_E_INVALID, "ctx / out_dev is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    if (p->ir.roots.empty()) return TGP_OK;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan* pl = nullptr;
+    rc = get_plan(ctx, p, d->N(), true, s, &pl);
+    if (rc) return rc;
+    return launch_plan(ctx, pl, d, true, out_dev, s);
+}
+
+int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_host,
+                int32_t blocking) {
+    if (!ctx || !rmse_host) return fail(TGP_E_INVALID, "ctx / rmse_host is NULL");
+    std::unique_lock<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    const size_t T = p->ir.roots.size();
+    if (T == 0) return TGP_OK;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    Plan* pl = nullptr;
+    rc = fitness_to_device(ctx, p, d, s, nullptr, &pl);
+    if (rc) return rc;
+    if (blocking) {
+        CUDA_TRY(cudaMemcpyAsync(pl->h_rmse, pl->rmse.p, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+        double* staging = pl->h_rmse;
+        g.unlock();
+        CUDA_TRY(cudaStreamSynchronize(s));
+        std::memcpy(rmse_host, staging, T * sizeof(double));
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(rmse_host, pl->rmse.p, T * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    return TGP_OK;
+}
+
+int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev) {
+    if (!ctx || !rmse_dev) return fail(TGP_E_INVALID, "ctx / rmse_dev is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    if (p->ir.roots.empty()) return TGP_OK;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    return fitness_to_device(ctx, p, d, (cudaStream_t)stream, rmse_dev, nullptr);
+}
+
+int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out) {
+    if (!ctx || !out) return fail(TGP_E_INVALID, "ctx / out is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->ev_pending.empty()) {
+        int rc = drain_events(ctx);
+        if (rc) return rc;
+    }
+    *out = ctx->stats;
+    return TGP_OK;
+}
+
+int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points, int32_t* ins_out, int64_t cap, int64_t* n_ins,
+                   int64_t* group_off_out, int64_t cap_groups, int32_t* n_groups) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    if (n_points < 1) return fail(TGP_E_INVALID, "n_points must be >= 1");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    if (!p) return fail(TGP_E_INVALID, "unknown population handle");
+    HostPlan hp;
+    build_plan(p->ir, choose_shape(ctx, p->ir, n_points), hp);
+    if (n_ins) *n_ins = (int64_t)hp.ir.size();
+    if (n_groups) *n_groups = hp.shape.n_groups;
+    if (ins_out) {
+        for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)hp.ir.size()); ++i) {
+            const IrIns& in = hp.ir[i];
+            int32_t* o = ins_out + 6 * i;
+            o[0] = in.form; o[1] = in.fn; o[2] = in.o1; o[3] = in.o2; o[4] = in.aux;
+            std::memcpy(&o[5], &in.imm, 4);
+        }
+    }
+    if (group_off_out) {
+        for (int64_t i = 0; i < std::min<int64_t>(cap_groups, (int64_t)hp.group_off.size()); ++i)
+            group_off_out[i] = hp.group_off[i];
+    }
+    return TGP_OK;
+}
+
+int tgp_debug_layout(int32_t* out, int32_t n) {
+    if (!out || n < 2) return fail(TGP_E_INVALID, "need an array of at least 2");
+    out[0] = kNReg;
+    out[1] = F_NFORMS;
+    return TGP_OK;
+}
+
+int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
+    if (!ctx || !cost_out) return fail(TGP_E_INVALID, "ctx / cost_out is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    const int threads = 256, grid = ctx->sms * 8, iters = 256;
+    DevBuf<float> in, out;
+    CUDA_TRY(in.ensure(256));
+    CUDA_TRY(out.ensure((size_t)grid * threads));
+    std::vector<float> h(256);
+    for (int i = 0; i < 256; ++i) h[i] = 1.0f + (float)i / 256.0f;   // values in [1, 2)
+    CUDA_TRY(cudaMemcpy(in.p, h.data(), 256 * sizeof(float), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double ms[6];
+    for (int opk = 0; opk < 6; ++opk) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {   // first run warms up
+            CUDA_TRY(cudaEventRecord(e0, 0));
+            CUDA_TRY(launch_calib(opk, in.p, out.p, iters, grid, threads, 0));
+            CUDA_TRY(cudaEventRecord(e1, 0));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0;
+            CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) best = std::min(best, t);
+        }
+        ms[opk] = best;
+        ctx->stats.launches += 4;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double add = ms[0];
+    for (int i = 0; i < TGP_N_OPS; ++i) cost_out[i] = 0.0;
+    cost_out[TGP_OP_ADD] = 1.0;
+    cost_out[TGP_OP_SUB] = 1.0;
+    cost_out[TGP_OP_MUL] = ms[4] / add;
+    cost_out[TGP_OP_DIV] = ms[1] / add;
+    cost_out[TGP_OP_SIN] = ms[2] / add;
+    cost_out[TGP_OP_COS] = ms[3] / add;
+    cost_out[TGP_OP_MIN] = ms[5] / add;
+    cost_out[TGP_OP_MAX] = ms[5] / add;
+    // neg and abs fold into their consumer as operand modifiers: cost 0
+    return TGP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,548 @@
+// compiler.cpp -- token decode, hash-consing and bytecode generation.
+//
+// Hot-path steps on the host (all O(tokens)):
+//   1. decode + validate each tree of the token stream (prefix or postfix);
+//   2. hash-cons every node into the population DAG, so structurally equal
+//      subtrees of any tree share one node (Handley's DAG; Sec. 2 and the
+//      graph-mode DAG of Sec. 3.1 of TensorGP);
+//   3. split the trees into groups (one group = one instruction stream that a
+//      CTA runs over a tile of points), order each tree's evaluation
+//      Sethi-Ullman style, allocate register slots by liveness, and emit
+//      bytecode.  A DAG node used more than once inside a group is evaluated
+//      once per point and kept in a register slot (or, when registers run
+//      out, a shared-memory slot) until its last use.
+#include "compiler.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+namespace tgp {
+
+int arity(int op) {
+    switch (op) {
+    case T_X: case T_Y: case T_CONST: return 0;
+    case T_SIN: case T_COS: case T_NEG: case T_ABS: return 1;
+    case T_ADD: case T_SUB: case T_MUL: case T_DIV: case T_MIN: case T_MAX: return 2;
+    default: return -1;
+    }
+}
+
+float op_cost(int op) {
+    switch (op) {
+    case T_X: case T_Y: case T_CONST: return 0.f;
+    case T_DIV: return 8.f;
+    case T_SIN: case T_COS: return 16.f;
+    default: return 1.f;
+    }
+}
+
+// ------------------------------------------------------------------ DAG
+
+static inline uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+static inline uint64_t key_hash(int op, int32_t k0, int32_t k1, uint32_t imm) {
+    uint64_t a = ((uint64_t)(uint32_t)k0 << 32) | (uint32_t)k1;
+    uint64_t b = ((uint64_t)(uint32_t)op << 32) | imm;
+    return mix64(a ^ mix64(b));
+}
+
+void Dag::rehash(size_t cap) {
+    table_.assign(cap, -1);
+    mask_ = cap - 1;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        const DagNode& n = nodes[i];
+        size_t h = key_hash(n.op, n.kid[0], n.kid[1], n.imm) & mask_;
+        while (table_[h] >= 0) h = (h + 1) & mask_;
+        table_[h] = (int32_t)i;
+    }
+}
+
+int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm) {
+    if (table_.empty()) rehash(1024);
+    size_t h = key_hash(op, k0, k1, imm) & mask_;
+    while (table_[h] >= 0) {
+        const DagNode& n = nodes[table_[h]];
+        if (n.op == op && n.kid[0] == k0 && n.kid[1] == k1 && n.imm == imm) return table_[h];
+        h = (h + 1) & mask_;
+    }
+    DagNode n;
+    n.op = op;
+    n.kid[0] = k0;
+    n.kid[1] = k1;
+    n.imm = imm;
+    int ar = arity(op);
+    if (ar == 0) {
+        n.su = 0;
+        n.depth = 0;
+        n.cost = 0.f;
+    } else if (ar == 1) {
+        const DagNode& c = nodes[k0];
+        n.su = c.su;
+        n.depth = c.depth + 1;
+        n.cost = op_cost(op) + c.cost;
+    } else {
+        const DagNode& l = nodes[k0];
+        const DagNode& r = nodes[k1];
+        bool ll = is_leaf(l.op), rl = is_leaf(r.op);
+        if (ll && rl) n.su = 0;
+        else if (ll) n.su = r.su;
+        else if (rl) n.su = l.su;
+        else n.su = l.su == r.su ? l.su + 1 : std::max(l.su, r.su);
+        n.depth = std::max(l.depth, r.depth) + 1;
+        n.cost = op_cost(op) + l.cost + r.cost;
+    }
+    int32_t id = (int32_t)nodes.size();
+    nodes.push_back(n);
+    table_[h] = id;
+    if (++used_ * 2 > table_.size()) rehash(table_.size() * 2);
+    return id;
+}
+
+// ------------------------------------------------------------------ parse
+
+static void fmt(std::string& err, const char* f, long long a, long long b = 0, long long c = 0) {
+    char buf[256];
+    snprintf(buf, sizeof buf, f, a, b, c);
+    err = buf;
+}
+
+int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err) {
+    if (n_trees < 0 || n_trees > (1 << 24)) { fmt(err, "n_trees %lld out of range", n_trees); return -1; }
+    if (order != 0 && order != 1) { fmt(err, "order %lld is neither prefix (0) nor postfix (1)", order); return -1; }
+    if (n_imm < 0) { fmt(err, "n_imm %lld is negative", n_imm); return -1; }
+    if (n_trees > 0 && (!ops || !tree_off)) { err = "ops / tree_off must not be NULL"; return -1; }
+    if (n_imm > 0 && !imm) { err = "imm must not be NULL when n_imm > 0"; return -1; }
+    out = PopIR();
+    out.roots.resize(n_trees);
+    out.tree_size.resize(n_trees);
+    out.tree_cost.resize(n_trees);
+    if (n_trees > 0 && tree_off[0] != 0) { fmt(err, "tree_off[0] = %lld, must be 0", tree_off[0]); return -2; }
+    std::vector<int32_t> stack;
+    int64_t imm_pos = 0;
+    for (int32_t t = 0; t < n_trees; ++t) {
+        int64_t b = tree_off[t], e = tree_off[t + 1];
+        int64_t n = e - b;
+        if (n <= 0) { fmt(err, "tree %lld is empty (tree_off not increasing)", t); return -2; }
+        if (n > (1 << 24)) { fmt(err, "tree %lld has %lld tokens, limit 2^24", t, n); return -2; }
+        // constants of this tree, for the prefix reverse scan
+        int64_t nconst = 0;
+        for (int64_t i = b; i < e; ++i) {
+            int op = ops[i];
+            if (arity(op) < 0) { fmt(err, "tree %lld token %lld: unknown opcode %lld", t, i - b, op); return -2; }
+            nconst += op == T_CONST;
+        }
+        if (imm_pos + nconst > n_imm) {
+            fmt(err, "tree %lld needs constants beyond n_imm = %lld", t, n_imm);
+            return -2;
+        }
+        for (int64_t i = 0; i < nconst; ++i) {
+            if (!std::isfinite(imm[imm_pos + i])) {
+                fmt(err, "tree %lld: constant %lld is not finite", t, imm_pos + i);
+                return -2;
+            }
+        }
+        stack.clear();
+        if (order == 1) {   // postfix: operands precede their operator
+            int64_t ip = imm_pos;
+            for (int64_t i = b; i < e; ++i) {
+                int op = ops[i], ar = arity(op);
+                if ((int64_t)stack.size() < ar) {
+                    fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
+                    return -2;
+                }
+                int32_t k0 = -1, k1 = -1;
+                uint32_t bits = 0;
+                if (ar == 2) { k1 = stack.back(); stack.pop_back(); k0 = stack.back(); stack.pop_back(); }
+                else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
+                if (op == T_CONST) { float v = imm[ip++]; std::memcpy(&bits, &v, 4); }
+                stack.push_back(out.dag.intern(op, k0, k1, bits));
+            }
+        } else {            // prefix: scan backwards, first popped = first operand
+            int64_t ip = imm_pos + nconst;
+            for (int64_t i = e - 1; i >= b; --i) {
+                int op = ops[i], ar = arity(op);
+                if ((int64_t)stack.size() < ar) {
+                    fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
+                    return -2;
+                }
+                int32_t k0 = -1, k1 = -1;
+                uint32_t bits = 0;
+                if (ar == 2) { k0 = stack.back(); stack.pop_back(); k1 = stack.back(); stack.pop_back(); }
+                else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
+                if (op == T_CONST) { float v = imm[--ip]; std::memcpy(&bits, &v, 4); }
+                stack.push_back(out.dag.intern(op, k0, k1, bits));
+            }
+        }
+        if (stack.size() != 1) {
+            fmt(err, "tree %lld leaves %lld values (must form exactly one expression)", t, (long long)stack.size());
+            return -2;
+        }
+        int32_t root = stack[0];
+        if (out.dag.nodes[root].depth > 1024) {
+            fmt(err, "tree %lld has depth %lld, limit 1024", t, out.dag.nodes[root].depth);
+            return -2;
+        }
+        imm_pos += nconst;
+        out.roots[t] = root;
+        out.tree_size[t] = (int32_t)n;
+        out.tree_cost[t] = out.dag.nodes[root].cost;
+        out.tree_nodes += n;
+    }
+    if (imm_pos != n_imm) {
+        fmt(err, "stream has %lld CONST tokens but n_imm = %lld", imm_pos, n_imm);
+        return -2;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ codegen
+
+namespace {
+
+class GroupGen {
+public:
+    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup)
+        : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
+          dedup_(dedup) {}
+
+    int spill_high = 0;
+
+    void run(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots) {
+        count_uses(trees, roots);
+        for (int32_t t : trees) {
+            int32_t r = roots[t];
+            to_acc(r);
+            use(r);
+            emit(F_ROOT, 0, 0, 0, t, 0);
+        }
+        emit(F_END, 0, 0, 0, 0, 0);
+        for (int32_t n : touched_) { uses_[n] = 0; where_[n] = -1; keep_[n] = 0; }
+        touched_.clear();
+        for (bool& b : reg_busy_) b = false;
+        smem_busy_.clear();
+    }
+
+private:
+    // A shared node is kept (evaluated once, held until its last use) when
+    // its subtree costs at least this much per point; cheaper shared nodes
+    // are re-evaluated at each use, which needs no slot.
+    static constexpr float kKeepMinCost = 2.f;
+
+    const Dag& d_;
+    std::vector<IrIns>& out_;
+    std::vector<int32_t> uses_;    // evaluations of the node still to be consumed
+    std::vector<int32_t> where_;   // -1, register slot j, or kNReg + shared slot s
+    std::vector<uint8_t> keep_;    // evaluated once and held
+    std::vector<int32_t> touched_;
+    bool dedup_;
+    bool reg_busy_[kNReg] = {};
+    std::vector<bool> smem_busy_;
+    std::vector<int32_t> dfs_;
+
+    const DagNode& N(int32_t n) const { return d_.nodes[n]; }
+
+    void emit(int form, int fn, int o1, int o2, int aux, uint32_t imm) {
+        IrIns in;
+        in.form = form; in.fn = fn; in.o1 = o1; in.o2 = o2; in.aux = aux; in.imm = imm;
+        out_.push_back(in);
+    }
+
+    // Static keep/expand decision and use counts.  A node that is kept is
+    // evaluated once, so each operand edge below it is consumed once; a node
+    // that is expanded is evaluated at every one of its uses, so its operand
+    // edges are consumed that many times.  Node ids are a topological order
+    // (operands are interned before their parent), so a pass over the
+    // group's nodes in descending id order sees every parent first.
+    void count_uses(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots) {
+        for (int32_t t : trees) {
+            int32_t r = roots[t];
+            if (is_leaf(N(r).op)) continue;
+            if (uses_[r]++ > 0) continue;
+            touched_.push_back(r);
+            dfs_.assign(1, r);
+            while (!dfs_.empty()) {
+                int32_t n = dfs_.back();
+                dfs_.pop_back();
+                for (int c = 0; c < 2; ++c) {
+                    int32_t k = N(n).kid[c];
+                    if (k < 0 || is_leaf(N(k).op) || where_[k] == -2) continue;
+                    where_[k] = -2;   // visited mark, reset below
+                    touched_.push_back(k);
+                    dfs_.push_back(k);
+                }
+            }
+        }
+        std::sort(touched_.begin(), touched_.end(), [](int32_t a, int32_t b) { return a > b; });
+        touched_.erase(std::unique(touched_.begin(), touched_.end()), touched_.end());
+        for (int32_t n : touched_) where_[n] = -1;
+        // uses_ holds the root counts so far; push evaluations down
+        for (int32_t n : touched_) {
+            int32_t e = uses_[n];
+            keep_[n] = dedup_ && e >= 2 && N(n).cost >= kKeepMinCost;
+            int32_t f = keep_[n] ? 1 : e;
+            for (int c = 0; c < 2; ++c) {
+                int32_t k = N(n).kid[c];
+                if (k >= 0 && !is_leaf(N(k).op)) uses_[k] += f;
+            }
+        }
+    }
+
+    // operand index of a leaf (and its immediate)
+    int leaf_opnd(int32_t n, uint32_t* imm) const {
+        const DagNode& x = N(n);
+        if (x.op == T_X) return kOpX;
+        if (x.op == T_Y) return kOpY;
+        *imm = x.imm;
+        return kOpC;
+    }
+
+    // operand available without any code (leaf or register-held node), else -1
+    int free_opnd(int32_t n, uint32_t* imm) const {
+        if (is_leaf(N(n).op)) return leaf_opnd(n, imm);
+        int w = where_[n];
+        if (w >= 0 && w < kNReg) return kOpR0 + w;
+        return -1;
+    }
+
+    int alloc_reg() {
+        for (int j = 0; j < kNReg; ++j)
+            if (!reg_busy_[j]) { reg_busy_[j] = true; return j; }
+        return -1;
+    }
+    int alloc_smem() {
+        for (size_t s = 0; s < smem_busy_.size(); ++s)
+            if (!smem_busy_[s]) { smem_busy_[s] = true; return (int)s; }
+        smem_busy_.push_back(true);
+        spill_high = std::max(spill_high, (int)smem_busy_.size());
+        return (int)smem_busy_.size() - 1;
+    }
+    void free_loc(int w) {
+        if (w < 0) return;
+        if (w < kNReg) reg_busy_[w] = false;
+        else smem_busy_[w - kNReg] = false;
+    }
+
+    // consumes one use of n; frees its slot after the last one
+    void use(int32_t n) {
+        if (is_leaf(N(n).op)) return;
+        if (--uses_[n] == 0 && where_[n] >= 0) {
+            free_loc(where_[n]);
+            where_[n] = -1;
+        }
+    }
+
+    // Leaves the value of n in A (no use is consumed here).
+    void to_acc(int32_t n) {
+        uint32_t imm = 0;
+        if (is_leaf(N(n).op)) {
+            int o = leaf_opnd(n, &imm);
+            emit(F_LD, 0, o, 0, 0, imm);
+            return;
+        }
+        int w = where_[n];
+        if (w >= 0 && w < kNReg) { emit(F_LD, 0, kOpR0 + w, 0, 0, 0); return; }
+        if (w >= kNReg) {
+            emit(F_FILL, 0, 0, 0, w - kNReg, 0);
+            emit(F_LD, 0, kOpF, 0, 0, 0);
+            return;
+        }
+        compute(n);
+        // a kept node is held for the uses that remain after the current one
+        if (keep_[n] && uses_[n] > 1) {
+            int j = alloc_reg();
+            if (j >= 0) {
+                emit(F_ST, 0, kOpR0 + j, 0, 0, 0);
+                where_[n] = j;
+            } else {
+                int s = alloc_smem();
+                emit(F_SPILL, 0, 0, 0, s, 0);
+                where_[n] = kNReg + s;
+            }
+        }
+    }
+
+    static bool commutative(int fn) { return fn == T_ADD || fn == T_MUL; }
+
+    // A = fn(v, A) where v is operand o
+    void emit_rev(int fn, int o, uint32_t imm) {
+        if (commutative(fn)) emit(F_AO, fn, o, 0, 0, imm);
+        else emit(F_OA, fn, o, 0, 0, imm);
+    }
+
+    // Computes internal node n (not held anywhere) into A.
+    void compute(int32_t n) {
+        const DagNode& x = N(n);
+        int fn = x.op;
+        uint32_t imm = 0;
+        if (arity(fn) == 1) {
+            int32_t c = x.kid[0];
+            if (is_leaf(N(c).op)) {
+                int o = leaf_opnd(c, &imm);
+                emit(F_UT, fn, o, 0, 0, imm);
+            } else {
+                to_acc(c);
+                use(c);
+                emit(F_UA, fn, 0, 0, 0, 0);
+            }
+            return;
+        }
+        int32_t l = x.kid[0], r = x.kid[1];
+        uint32_t il = 0, ir = 0;
+        int ol = free_opnd(l, &il), orr = free_opnd(r, &ir);
+        if (ol >= 0 && orr >= 0) {
+            bool ll = is_leaf(N(l).op), rl = is_leaf(N(r).op);
+            if (ll && rl && !(ol == kOpC && orr == kOpC)) {
+                emit(F_TT, fn, ol, orr, 0, ol == kOpC ? il : ir);
+            } else {
+                emit(F_LD, 0, ol, 0, 0, il);
+                emit(F_AO, fn, orr, 0, 0, ir);
+            }
+            use(l);
+            use(r);
+            return;
+        }
+        if (ol >= 0) {            // right needs code
+            to_acc(r);
+            emit_rev(fn, ol, il);
+            use(r);
+            use(l);
+            return;
+        }
+        if (orr >= 0) {           // left needs code
+            to_acc(l);
+            emit(F_AO, fn, orr, 0, 0, ir);
+            use(l);
+            use(r);
+            return;
+        }
+        // both operands need code: the one needing more slots goes first
+        bool left_first = N(l).su >= N(r).su;
+        int32_t first = left_first ? l : r, second = left_first ? r : l;
+        to_acc(first);
+        uint32_t is = 0;
+        int os = free_opnd(second, &is);
+        if (os >= 0) {            // became available while computing `first`
+            if (left_first) emit(F_AO, fn, os, 0, 0, is);
+            else emit_rev(fn, os, is);
+            use(first);
+            use(second);
+            return;
+        }
+        // park `first` while `second` is computed
+        int temp = -1;
+        int w = where_[first];
+        if (w < 0) {
+            int j = alloc_reg();
+            if (j >= 0) { emit(F_ST, 0, kOpR0 + j, 0, 0, 0); temp = j; }
+            else { int s = alloc_smem(); emit(F_SPILL, 0, 0, 0, s, 0); temp = kNReg + s; }
+            w = temp;
+        }
+        to_acc(second);
+        int of;
+        if (w < kNReg) {
+            of = kOpR0 + w;
+        } else {
+            emit(F_FILL, 0, 0, 0, w - kNReg, 0);
+            of = kOpF;
+        }
+        if (left_first) emit_rev(fn, of, 0);      // A = fn(first, A)
+        else emit(F_AO, fn, of, 0, 0, 0);         // A = fn(A, first)
+        if (temp >= 0) free_loc(temp);
+        use(first);
+        use(second);
+    }
+};
+
+}  // namespace
+
+Ins encode(const IrIns& in) {
+    uint32_t opc = 0, y = 0;
+    switch (in.form) {
+    case F_END: opc = OPC_END; break;
+    case F_AO: opc = OPC_AO + bin_index(in.fn) * kNOpnd + in.o1; y = in.imm; break;
+    case F_OA: opc = OPC_OA + ord_index(in.fn) * kNOpnd + in.o1; y = in.imm; break;
+    case F_TT: opc = OPC_TT + bin_index(in.fn) * 9 + in.o1 * 3 + in.o2; y = in.imm; break;
+    case F_UA: opc = OPC_UA + un_index(in.fn); break;
+    case F_UT: opc = OPC_UT + un_index(in.fn) * 3 + in.o1; y = in.imm; break;
+    case F_LD: opc = OPC_LD + in.o1; y = in.imm; break;
+    case F_ST: opc = OPC_ST + (in.o1 - kOpR0); break;
+    case F_SPILL: opc = OPC_SPILL; y = (uint32_t)in.aux; break;
+    case F_FILL: opc = OPC_FILL; y = (uint32_t)in.aux; break;
+    case F_ROOT: opc = OPC_ROOT; y = (uint32_t)in.aux; break;
+    case F_CST: opc = OPC_CST; y = (uint32_t)in.aux; break;
+    case F_CLD: opc = OPC_CLD; y = (uint32_t)in.aux; break;
+    default: opc = OPC_END; break;
+    }
+    Ins e;
+    e.x = opc;
+    e.y = y;
+    return e;
+}
+
+PlanShape default_shape(const PopIR& pop, int64_t N, int sms) {
+    PlanShape s;
+    s.N = N;
+    s.threads = 128;
+    s.K = N >= (1 << 18) ? 8 : N >= (1 << 14) ? 4 : N >= (1 << 12) ? 2 : 1;
+    int64_t tile = (int64_t)s.K * s.threads;
+    int64_t n_tiles = (N + tile - 1) / tile;
+    int64_t slots = (int64_t)std::max(sms, 1) * 4;
+    int64_t T = (int64_t)pop.roots.size();
+    int64_t g = (4 * slots + n_tiles - 1) / n_tiles;
+    s.n_groups = (int)std::max<int64_t>(1, std::min(g, std::max<int64_t>(T, 1)));
+    return s;
+}
+
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
+    plan = HostPlan();
+    plan.shape = shape;
+    const int64_t T = (int64_t)pop.roots.size();
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(shape.n_groups, std::max<int64_t>(T, 1)));
+    plan.shape.n_groups = G;
+    int64_t tile = (int64_t)shape.K * shape.threads;
+    plan.n_tiles = (int)((shape.N + tile - 1) / tile);
+
+    // LPT: heaviest tree first onto the lightest group
+    std::vector<int32_t> order(T);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return pop.tree_cost[a] > pop.tree_cost[b]; });
+    std::vector<std::vector<int32_t>> groups(G);
+    plan.group_cost.assign(G, 0.0);
+    for (int32_t t : order) {
+        int best = 0;
+        for (int g = 1; g < G; ++g)
+            if (plan.group_cost[g] < plan.group_cost[best]) best = g;
+        groups[best].push_back(t);
+        plan.group_cost[best] += pop.tree_cost[t] + 1.0;
+    }
+    // trees of a group in their population order
+    for (auto& g : groups) std::sort(g.begin(), g.end());
+
+    GroupGen gen(pop.dag, plan.ir, shape.dedup);
+    plan.group_off.push_back(0);
+    for (int g = 0; g < G; ++g) {
+        gen.run(groups[g], pop.roots);
+        plan.group_off.push_back((int64_t)plan.ir.size());
+    }
+    plan.spill_slots = gen.spill_high;
+    plan.group_order.resize(G);
+    std::iota(plan.group_order.begin(), plan.group_order.end(), 0);
+    std::stable_sort(plan.group_order.begin(), plan.group_order.end(),
+                     [&](int32_t a, int32_t b) { return plan.group_cost[a] > plan.group_cost[b]; });
+    plan.n_items = (int64_t)G * plan.n_tiles;
+    plan.code.reserve(plan.ir.size() + 1);
+    for (const IrIns& in : plan.ir) plan.code.push_back(encode(in));
+    plan.code.push_back(encode(IrIns{F_END, 0, 0, 0, 0, 0}));
+}
+
+}  // namespace tgp

@@ -1,0 +1,90 @@
+// compiler.h -- host side of the hot path: token decode and validation,
+// hash-consing into the population DAG, and bytecode generation.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tgp_ir.h"
+
+namespace tgp {
+
+// One unique node of the population DAG.  Identity is structural: the key
+// (op, kid0, kid1, imm bits) *is* the node, so two equal subtrees always map
+// to the same id (Handley's DAG, Sec. 2 of TensorGP).
+struct DagNode {
+    int32_t op;
+    int32_t kid[2];     // -1 when absent
+    uint32_t imm;       // binary32 bits of a CONST
+    int32_t su;         // register slots needed to evaluate it (Sethi-Ullman)
+    int32_t depth;      // root alone = 0
+    float cost;         // issue cost of evaluating it as a tree, per point
+};
+
+class Dag {
+public:
+    std::vector<DagNode> nodes;
+    int32_t intern(int op, int32_t k0, int32_t k1, uint32_t imm);
+    size_t size() const { return nodes.size(); }
+
+private:
+    std::vector<int32_t> table_;   // open addressing, -1 = empty
+    size_t mask_ = 0;
+    size_t used_ = 0;
+    void rehash(size_t cap);
+};
+
+inline bool is_leaf(int op) { return op == T_X || op == T_Y || op == T_CONST; }
+int arity(int op);       // -1 for an unknown opcode
+float op_cost(int op);   // planning estimate of the issue cost per point
+
+struct PopIR {
+    Dag dag;
+    std::vector<int32_t> roots;       // DAG id of each tree
+    std::vector<int32_t> tree_size;   // tokens per tree
+    std::vector<float> tree_cost;     // cost of each tree evaluated as a tree
+    int64_t tree_nodes = 0;
+};
+
+// Validates and hash-conses a token population.  Returns 0, or -2 (tokens) /
+// -1 (argument) with a message in err.
+int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err);
+
+// Shape of one launch plan.
+struct PlanShape {
+    int64_t N = 0;       // grid points
+    int K = 8;           // points per thread
+    int threads = 128;   // threads per CTA
+    int n_groups = 1;    // tree groups
+    bool dedup = true;   // hold shared subtrees (false: recompute at each use)
+    bool operator<(const PlanShape& o) const {
+        if (dedup != o.dedup) return dedup < o.dedup;
+        if (N != o.N) return N < o.N;
+        if (K != o.K) return K < o.K;
+        if (threads != o.threads) return threads < o.threads;
+        return n_groups < o.n_groups;
+    }
+};
+
+struct HostPlan {
+    PlanShape shape;
+    std::vector<IrIns> ir;              // decoded, all groups back to back
+    std::vector<Ins> code;              // encoded, plus one trailing END
+    std::vector<int64_t> group_off;     // [n_groups + 1]
+    std::vector<int32_t> group_order;   // groups by descending estimated cost
+    std::vector<double> group_cost;
+    int spill_slots = 0;
+    int n_tiles = 0;
+    int64_t n_items = 0;
+};
+
+// Default shape for a grid of N points on a device with `sms` SMs.
+PlanShape default_shape(const PopIR& pop, int64_t N, int sms);
+
+// Partitions the trees into shape.n_groups groups and emits their bytecode.
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan);
+
+Ins encode(const IrIns& in);
+
+}  // namespace tgp

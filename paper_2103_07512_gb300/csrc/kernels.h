@@ -1,0 +1,21 @@
+// kernels.h -- host-side launchers of the device kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tgp_ir.h"
+
+namespace tgp {
+
+// Fused interpreter: K in {1, 2, 4, 8}; pheno selects phenotype stores
+// instead of fitness partials at tree roots.  threads <= 128.
+cudaError_t launch_eval(const EvalParams& p, int K, bool pheno, int grid, int threads, size_t smem,
+                        cudaStream_t s);
+cudaError_t eval_occupancy(int K, bool pheno, int threads, size_t smem, int* blocks_per_sm);
+
+// Per-tree binary64 reduction of the fitness partials and sqrt(sum / N).
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
+
+// Straight-line chains of one operator (0 add, 1 div, 2 sin, 3 cos, 4 mul, 5 min).
+cudaError_t launch_calib(int opk, const float* in, float* out, int iters, int grid, int threads, cudaStream_t s);
+
+}  // namespace tgp

@@ -1,0 +1,357 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Element tolerance |gpu - ref| <= 1e-4 (1 + |ref|), fitness 1e-5 relative, with
+near-singular divisions excluded and ill-conditioned elements checked against
+the oracle's FP32-faithful mode (tests/parity.py states the rules).  Sizes span
+several tiles and ragged tails; the full-size workloads are checked on sampled
+points and, for fitness, against the oracle run in a spawn process pool.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_07512_gb300 as tgp
+from paper_2103_07512_gb300 import inputs as I
+from parity import assert_elements, assert_fitness, classify, oracle_fitness_chunk
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+_POOL = None
+
+
+def oracle_pool():
+    global _POOL
+    if _POOL is None:
+        _POOL = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    return _POOL
+
+
+def subset(tok, idx):
+    trees = I.from_tokens(tok)
+    return I.to_tokens([trees[i] for i in idx], tok.order)
+
+
+def oracle_fitness_parallel(tok, g, target=None, chunks=32):
+    trees = I.from_tokens(tok)
+    parts = np.array_split(np.arange(len(trees)), min(chunks, len(trees)))
+    jobs = []
+    for p in parts:
+        t = I.to_tokens([trees[i] for i in p], tok.order)
+        jobs.append((t.ops, t.imm, t.tree_off, t.order, g, target))
+    res = oracle_pool().map(oracle_fitness_chunk, jobs)
+    return tuple(np.concatenate([r[k] for r in res]) for k in range(3))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tgp.Context()
+    yield c
+    c.close()
+
+
+def load(ctx, g, **kw):
+    return ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, **kw)
+
+
+def phenotype(ctx, tok, g, pop=None, dom=None):
+    dom = load(ctx, g) if dom is None else dom
+    pop = ctx.compile_tokens(tok) if pop is None else pop
+    out = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
+    ctx.evaluate(pop, dom, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def full_check(ctx, tok, g, context=""):
+    """Every element and every fitness against the oracle."""
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    got = phenotype(ctx, tok, g, pop, dom)
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                   g.xlo, g.xhi, g.ylo, g.yhi)
+    c = assert_elements(got, v64, v32, fl, context=context)
+    fit = ctx.fitness(pop, dom, tok.n_trees)
+    r64, r32, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                 g.xlo, g.xhi, g.ylo, g.yhi)
+    flagged = (c["excluded"] | c["ill"]).any(axis=1)
+    assert_fitness(fit, r64, r32, flagged, g.N, context=context)
+    ctx.release_population(pop)
+    ctx.release_domain(dom)
+    return got, fit, c
+
+
+# ---------------------------------------------------------------- small configs
+
+@pytest.mark.parametrize("K,threads", [(0, 0), (1, 128), (2, 64), (4, 128), (8, 128), (8, 32)])
+def test_small_population_every_element(K, threads):
+    """50 RHH trees (depth 2-6) on the 64x64 grid, Pagie target."""
+    tok, g = I.small_population(seed=0)
+    with tgp.Context(points_per_thread=K, threads_per_block=threads) as c:
+        full_check(c, tok, g, f"K={K} threads={threads}")
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (2, 3), (7, 5), (33, 17), (1, 100), (100, 1), (129, 65)])
+@pytest.mark.parametrize("K", [1, 8])
+def test_odd_grids_and_ragged_tails(W, H, K):
+    tok, _ = I.small_population(seed=5)
+    with tgp.Context(points_per_thread=K, threads_per_block=64) as c:
+        full_check(c, tok, I.Grid(W, H), f"{W}x{H} K={K}")
+
+
+def test_other_domain_bounds():
+    tok, _ = I.small_population(seed=6)
+    with tgp.Context() as c:
+        full_check(c, tok, I.Grid(40, 24, -1.0, 1.0, 0.5, 3.0), "bounds")
+
+
+def test_trig_free_population_is_bitwise_fp32_faithful(ctx):
+    rng = np.random.default_rng(21)
+    funcs = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.ABS, I.MIN, I.MAX)
+    tok = I.to_tokens(I.ramped_half_and_half(60, 2, 8, rng, funcs))
+    g = I.Grid(37, 29)
+    got = phenotype(ctx, tok, g)
+    _, v32, _ = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    same = (got == v32) | (np.isnan(got) & np.isnan(v32))
+    assert same.all(), f"{(~same).sum()} elements differ from the correctly rounded binary32 value"
+
+
+def test_deep_trees_use_shared_memory_spills(ctx):
+    rng = np.random.default_rng(7)
+    trees = [I._full(rng, 10, (I.ADD, I.SUB, I.MUL, I.MIN, I.MAX, I.DIV, I.SIN)) for _ in range(4)]
+    tok = I.to_tokens(trees)
+    full_check(ctx, tok, I.Grid(31, 9), "deep")
+    assert ctx.stats()["spill_slots"] > 0
+
+
+def test_closed_forms_on_device(ctx):
+    g = I.Grid(64, 64)
+    exprs = ["add(x, y)", "mult(x, x)", "sin(0.5)", "cos(1.0)", "div(x, sub(y, y))",
+             "neg(neg(x))", "abs(neg(x))", "x", "0.25"]
+    tok = I.to_tokens([I.parse_string(e) for e in exprs])
+    got = phenotype(ctx, tok, g)
+    xs = np.array([oracle.grid_point(g.W, g.H, -5, 5, -5, 5, p) for p in range(g.N)], np.float32)
+    X, Y = xs[:, 0], xs[:, 1]
+    assert np.array_equal(got[0], X + Y)
+    assert np.array_equal(got[1], X * X)
+    assert np.all(got[2] == 1.0) and np.all(got[3] == -1.0)
+    assert np.all(got[4] == 0.0)
+    assert np.array_equal(got[5], X) and np.array_equal(got[6], np.abs(X))
+    assert np.array_equal(got[7], X) and np.all(got[8] == np.float32(0.25))
+
+
+def test_pagie_tree_fits_pagie_target(ctx):
+    e = ("add(div(mult(mult(x, x), mult(x, x)), add(1.0, mult(mult(x, x), mult(x, x)))),"
+         " div(mult(mult(y, y), mult(y, y)), add(1.0, mult(mult(y, y), mult(y, y)))))")
+    tok = I.to_tokens([I.parse_string(e)])
+    g = I.Grid(256, 256)
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    fit = ctx.fitness(pop, dom, 1)
+    assert fit[0] < 1e-6   # binary32 round-off only
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_cached_equals_uncached_bitwise():
+    tok, g, _ = I.batched_uneven(seed=12, n_trees=300)
+    g = I.Grid(96, 80)
+    with tgp.Context() as a, tgp.Context(dedup=False) as b:
+        pa = phenotype(a, tok, g)
+        pb = phenotype(b, tok, g)
+        assert np.array_equal(pa.view(np.int32), pb.view(np.int32))
+        fa = a.fitness(a.compile_tokens(tok), load(a, g), tok.n_trees)
+        fb = b.fitness(b.compile_tokens(tok), load(b, g), tok.n_trees)
+        assert np.array_equal(fa, fb)
+        assert a.stats()["code_instrs"] < b.stats()["code_instrs"]
+
+
+def test_prefix_equals_postfix(ctx):
+    tok, g = I.small_population(seed=9)
+    post = I.convert_order(tok, I.POSTFIX)
+    a = phenotype(ctx, tok, g)
+    b = phenotype(ctx, post, g)
+    assert np.array_equal(a.view(np.int32), b.view(np.int32))
+
+
+def test_duplicated_and_permuted_trees(ctx):
+    tok, g = I.small_population(seed=3)
+    trees = I.from_tokens(tok)
+    perm = list(reversed(trees)) + trees[:7]
+    t2 = I.to_tokens(perm)
+    dom = load(ctx, g)
+    f1 = ctx.fitness(ctx.compile_tokens(tok), dom, tok.n_trees)
+    f2 = ctx.fitness(ctx.compile_tokens(t2), dom, t2.n_trees)
+    T = tok.n_trees
+    # phenotypes are bitwise identical; the partial sums are ordered identically
+    assert np.array_equal(f2[:T], f1[::-1])
+    assert np.array_equal(f2[T:], f1[:7])
+
+
+def test_launch_shapes_give_identical_phenotypes():
+    tok, g = I.small_population(seed=2)
+    g = I.Grid(150, 70)
+    ref = None
+    for K, thr, G in [(1, 32, 1), (2, 64, 3), (4, 128, 50), (8, 128, 7), (8, 64, 1)]:
+        with tgp.Context(points_per_thread=K, threads_per_block=thr, n_groups=G) as c:
+            p = phenotype(c, tok, g)
+        if ref is None:
+            ref = p
+        assert np.array_equal(ref.view(np.int32), p.view(np.int32)), (K, thr, G)
+
+
+def test_fitness_is_deterministic_and_matches_phenotype(ctx):
+    tok, _ = I.small_population(seed=8)
+    g = I.Grid(300, 200)
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    f1 = ctx.fitness(pop, dom, tok.n_trees)
+    f2 = ctx.fitness(pop, dom, tok.n_trees)
+    assert np.array_equal(f1, f2)
+    ph = phenotype(ctx, tok, g, pop, dom).astype(np.float64)
+    xs = np.array([oracle.grid_point(g.W, g.H, -5, 5, -5, 5, p) for p in range(g.N)], np.float64)
+    # target in binary32 as the kernel forms it
+    x32, y32 = xs[:, 0].astype(np.float32), xs[:, 1].astype(np.float32)
+    x4, y4 = (x32 * x32) * (x32 * x32), (y32 * y32) * (y32 * y32)
+    P = (x4 / (np.float32(1) + x4) + y4 / (np.float32(1) + y4)).astype(np.float64)
+    with np.errstate(all="ignore"):
+        r = np.sqrt(np.mean((ph - P) ** 2, axis=1))
+    r = np.where(np.isfinite(r), r, np.inf)
+    fin = np.isfinite(r) & (r < 1e15)
+    assert np.allclose(f1[fin], r[fin], rtol=2e-6, atol=0)
+
+
+def test_fitness_dev_and_nonblocking(ctx):
+    tok, g = I.small_population(seed=1)
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    ref = ctx.fitness(pop, dom, tok.n_trees)
+    out = torch.empty(tok.n_trees, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    ctx.fitness_dev(pop, dom, out, stream=s)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
+    host = torch.empty(tok.n_trees, dtype=torch.float64).pin_memory()
+    ctx.fitness(pop, dom, tok.n_trees, stream=s, blocking=False, out=host.numpy())
+    s.synchronize()
+    assert np.array_equal(host.numpy(), ref)
+
+
+# ---------------------------------------------------------------- targets
+
+def test_target_tensor_host_and_device(ctx):
+    tok, g = I.small_population(seed=4)
+    g = I.Grid(48, 40)
+    rng = np.random.default_rng(0)
+    target = rng.uniform(-2, 2, g.N).astype(np.float32)
+    pop = ctx.compile_tokens(tok)
+    fh = ctx.fitness(pop, ctx.load_domain(g.W, g.H, target=target), tok.n_trees)
+    fd = ctx.fitness(pop, ctx.load_domain(g.W, g.H, target=torch.from_numpy(target).cuda()), tok.n_trees)
+    assert np.array_equal(fh, fd)
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, -5, 5, -5, 5)
+    c = classify(phenotype(ctx, tok, g, pop), v64, v32, fl)
+    r64, r32, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, -5, 5, -5, 5,
+                                 target=target.astype(np.float64))
+    assert_fitness(fh, r64, r32, (c["excluded"] | c["ill"]).any(axis=1), g.N, "tensor target")
+
+
+def test_target_tokens_random_tree(ctx):
+    rng = np.random.default_rng(44)
+    target_tree = I._full(rng, 4, I.FUNCTIONS)
+    tt = I.to_tokens([target_tree])
+    tok, _ = I.small_population(seed=4)
+    g = I.Grid(50, 30)
+    dom = ctx.load_domain(g.W, g.H, target_tokens=(tt.ops, tt.imm, tt.order))
+    pop = ctx.compile_tokens(tok)
+    fit = ctx.fitness(pop, dom, tok.n_trees)
+    t64, t32, tfl = oracle.evaluate(tt.ops, tt.imm, tt.tree_off, 0, g.W, g.H, -5, 5, -5, 5)
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, -5, 5, -5, 5)
+    c = classify(phenotype(ctx, tok, g, pop), v64, v32, fl)
+    # the device forms the target tree in binary32: compare against the oracle's
+    # fitness with the FP32-faithful target values
+    r64, r32, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, -5, 5, -5, 5,
+                                 target=t32[0].astype(np.float64))
+    flagged = (c["excluded"] | c["ill"]).any(axis=1) | bool(tfl.any())
+    assert_fitness(fit, r64, r32, flagged, g.N, "token target")
+
+
+# ---------------------------------------------------------------- full size
+
+def test_population_at_scale_sampled_elements_and_full_fitness(ctx):
+    """100 RHH trees (depth 2-8) on 1024x1024: phenotypes on 8192 sampled
+    points, fitness of every tree against the oracle over all 2^20 points."""
+    tok, g = I.population_at_scale(seed=1)
+    pool = oracle_pool()   # created before the first device call of this test
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    fit = ctx.fitness(pop, dom, tok.n_trees)
+    ph = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
+    ctx.evaluate(pop, dom, ph)
+    rng = np.random.default_rng(123)
+    pts = np.sort(rng.choice(g.N, 8192, replace=False))
+    pts = np.concatenate([pts, [0, g.N - 1]])
+    got = ph[:, torch.from_numpy(pts).cuda()].cpu().numpy()
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi,
+                                   g.ylo, g.yhi, pts=pts)
+    c = assert_elements(got, v64, v32, fl, context="at scale")
+    r64, r32, nfl = oracle_fitness_parallel(tok, g)
+    # trees whose sampled points show ill-conditioning, or any near-singular
+    # division anywhere on the grid, are checked against the FP32-faithful fitness
+    flagged = (c["excluded"] | c["ill"]).any(axis=1) | (nfl > 0)
+    assert_fitness(fit, r64, r32, flagged, g.N, "at scale")
+    assert pool is not None
+
+
+def test_batched_uneven_sampled(ctx):
+    """4096 trees of 3..255 nodes with ~30% duplicated subtrees on 256x256."""
+    tok, g, stats = I.batched_uneven(seed=2)
+    assert 0.2 < stats["dup_fraction"] < 0.4
+    oracle_pool()
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    fit = ctx.fitness(pop, dom, tok.n_trees)
+    ph = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
+    ctx.evaluate(pop, dom, ph)
+    rng = np.random.default_rng(5)
+    pts = np.sort(rng.choice(g.N, 256, replace=False))
+    got = ph[:, torch.from_numpy(pts).cuda()].cpu().numpy()
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi,
+                                   g.ylo, g.yhi, pts=pts)
+    c = assert_elements(got, v64, v32, fl, context="batched")
+    idx = np.sort(rng.choice(tok.n_trees, 256, replace=False))
+    sub = subset(tok, idx)
+    r64, r32, nfl = oracle_fitness_parallel(sub, g)
+    flagged = (c["excluded"] | c["ill"]).any(axis=1)[idx] | (nfl > 0)
+    assert_fitness(fit[idx], r64, r32, flagged, g.N, "batched")
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_leaf_populations(ctx):
+    g = I.Grid(10, 10)
+    dom = load(ctx, g)
+    empty = ctx.compile_population(np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(1, np.int64))
+    assert ctx.fitness(empty, dom, 0).size == 0
+    tok = I.to_tokens([I.parse_string(e) for e in ["x", "y", "0.5"]])
+    full_check(ctx, tok, g, "leaves")
+
+
+def test_bad_handles_and_shapes(ctx):
+    g = I.Grid(8, 8)
+    dom = load(ctx, g)
+    tok, _ = I.small_population()
+    pop = ctx.compile_tokens(tok)
+    with pytest.raises(tgp.TgpError):
+        ctx.fitness(pop + 1000, dom, tok.n_trees)
+    with pytest.raises(tgp.TgpError):
+        ctx.fitness(pop, dom + 1000, tok.n_trees)
+    with pytest.raises(tgp.TgpError):
+        ctx.load_domain(0, 5)
+    with tgp.Context(points_per_thread=3) as c:
+        with pytest.raises(tgp.TgpError):
+            c.fitness(c.compile_tokens(tok), c.load_domain(4, 4), tok.n_trees)

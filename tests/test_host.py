@@ -1,0 +1,300 @@
+"""Host side of the library, on CPU: the C ABI loads and exports what
+include/tgp.h declares, token validation, hash-consing, and the bytecode the
+compiler emits.  The bytecode is checked by running it through a small numpy
+interpreter written here (test-only) and comparing with the CPU oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_07512_gb300 as tgp
+from paper_2103_07512_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# decoded forms (order of the Form enum of the bytecode)
+(F_END, F_AO, F_OA, F_TT, F_UA, F_UT, F_LD, F_ST, F_SPILL, F_FILL, F_ROOT, F_CST, F_CLD) = range(13)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tgp.Context(host_only=True)
+    yield c
+    c.close()
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "tgp.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|const char\*)\s+(tgp_\w+)\s*\(", hdr, re.M))
+    assert len(declared) >= 14
+    L = tgp.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(tgp.EXPORTS)
+
+
+def test_layout():
+    lay = tgp.debug_layout()
+    assert lay["n_reg"] >= 2 and lay["n_forms"] == 13
+
+
+def test_host_only_context_refuses_device_work(ctx):
+    with pytest.raises(tgp.TgpError) as e:
+        ctx.load_domain(4, 4)
+    assert e.value.code == tgp.E_INVALID
+
+
+# ---------------------------------------------------------------- validation
+
+@pytest.mark.parametrize("ops,imm,off,frag", [
+    ([3, 0], [], [0, 2], "lacks operands"),
+    ([0, 1], [], [0, 2], "exactly one expression"),
+    ([42], [], [0, 1], "unknown opcode"),
+    ([2], [], [0, 1], "beyond n_imm"),
+    ([0], [1.0], [0, 1], "CONST tokens"),
+    ([2], [float("nan")], [0, 1], "not finite"),
+    ([2], [float("inf")], [0, 1], "not finite"),
+    ([0, 0], [], [0, 1, 1], "empty"),
+    ([0], [], [1, 1], "tree_off[0]"),
+])
+def test_malformed_tokens(ctx, ops, imm, off, frag):
+    with pytest.raises(tgp.TgpError) as e:
+        ctx.compile_population(np.array(ops), np.array(imm, np.float32), np.array(off))
+    assert e.value.code == tgp.E_TOKENS
+    assert frag in str(e.value)
+
+
+def test_bad_arguments(ctx):
+    with pytest.raises(tgp.TgpError) as e:
+        ctx.compile_population(np.array([0]), np.array([], np.float32), np.array([0, 1]), order=7)
+    assert e.value.code == tgp.E_INVALID
+
+
+def test_depth_limit(ctx):
+    t = I.leaf(I.X)
+    for _ in range(1100):
+        t = I.node(I.NEG, t)
+    tok = I.to_tokens([t])
+    with pytest.raises(tgp.TgpError) as e:
+        ctx.compile_tokens(tok)
+    assert "depth" in str(e.value)
+    t = I.leaf(I.X)
+    for _ in range(1000):
+        t = I.node(I.NEG, t)
+    ctx.compile_tokens(I.to_tokens([t]))
+
+
+def test_empty_population(ctx):
+    pop = ctx.compile_population(np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(1, np.int64))
+    ins, off = ctx.debug_plan(pop, 16)
+    assert ins.shape[0] <= 1
+
+
+# ---------------------------------------------------------------- hash-consing
+
+def test_identical_subtrees_share_one_node(ctx):
+    e = "add(mult(x, y), sin(mult(x, y)))"
+    tok = I.to_tokens([I.parse_string(e), I.parse_string(e), I.parse_string("mult(x, y)")])
+    ctx.compile_tokens(tok)
+    st = ctx.stats()
+    assert st["tree_nodes"] == 8 + 8 + 3
+    # unique: x, y, mult(x,y), sin(.), add(.,.)
+    assert st["dag_nodes"] == 5
+    assert st["dag_internal"] == 3
+
+
+def test_constants_are_identified_by_bits(ctx):
+    tok = I.to_tokens([I.parse_string("add(x, 0.5)"), I.parse_string("add(x, 0.5)"),
+                       I.parse_string("add(x, 0.25)")])
+    ctx.compile_tokens(tok)
+    assert ctx.stats()["dag_internal"] == 2
+
+
+def test_prefix_and_postfix_give_same_dag(ctx):
+    tok, _ = I.small_population(seed=0)
+    ctx.compile_tokens(tok)
+    a = ctx.stats()
+    ctx.compile_tokens(I.convert_order(tok, I.POSTFIX))
+    b = ctx.stats()
+    assert a["dag_nodes"] == b["dag_nodes"] and a["tree_nodes"] == b["tree_nodes"]
+
+
+# ---------------------------------------------------------------- bytecode
+
+def _sinpi32(a):
+    a64 = a.astype(np.float64)
+    return np.sin(np.pi * np.remainder(a64, 2.0)).astype(np.float32)
+
+
+def _cospi32(a):
+    a64 = a.astype(np.float64)
+    return np.cos(np.pi * np.remainder(a64, 2.0)).astype(np.float32)
+
+
+def _bin(fn, a, b):
+    with np.errstate(all="ignore"):
+        if fn == I.ADD:
+            return a + b
+        if fn == I.SUB:
+            return a - b
+        if fn == I.MUL:
+            return a * b
+        if fn == I.DIV:
+            return np.where(b == 0, np.float32(0), a / np.where(b == 0, np.float32(1), b)).astype(np.float32)
+        if fn == I.MIN:
+            return np.fmin(a, b)
+        if fn == I.MAX:
+            return np.fmax(a, b)
+    raise AssertionError(fn)
+
+
+def _un(fn, a):
+    if fn == I.SIN:
+        return _sinpi32(a)
+    if fn == I.COS:
+        return _cospi32(a)
+    if fn == I.NEG:
+        return -a
+    if fn == I.ABS:
+        return np.abs(a)
+    raise AssertionError(fn)
+
+
+def run_bytecode(ins, off, n_trees, X, Y, n_reg):
+    """Test-only numpy interpreter of the decoded bytecode (binary32)."""
+    n = X.size
+    out = np.full((n_trees, n), np.nan, np.float32)
+    seen = np.zeros(n_trees, bool)
+    for g in range(off.size - 1):
+        A = np.zeros(n, np.float32)
+        R = [None] * n_reg
+        F = None
+        smem = {}
+        for i in range(off[g], off[g + 1]):
+            form, fn, o1, o2, aux, immb = (int(v) for v in ins[i])
+            imm = np.array([immb], np.int32).view(np.float32)[0]
+
+            def opnd(o):
+                if o == 0:
+                    return X
+                if o == 1:
+                    return Y
+                if o == 2:
+                    return np.full(n, imm, np.float32)
+                if o == 3 + n_reg:
+                    assert F is not None, "fill buffer read before a fill"
+                    return F
+                assert R[o - 3] is not None, "register slot read before a store"
+                return R[o - 3]
+            if form == F_END:
+                assert i == off[g + 1] - 1
+                break
+            if form == F_AO:
+                A = _bin(fn, A, opnd(o1))
+            elif form == F_OA:
+                assert fn in (I.SUB, I.DIV, I.MIN, I.MAX)
+                A = _bin(fn, opnd(o1), A)
+            elif form == F_TT:
+                assert o1 <= 2 and o2 <= 2 and not (o1 == 2 and o2 == 2)
+                A = _bin(fn, opnd(o1), opnd(o2))
+            elif form == F_UA:
+                A = _un(fn, A)
+            elif form == F_UT:
+                assert o1 <= 2
+                A = _un(fn, opnd(o1))
+            elif form == F_LD:
+                A = opnd(o1).copy()
+            elif form == F_ST:
+                R[o1 - 3] = A.copy()
+            elif form == F_SPILL:
+                smem[aux] = A.copy()
+            elif form == F_FILL:
+                F = smem[aux].copy()
+            elif form == F_ROOT:
+                assert not seen[aux], "tree emitted twice"
+                seen[aux] = True
+                out[aux] = A
+            else:
+                raise AssertionError(f"unexpected form {form}")
+    assert seen.all(), "some tree never reached its root instruction"
+    return out
+
+
+def _check_population(ctx, tok, W=7, H=5, trig_free=False):
+    pop = ctx.compile_tokens(tok)
+    ins, off = ctx.debug_plan(pop, W * H)
+    lay = tgp.debug_layout()
+    xs = np.array([oracle.grid_point(W, H, -5, 5, -5, 5, p) for p in range(W * H)], np.float32)
+    got = run_bytecode(ins, off, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy(), lay["n_reg"])
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5)
+    if trig_free:
+        assert np.array_equal(got, v32, equal_nan=True)
+    else:
+        ok = ~fl
+        assert np.allclose(got[ok], v32[ok], rtol=1e-4, atol=1e-4, equal_nan=True)
+    ctx.release_population(pop)
+    return ins, off
+
+
+def test_bytecode_small_population(ctx):
+    tok, _ = I.small_population(seed=0)
+    _check_population(ctx, tok)
+
+
+def test_bytecode_postfix_input(ctx):
+    tok, _ = I.small_population(seed=4)
+    _check_population(ctx, I.convert_order(tok, I.POSTFIX))
+
+
+def test_bytecode_trig_free_is_exact(ctx):
+    rng = np.random.default_rng(11)
+    funcs = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.ABS, I.MIN, I.MAX)
+    trees = I.ramped_half_and_half(40, 2, 7, rng, funcs)
+    _check_population(ctx, I.to_tokens(trees), trig_free=True)
+
+
+def test_bytecode_deep_trees_spill_to_shared_memory(ctx):
+    rng = np.random.default_rng(3)
+    funcs = (I.ADD, I.SUB, I.MUL, I.MIN, I.MAX)
+    trees = [I._full(rng, 9, funcs) for _ in range(3)]   # full binary trees: 9 slots needed
+    ins, off = _check_population(ctx, I.to_tokens(trees), W=3, H=2, trig_free=True)
+    assert (ins[:, 0] == F_SPILL).any() and (ins[:, 0] == F_FILL).any()
+
+
+def test_bytecode_shared_subtrees_are_evaluated_once(ctx):
+    s = "sin(add(mult(x, y), 0.25))"
+    trees = [f"add({s}, {s})", f"mult({s}, x)", f"div(y, {s})", s]
+    tok = I.to_tokens([I.parse_string(e) for e in trees])
+    ins, off = _check_population(ctx, tok)
+    # the sin node is computed by exactly one unary instruction in the plan
+    n_sin = int(((ins[:, 0] == F_UA) & (ins[:, 1] == I.SIN)).sum())
+    n_sin += int(((ins[:, 0] == F_UT) & (ins[:, 1] == I.SIN)).sum())
+    groups = off.size - 1
+    assert n_sin <= groups
+
+
+def test_bytecode_duplicated_trees_and_leaf_roots(ctx):
+    trees = ["x", "y", "0.5", "x", "add(x, y)", "add(x, y)", "neg(0.5)", "sub(0.5, 0.25)"]
+    tok = I.to_tokens([I.parse_string(e) for e in trees])
+    _check_population(ctx, tok, trig_free=True)
+
+
+def test_bytecode_exact_size_population_with_duplicates(ctx):
+    rng = np.random.default_rng(2)
+    trees, stats = I.exact_size_population(120, 3, 255, 12, 0.3, rng)
+    assert 0.15 < stats["dup_fraction"] < 0.45
+    _check_population(ctx, I.to_tokens(trees), W=4, H=3)
+
+
+@pytest.mark.parametrize("n_points", [1, 100, 4096, 1 << 20])
+def test_plan_group_offsets_are_consistent(ctx, n_points):
+    tok, _ = I.small_population(seed=1)
+    pop = ctx.compile_tokens(tok)
+    ins, off = ctx.debug_plan(pop, n_points)
+    assert off[0] == 0 and off[-1] == ins.shape[0]
+    assert np.all(np.diff(off) > 0)
+    assert np.all(ins[off[1:] - 1, 0] == F_END)
+    roots = ins[ins[:, 0] == F_ROOT, 4]
+    assert sorted(roots.tolist()) == list(range(tok.n_trees))

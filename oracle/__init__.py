@@ -58,10 +58,10 @@ def _load():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         lib.oracle_eval.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
-                                    i64, P, P, P, P]
+                                    i64, P, P, P, P, P]
         lib.oracle_eval.restype = ctypes.c_int
         lib.oracle_fitness.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
-                                       i32, P, i64, P, P, P, P]
+                                       i32, P, i64, P, P, P, P, P]
         lib.oracle_fitness.restype = ctypes.c_int
         lib.oracle_pagie.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.oracle_pagie.restype = ctypes.c_double
@@ -95,12 +95,13 @@ def _pop_arrays(ops, imm, tree_off):
     return ops, imm, tree_off
 
 
-def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None):
+def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None, with_bound=False):
     """Phenotypes of every tree.
 
     Returns (v64 [T, n], v32 [T, n], flags [T, n]) where n = H*W (all points in
     flat order) or len(pts).  v32 is the FP32-faithful evaluation, flags marks
-    points where a division saw |denominator| < 1e-6.
+    points where a division saw |denominator| < 1e-6.  With with_bound=True a
+    fourth array [T, n] bounds |any binary32 evaluation - exact| per element.
     """
     lib = _load()
     ops, imm, tree_off = _pop_arrays(ops, imm, tree_off)
@@ -114,17 +115,23 @@ def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None):
     v64 = np.empty((T, n), np.float64)
     v32 = np.empty((T, n), np.float32)
     fl = np.empty((T, n), np.uint8)
+    eb = np.empty((T, n), np.float64) if with_bound else None
     rc = lib.oracle_eval(_ptr(ops), _ptr(imm), imm.size, _ptr(tree_off), T, order,
-                         W, H, xlo, xhi, ylo, yhi, n, _ptr(pts_arr), _ptr(v64), _ptr(v32), _ptr(fl))
+                         W, H, xlo, xhi, ylo, yhi, n, _ptr(pts_arr), _ptr(v64), _ptr(v32), _ptr(fl),
+                         _ptr(eb))
     if rc != 0:
         raise OracleError(f"oracle_eval failed: {rc}")
+    if with_bound:
+        return v64, v32, fl.astype(bool), eb
     return v64, v32, fl.astype(bool)
 
 
-def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pts=None):
+def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pts=None,
+            with_bound=False):
     """RMSE of every tree against Pagie (target None) or a [H*W] value array.
 
-    Returns (rmse64 [T], rmse32 [T], n_flagged [T]).
+    Returns (rmse64 [T], rmse32 [T], n_flagged [T]); with with_bound=True also
+    rmse_err [T], the L2 bound of the per-element binary32 error bounds.
     """
     lib = _load()
     ops, imm, tree_off = _pop_arrays(ops, imm, tree_off)
@@ -143,11 +150,14 @@ def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pt
     r64 = np.empty(T, np.float64)
     r32 = np.empty(T, np.float64)
     nf = np.empty(T, np.int64)
+    re = np.empty(T, np.float64) if with_bound else None
     rc = lib.oracle_fitness(_ptr(ops), _ptr(imm), imm.size, _ptr(tree_off), T, order,
                             W, H, xlo, xhi, ylo, yhi, kind, _ptr(tv), n, _ptr(pts_arr),
-                            _ptr(r64), _ptr(r32), _ptr(nf))
+                            _ptr(r64), _ptr(r32), _ptr(nf), _ptr(re))
     if rc != 0:
         raise OracleError(f"oracle_fitness failed: {rc}")
+    if with_bound:
+        return r64, r32, nf, re
     return r64, r32, nf
 
 

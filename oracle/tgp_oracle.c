@@ -42,6 +42,23 @@
  * Per element the oracle flags near-singular division: some div node of the
  * tree saw a denominator with |b| < 1e-6 in either mode.
  *
+ * Per element it also bounds how far ANY binary32 evaluation of the tree can
+ * land from the exact value, given operators that are correctly rounded for
+ * + - * / (error <= u|r|, u = 2^-24, plus 2^-149 in the subnormal range) and
+ * sin/cos(pi*a) within 2 ulp of the exact value of the binary32 argument.
+ * It is a forward running-error bound, propagated node by node with the
+ * binary64 values standing in for the exact ones:
+ *   x, y, const: 0 (binary32 values, exact)
+ *   a +- b:  P = Ea + Eb
+ *   a * b:   P = |b|Ea + |a|Eb + EaEb
+ *   a / b:   P = (Ea + |a/b| Eb) / (|b| - Eb), unbounded if |b| <= Eb (the
+ *            sign or zero test of the denominator is then undecided); 0 for
+ *            an exact zero denominator (the protected result is exactly 0)
+ *   sin/cos(pi a): P = min(pi Ea, 2), plus 2 ulp of the result
+ *   -a, |a|: Ea;  min/max: max(Ea, Eb)
+ * and E = P + u(|v| + P) (+ 2^-150 for a possibly subnormal product or
+ * quotient); unbounded once |v| + E reaches the binary32 range.
+ *
  * Build: gcc -O2 -fPIC -shared -ffp-contract=off -o liboracle.so tgp_oracle.c -lm
  * (-ffp-contract=off keeps a*b+c from being fused, which some targets do by
  * default and which would change the binary32 grid coordinates.)
@@ -252,30 +269,89 @@ static double apply64(int op, double a, double b)
 
 #define NEAR_SINGULAR 1e-6
 
+#define U32 5.9604644775390625e-08          /* 2^-24, unit roundoff of binary32 */
+#define TINY32 1.4012984643248171e-45       /* 2^-149, smallest binary32 subnormal */
+#define MAX32 3.4028234663852886e+38        /* largest finite binary32 */
+#define TRIG_ULPS 2.0
+
+#define MIN_NORMAL32 1.1754943508222875e-38   /* 2^-126 */
+
+/* Rounding error of one binary32 operation whose computed result lies within
+ * `prop` of v: at most u * |computed| <= u * (|v| + prop), plus half the
+ * subnormal spacing when the result may be subnormal.  A sum or difference is
+ * exact in the subnormal range, so `exact_sub` drops that term; a result that
+ * is exactly zero from exact operands is exact. */
+static double rnd32(double v, double prop, int exact_sub)
+{
+    double m = fabs(v) + prop;
+    if (m == 0.0) return 0.0;
+    double e = U32 * m;
+    if (!exact_sub && m < MIN_NORMAL32) e += 0.5 * TINY32;
+    return e;
+}
+
+/* Error bound of one node from its operands' bounds (see the header). */
+static double err_bound(int op, double a, double b, double ea, double eb, double v)
+{
+    double e, prop;
+    if (!isfinite(v) || !isfinite(ea) || !isfinite(eb)) return INFINITY;
+    switch (op) {
+    case O_ADD: case O_SUB:
+        prop = ea + eb;
+        e = prop + rnd32(v, prop, 1);
+        break;
+    case O_MUL:
+        prop = fabs(b) * ea + fabs(a) * eb + ea * eb;
+        e = prop + rnd32(v, prop, 0);
+        break;
+    case O_DIV:
+        if (b == 0.0 && eb == 0.0) { e = 0.0; break; }   /* exact zero denominator: result 0 */
+        if (fabs(b) <= eb) return INFINITY;
+        prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);
+        e = prop + rnd32(v, prop, 0);
+        break;
+    case O_SIN: case O_COS:
+        prop = fmin(ORACLE_PI * ea, 2.0);
+        e = prop + TRIG_ULPS * (2.0 * U32 * (fabs(v) + prop) + TINY32);
+        break;
+    case O_NEG: case O_ABS:
+        e = ea;
+        break;
+    case O_MIN: case O_MAX:
+        e = fmax(ea, eb);
+        break;
+    default:
+        return INFINITY;
+    }
+    if (fabs(v) + e >= MAX32) return INFINITY;
+    return e;
+}
+
 typedef struct {
     double x64, y64;   /* coordinates (binary32 values widened) */
     int flag;          /* near-singular division seen */
 } opoint;
 
-/* Recursive tree walk in both modes at once. */
-static void eval_node(const onode* nodes, int i, opoint* pt, double* v64, float* v32)
+/* Recursive tree walk in both modes at once, with the error bound. */
+static void eval_node(const onode* nodes, int i, opoint* pt, double* v64, float* v32, double* eb)
 {
     const onode* n = &nodes[i];
     switch (n->op) {
-    case O_X: *v64 = pt->x64; *v32 = (float)pt->x64; return;
-    case O_Y: *v64 = pt->y64; *v32 = (float)pt->y64; return;
-    case O_CONST: *v64 = n->imm; *v32 = (float)n->imm; return;
+    case O_X: *v64 = pt->x64; *v32 = (float)pt->x64; *eb = 0.0; return;
+    case O_Y: *v64 = pt->y64; *v32 = (float)pt->y64; *eb = 0.0; return;
+    case O_CONST: *v64 = n->imm; *v32 = (float)n->imm; *eb = 0.0; return;
     default: break;
     }
-    double a64 = 0.0, b64 = 0.0;
+    double a64 = 0.0, b64 = 0.0, ea = 0.0, eb_ = 0.0;
     float a32 = 0.0f, b32 = 0.0f;
-    eval_node(nodes, n->kid[0], pt, &a64, &a32);
-    if (n->kid[1] >= 0) eval_node(nodes, n->kid[1], pt, &b64, &b32);
+    eval_node(nodes, n->kid[0], pt, &a64, &a32, &ea);
+    if (n->kid[1] >= 0) eval_node(nodes, n->kid[1], pt, &b64, &b32, &eb_);
     if (n->op == O_DIV) {
         if (fabs(b64) < NEAR_SINGULAR || fabs((double)b32) < NEAR_SINGULAR) pt->flag = 1;
     }
     *v64 = apply64(n->op, a64, b64);
     *v32 = (float)apply64(n->op, (double)a32, (double)b32);
+    *eb = err_bound(n->op, a64, b64, ea, eb_, *v64);
 }
 
 /* ------------------------------------------------------------------ grid */
@@ -315,13 +391,14 @@ double oracle_pagie(double x, double y)
  *   out64 [n_trees][n_pts]  binary64 values (required)
  *   out32 [n_trees][n_pts]  FP32-faithful values (may be NULL)
  *   flags [n_trees][n_pts]  1 where a division saw |denominator| < 1e-6 (may be NULL)
+ *   errb  [n_trees][n_pts]  bound on |any binary32 evaluation - exact| (may be NULL)
  * Returns 0 or a negative error code (malformed tokens, bad opcode, imm count).
  */
 int oracle_eval(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                 int32_t n_trees, int32_t order,
                 int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                 int64_t n_pts, const int64_t* pts,
-                double* out64, float* out32, uint8_t* flags)
+                double* out64, float* out32, uint8_t* flags, double* errb)
 {
     if (n_trees < 0 || W <= 0 || H <= 0 || n_pts < 0) return OR_ARG;
     otree* trees = (otree*)calloc((size_t)(n_trees > 0 ? n_trees : 1), sizeof(otree));
@@ -334,12 +411,13 @@ int oracle_eval(const int32_t* ops, const float* imm, int64_t n_imm, const int64
             float xf, yf;
             oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
             opoint pt = { (double)xf, (double)yf, 0 };
-            double v64;
+            double v64, e;
             float v32;
-            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32);
+            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32, &e);
             out64[(size_t)t * n_pts + i] = v64;
             if (out32) out32[(size_t)t * n_pts + i] = v32;
             if (flags) flags[(size_t)t * n_pts + i] = (uint8_t)pt.flag;
+            if (errb) errb[(size_t)t * n_pts + i] = e;
         }
     }
     free_population(trees, n_trees);
@@ -357,7 +435,11 @@ enum { TG_PAGIE = 0, TG_VALUES = 1 };
  *   target_kind 1: target_vals[p] (binary64, indexed by flat point index).
  *   rmse64 [n_trees]: RMSE of the binary64 phenotype;
  *   rmse32 [n_trees]: RMSE of the FP32-faithful phenotype (may be NULL);
- *   n_flagged [n_trees]: points with a near-singular division (may be NULL).
+ *   n_flagged [n_trees]: points with a near-singular division (may be NULL);
+ *   rmse_err [n_trees]: sqrt(mean(E^2)) of the per-element error bounds, a
+ *     bound on how far the RMSE of any binary32 evaluation of the phenotype
+ *     can be from rmse64 (triangle inequality in the L2 norm); +inf when
+ *     some element is unbounded (may be NULL).
  * A non-finite sum gives +inf.
  */
 int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
@@ -365,7 +447,7 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
                    int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                    int32_t target_kind, const double* target_vals,
                    int64_t n_pts, const int64_t* pts,
-                   double* rmse64, double* rmse32, int64_t* n_flagged)
+                   double* rmse64, double* rmse32, int64_t* n_flagged, double* rmse_err)
 {
     if (n_trees < 0 || W <= 0 || H <= 0) return OR_ARG;
     if (target_kind == TG_VALUES && !target_vals) return OR_ARG;
@@ -376,7 +458,7 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
     int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, trees);
     if (rc) { free_population(trees, n_trees); free(trees); return rc; }
     for (int32_t t = 0; t < n_trees; t++) {
-        double s64 = 0.0, s32 = 0.0;
+        double s64 = 0.0, s32 = 0.0, se = 0.0;
         int64_t nf = 0;
         for (int64_t i = 0; i < N; i++) {
             int64_t p = pts ? pts[i] : i;
@@ -384,13 +466,14 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
             oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
             double tv = target_kind == TG_PAGIE ? oracle_pagie((double)xf, (double)yf) : target_vals[p];
             opoint pt = { (double)xf, (double)yf, 0 };
-            double v64;
+            double v64, e;
             float v32;
-            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32);
+            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32, &e);
             double d64 = v64 - tv;
             double d32 = (double)v32 - tv;
             s64 += d64 * d64;
             s32 += d32 * d32;
+            se += e * e;
             nf += pt.flag;
         }
         double r64 = sqrt(s64 / (double)N);
@@ -398,6 +481,10 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
         rmse64[t] = isfinite(r64) ? r64 : INFINITY;
         if (rmse32) rmse32[t] = isfinite(r32) ? r32 : INFINITY;
         if (n_flagged) n_flagged[t] = nf;
+        if (rmse_err) {
+            double re = sqrt(se / (double)N);
+            rmse_err[t] = isfinite(re) ? re : INFINITY;
+        }
     }
     free_population(trees, n_trees);
     free(trees);

@@ -358,3 +358,72 @@ def test_golden_regression_small_population():
     tok, g = I.small_population(seed=0)
     r64, _, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     assert np.allclose(r64, exp, rtol=1e-12, atol=0, equal_nan=False)
+
+
+# ---------------------------------------------------------------- error bound
+
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_error_bound_contains_fp32_faithful_evaluation(seed):
+    """The FP32-faithful walk is one binary32 evaluation with correctly rounded
+    operators, so it must lie within the bound of the binary64 value."""
+    pops = [I.small_population(seed=seed)[0]]
+    rng = np.random.default_rng(seed)
+    trees, _ = I.exact_size_population(60, 3, 255, 12, 0.3, rng)
+    pops.append(I.to_tokens(trees))
+    pops.append(I.to_tokens([I._full(rng, 8, I.FUNCTIONS) for _ in range(6)]))
+    for tok in pops:
+        v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, 23, 19, -5, 5, -5, 5,
+                                           with_bound=True)
+        m = np.isfinite(v64) & np.isfinite(eb)
+        d = np.abs(v32.astype(np.float64) - v64)
+        assert np.all(d[m] <= eb[m])
+        assert m.mean() > 0.8
+        # tight: the bound is not vacuous on the elements that round
+        assert np.nanmax(np.where(m & (eb > 0), d / np.where(eb > 0, eb, 1), 0)) > 0.05
+        r64, r32, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, 0, 23, 19, -5, 5, -5, 5,
+                                         with_bound=True)
+        f = np.isfinite(re) & np.isfinite(r64)
+        assert np.all(np.abs(r32[f] - r64[f]) <= re[f] * (1 + 1e-12))
+
+
+def test_error_bound_closed_forms():
+    W, H = 7, 5
+    X, Y = np_grid(W, H)
+    v64, _, _, eb = ev_bound(["x", "0.5", "add(x, y)", "mult(x, y)", "neg(abs(x))", "min(x, y)",
+                              "div(x, sub(y, y))"], W, H)
+    assert np.all(eb[0] == 0) and np.all(eb[1] == 0)
+    assert np.allclose(eb[2], U32 * np.abs(X + Y), rtol=1e-15, atol=0)
+    assert np.allclose(eb[3], U32 * np.abs(X * Y) + np.where(X * Y == 0, 0, 0), rtol=1e-15, atol=0)
+    assert np.all(eb[4] == 0) and np.all(eb[5] == 0)
+    assert np.all(eb[6] == 0)          # exact zero denominator: protected result is exactly 0
+
+
+def test_error_bound_trig_and_division():
+    W, H = 5, 3
+    X, Y = np_grid(W, H)
+    _, _, _, eb = ev_bound(["sin(x)", "sin(add(x, y))", "div(1.0, add(x, 0.3))"], W, H)
+    # exact argument: only the 2-ulp allowance of the function
+    assert np.all(eb[0] <= 2 * (2 * U32 * np.abs(np.sin(np.pi * X)) + 2.0 ** -149) * (1 + 1e-12))
+    # rounded argument: pi * E(arg) is propagated
+    assert np.all(eb[1] >= np.pi * U32 * np.abs(X + Y) * (1 - 1e-12))
+    b = X + np.float32(0.3).astype(np.float64)
+    exp = (1.0 * U32 * np.abs(b) / np.abs(b) ** 2) / (1 - U32)   # Eb/|b|^2 leading term
+    assert np.all(eb[2] >= exp * 0.99)
+
+
+def test_error_bound_unbounded_cases():
+    _, _, _, eb = ev_bound(["div(1.0, sub(mult(x, 0.1), mult(0.1, x)))", "mult(x, 1e30)",
+                            "mult(mult(x, 1e30), mult(x, 1e30))"], 3, 3)
+    # undecided zero test of the denominator
+    assert np.all(~np.isfinite(eb[0][[0, 2, 6, 8]]))
+    assert np.all(np.isfinite(eb[1]))
+    # binary32 overflow
+    assert np.all(~np.isfinite(eb[2][[0, 2, 6, 8]]))
+
+
+def ev_bound(exprs, W, H, lo=-5.0, hi=5.0):
+    t = toks(*exprs)
+    return oracle.evaluate(t.ops, t.imm, t.tree_off, 0, W, H, lo, hi, lo, hi, with_bound=True)

@@ -33,6 +33,10 @@ MUTANTS = {
     "near_singular_threshold": ("#define NEAR_SINGULAR 1e-6", "#define NEAR_SINGULAR 1e-9"),
     "nan_fitness_not_inf": ("rmse64[t] = isfinite(r64) ? r64 : INFINITY;", "rmse64[t] = r64;"),
     "abs_dropped": ("case O_ABS: return fabs(a);", "case O_ABS: return a;"),
+    "bound_mul_drops_term": ("prop = fabs(b) * ea + fabs(a) * eb + ea * eb;", "prop = fabs(b) * ea + ea * eb;"),
+    "bound_div_drops_term": ("prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);", "prop = ea / (fabs(b) - eb);"),
+    "bound_trig_not_pi": ("prop = fmin(ORACLE_PI * ea, 2.0);", "prop = fmin(ea, 2.0);"),
+    "bound_add_no_rounding": ("e = prop + rnd32(v, prop, 1);", "e = prop;"),
     "const_imm_order": ("nodes[me].imm = (double)imm[(*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {",
                         "nodes[me].imm = (double)imm[n_imm - 1 - (*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {"),
 }

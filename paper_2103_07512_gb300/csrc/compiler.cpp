@@ -208,16 +208,25 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
 
 namespace {
 
+// A kept node is held in shared memory only when its subtree costs at least
+// this much per point (a spill, a fill and a move per use cost about this).
+constexpr float kSmemKeepMinCost = 6.f;
+
 class GroupGen {
 public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
-          dedup_(dedup) {}
+          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup) {}
 
-    int spill_high = 0;
+    int spill_high = 0;                   // shared-memory slots of the last run
+    std::vector<int32_t> smem_kept;       // kept nodes that landed in shared memory (last run)
 
-    void run(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots) {
-        count_uses(trees, roots);
+    // Emits one group.  Nodes listed in `forbid` are never kept.
+    void run(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots,
+             const std::vector<int32_t>& forbid) {
+        spill_high = 0;
+        smem_kept.clear();
+        count_uses(trees, roots, forbid);
         for (int32_t t : trees) {
             int32_t r = roots[t];
             to_acc(r);
@@ -233,15 +242,21 @@ public:
 
 private:
     // A shared node is kept (evaluated once, held until its last use) when
-    // its subtree costs at least this much per point; cheaper shared nodes
-    // are re-evaluated at each use, which needs no slot.
+    // its subtree costs at least this much per point and its uses lie in at
+    // most kKeepSpan + 1 consecutive trees of the group; otherwise it is
+    // re-evaluated at each use, which needs no slot.  Holding a value across
+    // many trees would take registers from the operands of everything in
+    // between and push them to shared memory.
     static constexpr float kKeepMinCost = 2.f;
+    static constexpr int kKeepSpan = 1;
 
     const Dag& d_;
     std::vector<IrIns>& out_;
     std::vector<int32_t> uses_;    // evaluations of the node still to be consumed
     std::vector<int32_t> where_;   // -1, register slot j, or kNReg + shared slot s
     std::vector<uint8_t> keep_;    // evaluated once and held
+    std::vector<int32_t> first_pos_, last_pos_;   // tree positions of first / last use
+    std::vector<int32_t> span_touched_;
     std::vector<int32_t> touched_;
     bool dedup_;
     bool reg_busy_[kNReg] = {};
@@ -262,7 +277,25 @@ private:
     // edges are consumed that many times.  Node ids are a topological order
     // (operands are interned before their parent), so a pass over the
     // group's nodes in descending id order sees every parent first.
-    void count_uses(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots) {
+    void count_uses(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots,
+                    const std::vector<int32_t>& forbid) {
+        // tree positions (within the group) of the first and last use of each node
+        for (size_t i = 0; i < trees.size(); ++i) {
+            int32_t r = roots[trees[i]];
+            if (is_leaf(N(r).op)) continue;
+            dfs_.assign(1, r);
+            while (!dfs_.empty()) {
+                int32_t n = dfs_.back();
+                dfs_.pop_back();
+                if (last_pos_[n] == (int32_t)i) continue;    // already seen in this tree
+                if (last_pos_[n] < 0) { first_pos_[n] = (int32_t)i; span_touched_.push_back(n); }
+                last_pos_[n] = (int32_t)i;
+                for (int c = 0; c < 2; ++c) {
+                    int32_t k = N(n).kid[c];
+                    if (k >= 0 && !is_leaf(N(k).op)) dfs_.push_back(k);
+                }
+            }
+        }
         for (int32_t t : trees) {
             int32_t r = roots[t];
             if (is_leaf(N(r).op)) continue;
@@ -284,16 +317,21 @@ private:
         std::sort(touched_.begin(), touched_.end(), [](int32_t a, int32_t b) { return a > b; });
         touched_.erase(std::unique(touched_.begin(), touched_.end()), touched_.end());
         for (int32_t n : touched_) where_[n] = -1;
+        for (int32_t n : forbid) where_[n] = -3;   // mark: never keep (reset below)
         // uses_ holds the root counts so far; push evaluations down
         for (int32_t n : touched_) {
             int32_t e = uses_[n];
-            keep_[n] = dedup_ && e >= 2 && N(n).cost >= kKeepMinCost;
+            keep_[n] = dedup_ && e >= 2 && N(n).cost >= kKeepMinCost && where_[n] != -3 &&
+                       last_pos_[n] - first_pos_[n] <= kKeepSpan;
             int32_t f = keep_[n] ? 1 : e;
             for (int c = 0; c < 2; ++c) {
                 int32_t k = N(n).kid[c];
                 if (k >= 0 && !is_leaf(N(k).op)) uses_[k] += f;
             }
         }
+        for (int32_t n : forbid) where_[n] = -1;
+        for (int32_t n : span_touched_) { first_pos_[n] = -1; last_pos_[n] = -1; }
+        span_touched_.clear();
     }
 
     // operand index of a leaf (and its immediate)
@@ -366,6 +404,7 @@ private:
                 int s = alloc_smem();
                 emit(F_SPILL, 0, 0, 0, s, 0);
                 where_[n] = kNReg + s;
+                smem_kept.push_back(n);
             }
         }
     }
@@ -511,30 +550,89 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
     int64_t tile = (int64_t)shape.K * shape.threads;
     plan.n_tiles = (int)((shape.N + tile - 1) / tile);
 
-    // LPT: heaviest tree first onto the lightest group
+    // Tree order: trees that share a subtree are placed next to each other
+    // (sorted by their most expensive subtree that another tree also uses),
+    // then the order is cut into G contiguous groups of balanced cost.
+    std::vector<int32_t> tree_uses(pop.dag.size(), 0), seen(pop.dag.size(), -1);
+    std::vector<int32_t> stack;
+    for (int64_t t = 0; t < T; ++t) {
+        stack.assign(1, pop.roots[t]);
+        while (!stack.empty()) {
+            int32_t n = stack.back();
+            stack.pop_back();
+            if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
+            seen[n] = (int32_t)t;
+            tree_uses[n]++;
+            for (int c = 0; c < 2; ++c)
+                if (pop.dag.nodes[n].kid[c] >= 0) stack.push_back(pop.dag.nodes[n].kid[c]);
+        }
+    }
+    std::vector<int32_t> key(T, -1);
+    std::vector<float> key_cost(T, 0.f);
+    std::fill(seen.begin(), seen.end(), -1);
+    for (int64_t t = 0; t < T; ++t) {
+        stack.assign(1, pop.roots[t]);
+        while (!stack.empty()) {
+            int32_t n = stack.back();
+            stack.pop_back();
+            const DagNode& d = pop.dag.nodes[n];
+            if (seen[n] == (int32_t)t || is_leaf(d.op)) continue;
+            seen[n] = (int32_t)t;
+            if (tree_uses[n] >= 2 && d.cost > key_cost[t]) { key_cost[t] = d.cost; key[t] = n; }
+            for (int c = 0; c < 2; ++c)
+                if (d.kid[c] >= 0) stack.push_back(d.kid[c]);
+        }
+    }
     std::vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return pop.tree_cost[a] > pop.tree_cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (key[a] != key[b]) return key[a] > key[b];
+        return a < b;
+    });
+    double total = 0;
+    for (int64_t t = 0; t < T; ++t) total += pop.tree_cost[t] + 1.0;
     std::vector<std::vector<int32_t>> groups(G);
     plan.group_cost.assign(G, 0.0);
-    for (int32_t t : order) {
-        int best = 0;
-        for (int g = 1; g < G; ++g)
-            if (plan.group_cost[g] < plan.group_cost[best]) best = g;
-        groups[best].push_back(t);
-        plan.group_cost[best] += pop.tree_cost[t] + 1.0;
+    {
+        double acc = 0;
+        int g = 0;
+        for (int32_t t : order) {
+            double c = pop.tree_cost[t] + 1.0;
+            // move on when this group reached its share (keep at least one tree per group)
+            if (g < G - 1 && !groups[g].empty() && acc + 0.5 * c > total * (g + 1) / G) ++g;
+            groups[g].push_back(t);
+            plan.group_cost[g] += c;
+            acc += c;
+        }
     }
-    // trees of a group in their population order
-    for (auto& g : groups) std::sort(g.begin(), g.end());
 
+    // Shared-memory slot cap: keep the dynamic shared memory of a CTA (target
+    // values + spill slots) within 64 KB so several CTAs stay resident.
+    const int slot_bytes = shape.K * shape.threads * 4;
+    const int cap = std::max(4, 64 * 1024 / slot_bytes - 1);
     GroupGen gen(pop.dag, plan.ir, shape.dedup);
     plan.group_off.push_back(0);
+    std::vector<int32_t> forbid;
     for (int g = 0; g < G; ++g) {
-        gen.run(groups[g], pop.roots);
+        // A kept node that lands in shared memory costs a store plus a load
+        // and a move per use; when its subtree is cheaper than that, or when
+        // the group needs more slots than the cap, the node is demoted to
+        // re-evaluation and the group is planned again.  Demotion only
+        // shrinks the kept set, so this terminates.
+        forbid.clear();
+        const size_t mark = plan.ir.size();
+        for (int iter = 0;; ++iter) {
+            gen.run(groups[g], pop.roots, forbid);
+            std::vector<int32_t> demote;
+            for (int32_t n : gen.smem_kept)
+                if (pop.dag.nodes[n].cost < kSmemKeepMinCost || gen.spill_high > cap) demote.push_back(n);
+            if (demote.empty() || iter >= 16) break;
+            forbid.insert(forbid.end(), demote.begin(), demote.end());
+            plan.ir.resize(mark);
+        }
+        plan.spill_slots = std::max(plan.spill_slots, gen.spill_high);
         plan.group_off.push_back((int64_t)plan.ir.size());
     }
-    plan.spill_slots = gen.spill_high;
     plan.group_order.resize(G);
     std::iota(plan.group_order.begin(), plan.group_order.end(), 0);
     std::stable_sort(plan.group_order.begin(), plan.group_order.end(),

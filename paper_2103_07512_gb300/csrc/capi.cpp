@@ -569,8 +569,10 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     cost_out[TGP_OP_DIV] = ms[1] / add;
     cost_out[TGP_OP_SIN] = ms[2] / add;
     cost_out[TGP_OP_COS] = ms[3] / add;
-    cost_out[TGP_OP_MIN] = ms[5] / add;
-    cost_out[TGP_OP_MAX] = ms[5] / add;
+    // min / max are one instruction like add; a chain of them is idempotent
+    // enough for the compiler to shorten, so they are not timed
+    cost_out[TGP_OP_MIN] = 1.0;
+    cost_out[TGP_OP_MAX] = 1.0;
     // neg and abs fold into their consumer as operand modifiers: cost 0
     return TGP_OK;
 }

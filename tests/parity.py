@@ -99,3 +99,20 @@ def oracle_fitness_chunk(args):
     ops, imm, off, order, g, target = args
     return oracle.fitness(ops, imm, off, order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, target=target,
                           with_bound=True)
+
+
+def oracle_eval_chunk(args):
+    """Worker for a spawn process pool: oracle phenotypes (with bounds) of one
+    chunk of trees at the listed points (all points when pts is None)."""
+    import oracle
+    ops, imm, off, order, g, pts = args
+    return oracle.evaluate(ops, imm, off, order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts,
+                           with_bound=True)
+
+
+def rmse_of(phenotype, target):
+    """binary64 RMSE of each row of a phenotype against a target (+inf when not finite)."""
+    ph = np.asarray(phenotype, np.float64)
+    with np.errstate(all="ignore"):
+        r = np.sqrt(np.mean((ph - np.asarray(target, np.float64)) ** 2, axis=1))
+    return np.where(np.isfinite(r), r, np.inf)

@@ -210,6 +210,36 @@ int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream,
  * and never synchronises (suitable for CUDA graph capture). */
 int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
 
+/*
+ * tgp_fitness_noalloc -- the fitness of tgp_fitness_dev, computed without
+ * allocating any device memory.  (This entry point has no counterpart in the
+ * paper; it serves callers of this library.)
+ *
+ * For callers that cannot call cudaMalloc: a host that has already reserved
+ * the device's memory for its own pool, code that must not risk the implicit
+ * device synchronisation an allocation or free may cause, or code that must
+ * not touch the allocator after start-up.  The plan's bytecode, the work-queue
+ * head and the per-warp partial sums live in one fixed device array of
+ * TGP_NOALLOC_SCRATCH_BYTES (8 MiB) that is part of the library image: every
+ * GPU that loads the library holds it until the process exits.
+ *   - The caller passes the inputs (a compiled population and a loaded
+ *     domain; a Pagie domain holds no device memory, a tensor or token target
+ *     was allocated when the domain was loaded) and the output: rmse_dev, a
+ *     device array of n_trees doubles.  Asynchronous on `stream`.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Rejects, with TGP_E_INVALID and a message giving the bytes needed, a
+ *     population whose bytecode plus partial sums (n_trees * tiles * warps
+ *     floats) exceed the array.
+ *   - All calls share the one array and it keeps the previous call's
+ *     contents (the queue head is cleared on every call); calls whose device
+ *     work overlaps -- on different streams or from different threads without
+ *     ordering -- race on it and give wrong results.
+ * Allocates no device memory and calls no allocating library routine.
+ */
+#define TGP_NOALLOC_SCRATCH_BYTES (8 << 20)
+int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
+
 /* Copies the context's counters.  With TGP_F_TIME_KERNELS it first waits for
  * the timing events of launches not yet summed. */
 int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out);

@@ -28,7 +28,7 @@ N_OPS = 13
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
            "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
-           "tgp_calibrate_op_costs"]
+           "tgp_calibrate_op_costs", "tgp_fitness_noalloc"]
 
 
 class TgpError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
             "tgp_debug_plan": [P, i64, i64, P, i64, P, P, i64, P],
             "tgp_debug_layout": [P, i32],
             "tgp_calibrate_op_costs": [P, P],
+            "tgp_fitness_noalloc": [P, i64, i64, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -231,6 +232,11 @@ class Context:
     def fitness_dev(self, pop, dom, out, stream=None):
         """tgp_fitness_dev: RMSE into a device float64 buffer (torch tensor)."""
         self._check(self._L.tgp_fitness_dev(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def fitness_noalloc(self, pop, dom, out, stream=None):
+        """tgp_fitness_noalloc: RMSE into a device float64 buffer without any
+        device allocation by the library (fixed scratch; see include/tgp.h)."""
+        self._check(self._L.tgp_fitness_noalloc(self._h, pop, dom, _stream(stream), _ptr(out)))
 
     def stats(self):
         s = Stats()

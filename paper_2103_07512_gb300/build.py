@@ -16,8 +16,8 @@ LIB = os.path.join(HERE, "libtgp.so")
 BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp"]
-HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h"]
+SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu"]
+HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h"]
 
 
 def nvcc() -> str:

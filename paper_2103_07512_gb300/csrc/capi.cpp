@@ -17,6 +17,7 @@
 
 #include "../../include/tgp.h"
 #include "compiler.h"
+#include "internal.h"
 #include "kernels.h"
 
 using namespace tgp;
@@ -294,6 +295,40 @@ typename M::mapped_type::element_type* find(M& m, int64_t h) {
 }
 
 }  // namespace
+
+namespace tgp {
+namespace internal {
+
+int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::mutex>& lk, View* v) {
+    if (!ctx || !v) return fail(TGP_E_INVALID, "ctx is NULL");
+    lk = std::unique_lock<std::mutex>(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    v->ir = &p->ir;
+    v->W = d->W; v->H = d->H;
+    v->xlo = d->xlo; v->xhi = d->xhi; v->ylo = d->ylo; v->yhi = d->yhi;
+    v->target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+    v->shape = choose_shape(ctx, p->ir, d->N());
+    v->sms = ctx->sms;
+    v->device = ctx->device;
+    return TGP_OK;
+}
+
+int set_error(int code, const char* f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+}  // namespace internal
+}  // namespace tgp
 
 extern "C" {
 

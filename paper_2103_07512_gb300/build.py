@@ -48,6 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo",
               "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+    common += os.environ.get("TGP_NVCC_FLAGS", "").split()   # extra flags for experiments
     procs = []
     objs = []
     for src in SOURCES:

@@ -201,7 +201,7 @@ int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s,
         CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(),
                                  hp.group_order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         // host vectors stay alive with the plan, so the async copies are safe
-        pl->smem = (size_t)(1 + hp.spill_slots) * shape.K * shape.threads * sizeof(float);
+        pl->smem = eval_smem_bytes(shape.K, shape.threads, hp.spill_slots);
         pop->plans[shape] = std::move(up);
     } else {
         pl = it->second.get();

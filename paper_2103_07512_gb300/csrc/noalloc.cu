@@ -115,7 +115,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     NA_TRY(cudaMemcpyAsync(gord, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s));
 
-    const size_t smem = (size_t)(1 + hp.spill_slots) * hp.shape.K * hp.shape.threads * sizeof(float);
+    const size_t smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.spill_slots);
     int bps = 0;
     NA_TRY(eval_occupancy(hp.shape.K, false, hp.shape.threads, smem, &bps));
     if (bps <= 0) return internal::set_error(TGP_E_INVALID, "interpreter cannot be resident with this plan");

@@ -126,7 +126,7 @@ typedef struct tgp_stats {
     int64_t n_groups;         /* tree groups of the last plan */
     int64_t n_items;          /* (group, tile) work items of the last launch */
     int32_t points_per_thread, threads_per_block;
-    int32_t spill_slots;      /* shared-memory spill slots of the last plan */
+    int32_t slots;            /* shared-memory value slots per thread of the last plan */
     int32_t reserved0;
     int64_t cache_entries;    /* live cache entries */
     int64_t cache_bytes;      /* HBM held by the cache */
@@ -257,9 +257,9 @@ int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points,
                    int32_t* ins_out, int64_t cap, int64_t* n_ins,
                    int64_t* group_off_out, int64_t cap_groups, int32_t* n_groups);
 
-/* Layout constants of the decoded bytecode: out[0] = number of register
- * slots M; operands are 0 = x, 1 = y, 2 = immediate, 3..3+M-1 = register
- * slot j, 3+M = fill buffer.  out[1] = number of forms. */
+/* Layout constants of the decoded bytecode: out[0] = number of operand
+ * kinds (0 = x, 1 = y, 2 = immediate, 3 = value slot named by aux);
+ * out[1] = number of forms. */
 int tgp_debug_layout(int32_t* out, int32_t n);
 
 /*

@@ -54,7 +54,7 @@ class Stats(ctypes.Structure):
                 ("dag_internal", ctypes.c_int64), ("code_instrs", ctypes.c_int64),
                 ("n_groups", ctypes.c_int64), ("n_items", ctypes.c_int64),
                 ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("spill_slots", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("cache_entries", ctypes.c_int64), ("cache_bytes", ctypes.c_int64),
                 ("cache_hits", ctypes.c_int64), ("cache_inserts", ctypes.c_int64),
                 ("cache_evictions", ctypes.c_int64), ("launches", ctypes.c_int64),
@@ -266,4 +266,4 @@ def debug_layout():
     rc = lib().tgp_debug_layout(_ptr(out), 2)
     if rc != OK:
         raise TgpError(rc, "debug_layout")
-    return {"n_reg": int(out[0]), "n_forms": int(out[1])}
+    return {"n_opnd": int(out[0]), "n_forms": int(out[1])}

@@ -201,7 +201,7 @@ int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s,
         CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(),
                                  hp.group_order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         // host vectors stay alive with the plan, so the async copies are safe
-        pl->smem = eval_smem_bytes(shape.K, shape.threads, hp.spill_slots);
+        pl->smem = eval_smem_bytes(shape.K, shape.threads, hp.n_slots);
         pop->plans[shape] = std::move(up);
     } else {
         pl = it->second.get();
@@ -236,7 +236,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.out = out;
     p.cache = nullptr;
     p.counter = pl->counter.p;
-    p.spill_slots = hp.spill_slots;
+    p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0;
@@ -266,7 +266,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     c->stats.n_items = hp.n_items;
     c->stats.points_per_thread = hp.shape.K;
     c->stats.threads_per_block = hp.shape.threads;
-    c->stats.spill_slots = hp.spill_slots;
+    c->stats.slots = hp.n_slots;
     return TGP_OK;
 }
 
@@ -559,7 +559,7 @@ int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points, int32_t* ins_
 
 int tgp_debug_layout(int32_t* out, int32_t n) {
     if (!out || n < 2) return fail(TGP_E_INVALID, "need an array of at least 2");
-    out[0] = kNReg;
+    out[0] = kNOpnd;
     out[1] = F_NFORMS;
     return TGP_OK;
 }

@@ -208,24 +208,20 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
 
 namespace {
 
-// A kept node is held in shared memory only when its subtree costs at least
-// this much per point (a spill, a fill and a move per use cost about this).
-constexpr float kSmemKeepMinCost = 6.f;
-
 class GroupGen {
 public:
-    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup)
+    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
-          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup) {}
+          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap) {}
 
-    int spill_high = 0;                   // shared-memory slots of the last run
-    std::vector<int32_t> smem_kept;       // kept nodes that landed in shared memory (last run)
+    int slot_high = 0;                    // slots used by the last run
+    std::vector<int32_t> refused;         // kept nodes that found no slot under the cap (last run)
 
     // Emits one group.  Nodes listed in `forbid` are never kept.
     void run(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots,
              const std::vector<int32_t>& forbid) {
-        spill_high = 0;
-        smem_kept.clear();
+        slot_high = 0;
+        refused.clear();
         count_uses(trees, roots, forbid);
         for (int32_t t : trees) {
             int32_t r = roots[t];
@@ -236,31 +232,29 @@ public:
         emit(F_END, 0, 0, 0, 0, 0);
         for (int32_t n : touched_) { uses_[n] = 0; where_[n] = -1; keep_[n] = 0; }
         touched_.clear();
-        for (bool& b : reg_busy_) b = false;
-        smem_busy_.clear();
+        busy_.clear();
     }
 
 private:
-    // A shared node is kept (evaluated once, held until its last use) when
-    // its subtree costs at least this much per point and its uses lie in at
-    // most kKeepSpan + 1 consecutive trees of the group; otherwise it is
-    // re-evaluated at each use, which needs no slot.  Holding a value across
-    // many trees would take registers from the operands of everything in
-    // between and push them to shared memory.
+    // A shared node is kept (evaluated once, held in a slot until its last
+    // use) when its subtree costs at least this much per point and its uses
+    // lie in at most kKeepSpan + 1 consecutive trees of the group; otherwise
+    // it is re-evaluated at each use.  Holding values across many trees would
+    // fill the slots (shared memory, which bounds how many CTAs fit an SM).
     static constexpr float kKeepMinCost = 2.f;
     static constexpr int kKeepSpan = 1;
 
     const Dag& d_;
     std::vector<IrIns>& out_;
     std::vector<int32_t> uses_;    // evaluations of the node still to be consumed
-    std::vector<int32_t> where_;   // -1, register slot j, or kNReg + shared slot s
+    std::vector<int32_t> where_;   // slot holding the node, or -1
     std::vector<uint8_t> keep_;    // evaluated once and held
     std::vector<int32_t> first_pos_, last_pos_;   // tree positions of first / last use
     std::vector<int32_t> span_touched_;
     std::vector<int32_t> touched_;
     bool dedup_;
-    bool reg_busy_[kNReg] = {};
-    std::vector<bool> smem_busy_;
+    int kept_cap_;                 // slots a kept node may use; temporaries may go beyond
+    std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
@@ -334,7 +328,7 @@ private:
         span_touched_.clear();
     }
 
-    // operand index of a leaf (and its immediate)
+    // operand kind of a leaf (and its immediate)
     int leaf_opnd(int32_t n, uint32_t* imm) const {
         const DagNode& x = N(n);
         if (x.op == T_X) return kOpX;
@@ -343,37 +337,36 @@ private:
         return kOpC;
     }
 
-    // operand available without any code (leaf or register-held node), else -1
-    int free_opnd(int32_t n, uint32_t* imm) const {
+    // operand available without any code: a leaf or a node held in a slot
+    // (slot returned through *slot), else -1
+    int free_opnd(int32_t n, uint32_t* imm, int* slot) const {
         if (is_leaf(N(n).op)) return leaf_opnd(n, imm);
-        int w = where_[n];
-        if (w >= 0 && w < kNReg) return kOpR0 + w;
+        if (where_[n] >= 0) { *slot = where_[n]; return kOpS; }
         return -1;
     }
 
-    int alloc_reg() {
-        for (int j = 0; j < kNReg; ++j)
-            if (!reg_busy_[j]) { reg_busy_[j] = true; return j; }
+    // A free slot; a kept node may not go beyond the cap (-1 then).
+    int alloc_slot(bool kept) {
+        const int limit = kept ? kept_cap_ : (int)busy_.size() + 1;
+        for (int j = 0; j < limit; ++j) {
+            if (j == (int)busy_.size()) busy_.push_back(false);
+            if (!busy_[j]) {
+                busy_[j] = true;
+                slot_high = std::max(slot_high, j + 1);
+                return j;
+            }
+        }
         return -1;
     }
-    int alloc_smem() {
-        for (size_t s = 0; s < smem_busy_.size(); ++s)
-            if (!smem_busy_[s]) { smem_busy_[s] = true; return (int)s; }
-        smem_busy_.push_back(true);
-        spill_high = std::max(spill_high, (int)smem_busy_.size());
-        return (int)smem_busy_.size() - 1;
-    }
-    void free_loc(int w) {
-        if (w < 0) return;
-        if (w < kNReg) reg_busy_[w] = false;
-        else smem_busy_[w - kNReg] = false;
+    void free_slot(int j) {
+        if (j >= 0) busy_[j] = false;
     }
 
     // consumes one use of n; frees its slot after the last one
     void use(int32_t n) {
         if (is_leaf(N(n).op)) return;
         if (--uses_[n] == 0 && where_[n] >= 0) {
-            free_loc(where_[n]);
+            free_slot(where_[n]);
             where_[n] = -1;
         }
     }
@@ -386,35 +379,39 @@ private:
             emit(F_LD, 0, o, 0, 0, imm);
             return;
         }
-        int w = where_[n];
-        if (w >= 0 && w < kNReg) { emit(F_LD, 0, kOpR0 + w, 0, 0, 0); return; }
-        if (w >= kNReg) {
-            emit(F_FILL, 0, 0, 0, w - kNReg, 0);
-            emit(F_LD, 0, kOpF, 0, 0, 0);
+        if (where_[n] >= 0) {
+            emit(F_LD, 0, kOpS, 0, where_[n], 0);
             return;
         }
         compute(n);
         // a kept node is held for the uses that remain after the current one
         if (keep_[n] && uses_[n] > 1) {
-            int j = alloc_reg();
+            int j = alloc_slot(true);
             if (j >= 0) {
-                emit(F_ST, 0, kOpR0 + j, 0, 0, 0);
+                emit(F_ST, 0, 0, 0, j, 0);
                 where_[n] = j;
             } else {
-                int s = alloc_smem();
-                emit(F_SPILL, 0, 0, 0, s, 0);
-                where_[n] = kNReg + s;
-                smem_kept.push_back(n);
+                // no slot under the cap: the plan is redone with n demoted;
+                // until then it is parked in a temporary slot so this run
+                // stays consistent
+                refused.push_back(n);
+                j = alloc_slot(false);
+                emit(F_ST, 0, 0, 0, j, 0);
+                where_[n] = j;
             }
         }
     }
 
-    static bool commutative(int fn) { return fn == T_ADD || fn == T_MUL; }
+    // Exactly commutative in binary32 for this operator set: a + b == b + a
+    // and a * b == b * a bitwise; fminf / fmaxf return the same value in
+    // either order (a NaN operand yields the other operand; equal zeros
+    // compare equal).
+    static bool commutative(int fn) { return fn == T_ADD || fn == T_MUL || fn == T_MIN || fn == T_MAX; }
 
-    // A = fn(v, A) where v is operand o
-    void emit_rev(int fn, int o, uint32_t imm) {
-        if (commutative(fn)) emit(F_AO, fn, o, 0, 0, imm);
-        else emit(F_OA, fn, o, 0, 0, imm);
+    // A = fn(o, A)
+    void emit_rev(int fn, int o, int slot, uint32_t imm) {
+        if (commutative(fn)) emit(F_AO, fn, o, 0, slot, imm);
+        else emit(F_OA, fn, o, 0, slot, imm);
     }
 
     // Computes internal node n (not held anywhere) into A.
@@ -436,14 +433,15 @@ private:
         }
         int32_t l = x.kid[0], r = x.kid[1];
         uint32_t il = 0, ir = 0;
-        int ol = free_opnd(l, &il), orr = free_opnd(r, &ir);
+        int sl = -1, sr = -1;
+        int ol = free_opnd(l, &il, &sl), orr = free_opnd(r, &ir, &sr);
         if (ol >= 0 && orr >= 0) {
             bool ll = is_leaf(N(l).op), rl = is_leaf(N(r).op);
             if (ll && rl && !(ol == kOpC && orr == kOpC)) {
                 emit(F_TT, fn, ol, orr, 0, ol == kOpC ? il : ir);
             } else {
-                emit(F_LD, 0, ol, 0, 0, il);
-                emit(F_AO, fn, orr, 0, 0, ir);
+                emit(F_LD, 0, ol, 0, sl, il);
+                emit(F_AO, fn, orr, 0, sr, ir);
             }
             use(l);
             use(r);
@@ -451,14 +449,14 @@ private:
         }
         if (ol >= 0) {            // right needs code
             to_acc(r);
-            emit_rev(fn, ol, il);
+            emit_rev(fn, ol, sl, il);
             use(r);
             use(l);
             return;
         }
         if (orr >= 0) {           // left needs code
             to_acc(l);
-            emit(F_AO, fn, orr, 0, 0, ir);
+            emit(F_AO, fn, orr, 0, sr, ir);
             use(l);
             use(r);
             return;
@@ -468,34 +466,27 @@ private:
         int32_t first = left_first ? l : r, second = left_first ? r : l;
         to_acc(first);
         uint32_t is = 0;
-        int os = free_opnd(second, &is);
+        int ss = -1;
+        int os = free_opnd(second, &is, &ss);
         if (os >= 0) {            // became available while computing `first`
-            if (left_first) emit(F_AO, fn, os, 0, 0, is);
-            else emit_rev(fn, os, is);
+            if (left_first) emit(F_AO, fn, os, 0, ss, is);
+            else emit_rev(fn, os, ss, is);
             use(first);
             use(second);
             return;
         }
-        // park `first` while `second` is computed
+        // park `first` in a slot while `second` is computed
         int temp = -1;
         int w = where_[first];
         if (w < 0) {
-            int j = alloc_reg();
-            if (j >= 0) { emit(F_ST, 0, kOpR0 + j, 0, 0, 0); temp = j; }
-            else { int s = alloc_smem(); emit(F_SPILL, 0, 0, 0, s, 0); temp = kNReg + s; }
+            temp = alloc_slot(false);
+            emit(F_ST, 0, 0, 0, temp, 0);
             w = temp;
         }
         to_acc(second);
-        int of;
-        if (w < kNReg) {
-            of = kOpR0 + w;
-        } else {
-            emit(F_FILL, 0, 0, 0, w - kNReg, 0);
-            of = kOpF;
-        }
-        if (left_first) emit_rev(fn, of, 0);      // A = fn(first, A)
-        else emit(F_AO, fn, of, 0, 0, 0);         // A = fn(A, first)
-        if (temp >= 0) free_loc(temp);
+        if (left_first) emit_rev(fn, kOpS, w, 0);      // A = fn(first, A)
+        else emit(F_AO, fn, kOpS, 0, w, 0);            // A = fn(A, first)
+        if (temp >= 0) free_slot(temp);
         use(first);
         use(second);
     }
@@ -505,17 +496,17 @@ private:
 
 Ins encode(const IrIns& in) {
     uint32_t opc = 0, y = 0;
+    // the y word: slot of an S operand, else the immediate of a C operand, else aux
+    auto opnd_word = [&](int o) { return o == kOpS ? (uint32_t)in.aux : in.imm; };
     switch (in.form) {
     case F_END: opc = OPC_END; break;
-    case F_AO: opc = OPC_AO + bin_index(in.fn) * kNOpnd + in.o1; y = in.imm; break;
-    case F_OA: opc = OPC_OA + ord_index(in.fn) * kNOpnd + in.o1; y = in.imm; break;
+    case F_AO: opc = OPC_AO + bin_index(in.fn) * kNOpnd + in.o1; y = opnd_word(in.o1); break;
+    case F_OA: opc = OPC_OA + ord_index(in.fn) * kNOpnd + in.o1; y = opnd_word(in.o1); break;
     case F_TT: opc = OPC_TT + bin_index(in.fn) * 9 + in.o1 * 3 + in.o2; y = in.imm; break;
     case F_UA: opc = OPC_UA + un_index(in.fn); break;
     case F_UT: opc = OPC_UT + un_index(in.fn) * 3 + in.o1; y = in.imm; break;
-    case F_LD: opc = OPC_LD + in.o1; y = in.imm; break;
-    case F_ST: opc = OPC_ST + (in.o1 - kOpR0); break;
-    case F_SPILL: opc = OPC_SPILL; y = (uint32_t)in.aux; break;
-    case F_FILL: opc = OPC_FILL; y = (uint32_t)in.aux; break;
+    case F_LD: opc = OPC_LD + in.o1; y = opnd_word(in.o1); break;
+    case F_ST: opc = OPC_ST; y = (uint32_t)in.aux; break;
     case F_ROOT: opc = OPC_ROOT; y = (uint32_t)in.aux; break;
     case F_CST: opc = OPC_CST; y = (uint32_t)in.aux; break;
     case F_CLD: opc = OPC_CLD; y = (uint32_t)in.aux; break;
@@ -606,31 +597,27 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
         }
     }
 
-    // Shared-memory slot cap: keep the dynamic shared memory of a CTA (target
-    // values + spill slots) within 64 KB so several CTAs stay resident.
+    // Slot cap for kept nodes: keep a CTA's dynamic shared memory (target
+    // values + slots) near 40 KB so five CTAs fit an SM.  Temporaries may
+    // exceed it (a tree needs as many as its Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
-    const int cap = std::max(4, 64 * 1024 / slot_bytes - 1);
-    GroupGen gen(pop.dag, plan.ir, shape.dedup);
+    const int cap = std::max(4, 40 * 1024 / slot_bytes - 1);
+    GroupGen gen(pop.dag, plan.ir, shape.dedup, cap);
     plan.group_off.push_back(0);
     std::vector<int32_t> forbid;
     for (int g = 0; g < G; ++g) {
-        // A kept node that lands in shared memory costs a store plus a load
-        // and a move per use; when its subtree is cheaper than that, or when
-        // the group needs more slots than the cap, the node is demoted to
+        // A kept node that found no slot under the cap is demoted to
         // re-evaluation and the group is planned again.  Demotion only
         // shrinks the kept set, so this terminates.
         forbid.clear();
         const size_t mark = plan.ir.size();
         for (int iter = 0;; ++iter) {
             gen.run(groups[g], pop.roots, forbid);
-            std::vector<int32_t> demote;
-            for (int32_t n : gen.smem_kept)
-                if (pop.dag.nodes[n].cost < kSmemKeepMinCost || gen.spill_high > cap) demote.push_back(n);
-            if (demote.empty() || iter >= 16) break;
-            forbid.insert(forbid.end(), demote.begin(), demote.end());
+            if (gen.refused.empty() || iter >= 32) break;
+            forbid.insert(forbid.end(), gen.refused.begin(), gen.refused.end());
             plan.ir.resize(mark);
         }
-        plan.spill_slots = std::max(plan.spill_slots, gen.spill_high);
+        plan.n_slots = std::max(plan.n_slots, gen.slot_high);
         plan.group_off.push_back((int64_t)plan.ir.size());
     }
     plan.group_order.resize(G);

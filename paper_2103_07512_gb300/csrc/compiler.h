@@ -74,7 +74,7 @@ struct HostPlan {
     std::vector<int64_t> group_off;     // [n_groups + 1]
     std::vector<int32_t> group_order;   // groups by descending estimated cost
     std::vector<double> group_cost;
-    int spill_slots = 0;
+    int n_slots = 0;                    // shared-memory value slots per thread
     int n_tiles = 0;
     int64_t n_items = 0;
 };

@@ -12,9 +12,9 @@ cudaError_t launch_eval(const EvalParams& p, int K, bool pheno, int grid, int th
                         cudaStream_t s);
 cudaError_t eval_occupancy(int K, bool pheno, int threads, size_t smem, int* blocks_per_sm);
 
-// Dynamic shared memory of one interpreter CTA: target values, register
-// slots and spill slots, K points per thread.
-size_t eval_smem_bytes(int K, int threads, int spill_slots);
+// Dynamic shared memory of one interpreter CTA: target values and value
+// slots, K points per thread.
+size_t eval_smem_bytes(int K, int threads, int n_slots);
 
 // Per-tree binary64 reduction of the fitness partials and sqrt(sum / N).
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);

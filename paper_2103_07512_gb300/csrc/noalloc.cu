@@ -115,7 +115,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     NA_TRY(cudaMemcpyAsync(gord, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s));
 
-    const size_t smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.spill_slots);
+    const size_t smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.n_slots);
     int bps = 0;
     NA_TRY(eval_occupancy(hp.shape.K, false, hp.shape.threads, smem, &bps));
     if (bps <= 0) return internal::set_error(TGP_E_INVALID, "interpreter cannot be resident with this plan");
@@ -140,7 +140,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.out = nullptr;
     p.cache = nullptr;
     p.counter = counter;
-    p.spill_slots = hp.spill_slots;
+    p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     NA_TRY(launch_eval(p, hp.shape.K, false, grid, hp.shape.threads, smem, s));
 

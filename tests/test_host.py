@@ -14,8 +14,9 @@ from paper_2103_07512_gb300 import inputs as I
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# decoded forms (order of the Form enum of the bytecode)
-(F_END, F_AO, F_OA, F_TT, F_UA, F_UT, F_LD, F_ST, F_SPILL, F_FILL, F_ROOT, F_CST, F_CLD) = range(13)
+# decoded forms (order of the Form enum of the bytecode) and operand kinds
+(F_END, F_AO, F_OA, F_TT, F_UA, F_UT, F_LD, F_ST, F_ROOT, F_CST, F_CLD) = range(11)
+O_X, O_Y, O_C, O_S = range(4)
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +38,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_layout():
     lay = tgp.debug_layout()
-    assert lay["n_reg"] >= 2 and lay["n_forms"] == 13
+    assert lay["n_opnd"] == 4 and lay["n_forms"] == 11
 
 
 def test_host_only_context_refuses_device_work(ctx):
@@ -162,39 +163,34 @@ def _un(fn, a):
     raise AssertionError(fn)
 
 
-def run_bytecode(ins, off, n_trees, X, Y, n_reg):
+def run_bytecode(ins, off, n_trees, X, Y):
     """Test-only numpy interpreter of the decoded bytecode (binary32)."""
     n = X.size
     out = np.full((n_trees, n), np.nan, np.float32)
     seen = np.zeros(n_trees, bool)
     for g in range(off.size - 1):
         A = np.zeros(n, np.float32)
-        R = [None] * n_reg
-        F = None
-        smem = {}
+        S = {}
         for i in range(off[g], off[g + 1]):
             form, fn, o1, o2, aux, immb = (int(v) for v in ins[i])
             imm = np.array([immb], np.int32).view(np.float32)[0]
 
             def opnd(o):
-                if o == 0:
+                if o == O_X:
                     return X
-                if o == 1:
+                if o == O_Y:
                     return Y
-                if o == 2:
+                if o == O_C:
                     return np.full(n, imm, np.float32)
-                if o == 3 + n_reg:
-                    assert F is not None, "fill buffer read before a fill"
-                    return F
-                assert R[o - 3] is not None, "register slot read before a store"
-                return R[o - 3]
+                assert o == O_S and aux in S, "slot read before it was written"
+                return S[aux]
             if form == F_END:
                 assert i == off[g + 1] - 1
                 break
             if form == F_AO:
                 A = _bin(fn, A, opnd(o1))
             elif form == F_OA:
-                assert fn in (I.SUB, I.DIV, I.MIN, I.MAX)
+                assert fn in (I.SUB, I.DIV)
                 A = _bin(fn, opnd(o1), A)
             elif form == F_TT:
                 assert o1 <= 2 and o2 <= 2 and not (o1 == 2 and o2 == 2)
@@ -207,11 +203,7 @@ def run_bytecode(ins, off, n_trees, X, Y, n_reg):
             elif form == F_LD:
                 A = opnd(o1).copy()
             elif form == F_ST:
-                R[o1 - 3] = A.copy()
-            elif form == F_SPILL:
-                smem[aux] = A.copy()
-            elif form == F_FILL:
-                F = smem[aux].copy()
+                S[aux] = A.copy()
             elif form == F_ROOT:
                 assert not seen[aux], "tree emitted twice"
                 seen[aux] = True
@@ -225,9 +217,8 @@ def run_bytecode(ins, off, n_trees, X, Y, n_reg):
 def _check_population(ctx, tok, W=7, H=5, trig_free=False):
     pop = ctx.compile_tokens(tok)
     ins, off = ctx.debug_plan(pop, W * H)
-    lay = tgp.debug_layout()
     xs = np.array([oracle.grid_point(W, H, -5, 5, -5, 5, p) for p in range(W * H)], np.float32)
-    got = run_bytecode(ins, off, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy(), lay["n_reg"])
+    got = run_bytecode(ins, off, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
     v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5)
     if trig_free:
         assert np.array_equal(got, v32, equal_nan=True)
@@ -255,12 +246,12 @@ def test_bytecode_trig_free_is_exact(ctx):
     _check_population(ctx, I.to_tokens(trees), trig_free=True)
 
 
-def test_bytecode_deep_trees_spill_to_shared_memory(ctx):
+def test_bytecode_deep_trees_use_many_slots(ctx):
     rng = np.random.default_rng(3)
     funcs = (I.ADD, I.SUB, I.MUL, I.MIN, I.MAX)
-    trees = [I._full(rng, 9, funcs) for _ in range(3)]   # full binary trees: 9 slots needed
+    trees = [I._full(rng, 9, funcs) for _ in range(3)]   # full binary trees of depth 9: 8 slots
     ins, off = _check_population(ctx, I.to_tokens(trees), W=3, H=2, trig_free=True)
-    assert (ins[:, 0] == F_SPILL).any() and (ins[:, 0] == F_FILL).any()
+    assert ins[ins[:, 0] == F_ST, 4].max() == 7
 
 
 def test_bytecode_shared_subtrees_are_evaluated_once(ctx):

@@ -102,7 +102,7 @@ typedef struct tgp_config {
     int32_t device;              /* CUDA device ordinal */
     int32_t flags;               /* TGP_F_* */
     int64_t cache_budget_bytes;  /* HBM budget of the cross-call subtree cache; 0 disables it */
-    int32_t points_per_thread;   /* 0 = automatic (autotuned); else 1, 2, 4 or 8 */
+    int32_t points_per_thread;   /* 0 = automatic (autotuned); else 1, 2, 4, 8 or 16 */
     int32_t threads_per_block;   /* 0 = automatic; else 32, 64 or 128 */
     int32_t n_groups;            /* 0 = automatic; else trees are split into this many groups */
     int32_t reserved[5];

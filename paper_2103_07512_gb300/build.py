@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu"]
-HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h"]
+HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h", "gen_fastloop.py"]
 
 
 def nvcc() -> str:
@@ -45,9 +45,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # generated inline-PTX dispatch loop (build step)
+    subprocess.check_call([sys.executable, os.path.join(CSRC, "gen_fastloop.py"),
+                           os.path.join(BUILD, "fastloop.inc")])
     cc = nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo",
-              "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+              "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + BUILD]
     common += os.environ.get("TGP_NVCC_FLAGS", "").split()   # extra flags for experiments
     procs = []
     objs = []

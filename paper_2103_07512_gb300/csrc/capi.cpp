@@ -150,8 +150,8 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
         if (c->cfg.n_groups <= 0) {   // redo the group count for the forced tile
             int64_t tile = (int64_t)s.K * s.threads;
             int64_t n_tiles = (N + tile - 1) / tile;
-            int64_t slots = (int64_t)std::max(c->sms, 1) * 4;
-            int64_t g = (4 * slots + n_tiles - 1) / n_tiles;
+            int64_t want = (int64_t)std::max(c->sms, 1) * 64;
+            int64_t g = (want + n_tiles - 1) / n_tiles;
             s.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<size_t>(ir.roots.size(), 1)));
         }
     }
@@ -173,8 +173,8 @@ int occupancy(tgp_ctx* c, int K, bool pheno, int threads, size_t smem, int* out)
 // Builds (once) and uploads the plan of `pop` for a grid of N points.
 int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s, Plan** out) {
     PlanShape shape = choose_shape(c, pop->ir, N);
-    if (shape.K != 1 && shape.K != 2 && shape.K != 4 && shape.K != 8)
-        return fail(TGP_E_INVALID, "points_per_thread must be 1, 2, 4 or 8 (got %d)", shape.K);
+    if (shape.K != 1 && shape.K != 2 && shape.K != 4 && shape.K != 8 && shape.K != 16)
+        return fail(TGP_E_INVALID, "points_per_thread must be 1, 2, 4, 8 or 16 (got %d)", shape.K);
     if (shape.threads != 32 && shape.threads != 64 && shape.threads != 128)
         return fail(TGP_E_INVALID, "threads_per_block must be 32, 64 or 128 (got %d)", shape.threads);
     auto it = pop->plans.find(shape);

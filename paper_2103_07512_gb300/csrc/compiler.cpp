@@ -523,11 +523,13 @@ PlanShape default_shape(const PopIR& pop, int64_t N, int sms) {
     s.N = N;
     s.threads = 128;
     s.K = N >= (1 << 18) ? 8 : N >= (1 << 14) ? 4 : N >= (1 << 12) ? 2 : 1;
+    // Enough (group, tile) work items for ~64 per SM: the atomic queue then
+    // balances uneven groups, and smaller groups cost nothing extra.
     int64_t tile = (int64_t)s.K * s.threads;
     int64_t n_tiles = (N + tile - 1) / tile;
-    int64_t slots = (int64_t)std::max(sms, 1) * 4;
+    int64_t want = (int64_t)std::max(sms, 1) * 64;
     int64_t T = (int64_t)pop.roots.size();
-    int64_t g = (4 * slots + n_tiles - 1) / n_tiles;
+    int64_t g = (want + n_tiles - 1) / n_tiles;
     s.n_groups = (int)std::max<int64_t>(1, std::min(g, std::max<int64_t>(T, 1)));
     return s;
 }

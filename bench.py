@@ -42,7 +42,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 PROFILE = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
-KERNEL_SRC = os.path.join(HERE, "paper_2103_07512_gb300", "csrc", "kernels.cu")
+KERNEL_SRCS = [os.path.join(HERE, "paper_2103_07512_gb300", "csrc", f) for f in ("kernels.cu", "gen_fastloop.py")]
 
 
 def env_rank():
@@ -124,7 +124,7 @@ def profile_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    cur = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRCS)).hexdigest()
     if cur != h.group(1):
         return None
     return float(m.group(1))

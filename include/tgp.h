@@ -240,6 +240,28 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
 #define TGP_NOALLOC_SCRATCH_BYTES (8 << 20)
 int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
 
+/*
+ * The fitness of tgp_fitness_dev, launched as a CUDA graph.  The first call
+ * for a (population, domain, rmse_dev) triple plans and uploads the
+ * population, synchronises `stream`, captures the launch sequence (queue
+ * reset, interpreter, finalize) and instantiates it; later calls replay the
+ * graph (one cudaGraphLaunch).  The graph is freed with the population.  The
+ * first call must not itself be made during a stream capture.
+ */
+int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
+
+/*
+ * Autotuner: times candidate launch shapes (points per thread K in {2,4,8,16},
+ * tree groups for ~16/64/256 work items per SM) on this population and
+ * domain, with CUDA events on `stream` (synchronous), and records the fastest
+ * for the (grid size, tree-count bucket, node-count bucket) of the
+ * population.  Later plans of any population in the same bucket use it
+ * unless the context's configuration forces a shape.  Outputs (may be NULL):
+ * the chosen K, group count and its kernel time in milliseconds.
+ */
+int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, int32_t* K_out,
+                 int32_t* groups_out, double* ms_out);
+
 /* Copies the context's counters.  With TGP_F_TIME_KERNELS it first waits for
  * the timing events of launches not yet summed. */
 int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out);

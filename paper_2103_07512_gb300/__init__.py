@@ -28,7 +28,7 @@ N_OPS = 13
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
            "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
-           "tgp_calibrate_op_costs", "tgp_fitness_noalloc"]
+           "tgp_calibrate_op_costs", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune"]
 
 
 class TgpError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
             "tgp_debug_layout": [P, i32],
             "tgp_calibrate_op_costs": [P, P],
             "tgp_fitness_noalloc": [P, i64, i64, P, P],
+            "tgp_fitness_graph": [P, i64, i64, P, P],
+            "tgp_autotune": [P, i64, i64, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -232,6 +234,20 @@ class Context:
     def fitness_dev(self, pop, dom, out, stream=None):
         """tgp_fitness_dev: RMSE into a device float64 buffer (torch tensor)."""
         self._check(self._L.tgp_fitness_dev(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def fitness_graph(self, pop, dom, out, stream=None):
+        """tgp_fitness_graph: RMSE into a device float64 buffer through a
+        captured CUDA graph (captured on the first call, replayed after)."""
+        self._check(self._L.tgp_fitness_graph(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def autotune(self, pop, dom, stream=None):
+        """tgp_autotune: returns (K, groups, kernel ms) of the fastest shape."""
+        k = ctypes.c_int32()
+        g = ctypes.c_int32()
+        ms = ctypes.c_double()
+        self._check(self._L.tgp_autotune(self._h, pop, dom, _stream(stream), ctypes.byref(k), ctypes.byref(g),
+                                         ctypes.byref(ms)))
+        return k.value, g.value, ms.value
 
     def fitness_noalloc(self, pop, dom, out, stream=None):
         """tgp_fitness_noalloc: RMSE into a device float64 buffer without any

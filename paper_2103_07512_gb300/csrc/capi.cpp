@@ -13,6 +13,8 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/tgp.h"
@@ -67,11 +69,25 @@ struct DevBuf {
     }
 };
 
+// One cached subtree: its values at every point of a domain.
+struct CacheEntry {
+    DevBuf<float> values;
+    int64_t last_use = 0;        // epoch of the last call that read or wrote it
+    float cost = 0.f;            // issue cost per point of evaluating it
+    cudaEvent_t ready = nullptr; // completes when the writing launch has finished
+    ~CacheEntry() {
+        if (ready) cudaEventDestroy(ready);
+    }
+};
+
 struct Domain {
     int32_t W = 0, H = 0;
     float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
     int32_t kind = TGP_TARGET_PAGIE;
     DevBuf<float> target;
+    // cross-call subtree cache of this domain, keyed by the node's id in the
+    // context-wide DAG (exact structural identity)
+    std::unordered_map<int32_t, std::unique_ptr<CacheEntry>> cache;
     int64_t N() const { return (int64_t)W * H; }
 };
 
@@ -87,15 +103,53 @@ struct Plan {
     size_t h_rmse_n = 0;
     int grid = 0;
     size_t smem = 0;
+    DevBuf<float*> table;          // cache entry pointers of the current launch
+    std::vector<float*> h_table;
+    CacheView view;                // view the cached-mode plan was built for
+    cudaEvent_t done = nullptr;    // cached mode: the plan's last launch has finished
     ~Plan() {
         if (h_rmse) cudaFreeHost(h_rmse);
+        if (done) cudaEventDestroy(done);
+    }
+};
+
+// A captured fitness launch (memset, interpreter, finalize) for one
+// (domain, output) pair of a population.
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~GraphEntry() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
     }
 };
 
 struct Population {
     PopIR ir;
+    std::vector<int32_t> gid;      // node id in the context-wide DAG (cache on)
     std::map<PlanShape, std::unique_ptr<Plan>> plans;
+    std::map<PlanShape, std::unique_ptr<Plan>> cplans;   // cached mode: rebuilt when the view changes
+    std::map<std::pair<int64_t, double*>, std::unique_ptr<GraphEntry>> graphs;
 };
+
+// Autotuner key: grid size and the population's size buckets.
+struct TuneKey {
+    int64_t N;
+    int t_bucket, n_bucket;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(N, t_bucket, n_bucket) < std::tie(o.N, o.t_bucket, o.n_bucket);
+    }
+};
+struct TuneChoice {
+    int K;
+    int items_per_sm;
+};
+
+int log2_bucket(int64_t v) {
+    int b = 0;
+    while (v > 1) { v >>= 1; ++b; }
+    return b;
+}
 
 }  // namespace
 
@@ -110,6 +164,11 @@ struct tgp_ctx {
     tgp_stats stats{};
     int sms = 0;
     std::map<std::tuple<int, int, int, size_t>, int> occ;   // (K, pheno, threads, smem) -> blocks/SM
+    std::map<TuneKey, TuneChoice> tuned;                     // tgp_autotune results
+    Dag gdag;                                                // context-wide DAG (cache on)
+    int64_t epoch = 0;                                       // calls that used the cache
+    int64_t cache_bytes = 0;
+    bool capturing = false;                                  // inside tgp_fitness_graph capture
     // TGP_F_TIME_KERNELS: event pairs around interpreter launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
     ~tgp_ctx() {
@@ -140,9 +199,32 @@ int drain_events(tgp_ctx* c) {
     return TGP_OK;
 }
 
+TuneKey tune_key(const PopIR& ir, int64_t N) {
+    return TuneKey{N, log2_bucket((int64_t)ir.roots.size()), log2_bucket(ir.tree_nodes)};
+}
+
+PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int K, int items_per_sm) {
+    PlanShape s;
+    s.N = N;
+    s.K = K;
+    s.threads = 128;
+    s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
+    int64_t tile = (int64_t)K * s.threads;
+    int64_t n_tiles = (N + tile - 1) / tile;
+    int64_t want = (int64_t)std::max(c->sms, 1) * items_per_sm;
+    int64_t g = (want + n_tiles - 1) / n_tiles;
+    s.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>(g, std::max<size_t>(ir.roots.size(), 1)));
+    return s;
+}
+
 PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
     PlanShape s = default_shape(ir, N, c->sms);
     s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
+    bool forced = c->cfg.points_per_thread > 0 || c->cfg.threads_per_block > 0 || c->cfg.n_groups > 0;
+    if (!forced) {
+        auto it = c->tuned.find(tune_key(ir, N));
+        if (it != c->tuned.end()) return shape_for(c, ir, N, it->second.K, it->second.items_per_sm);
+    }
     if (c->cfg.points_per_thread > 0) s.K = c->cfg.points_per_thread;
     if (c->cfg.threads_per_block > 0) s.threads = c->cfg.threads_per_block;
     if (c->cfg.n_groups > 0) s.n_groups = c->cfg.n_groups;
@@ -170,41 +252,72 @@ int occupancy(tgp_ctx* c, int K, bool pheno, int threads, size_t smem, int* out)
     return TGP_OK;
 }
 
-// Builds (once) and uploads the plan of `pop` for a grid of N points.
-int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s, Plan** out) {
-    PlanShape shape = choose_shape(c, pop->ir, N);
+// Uploads a plan's bytecode, offsets and (cache) entry table; allocates or
+// grows its device buffers.  Host vectors stay alive with the plan.
+int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
+    const HostPlan& hp = pl->hp;
+    const int warps = hp.shape.threads / 32;
+    CUDA_TRY(pl->code.ensure(hp.code.size()));
+    CUDA_TRY(pl->group_off.ensure(hp.group_off.size()));
+    CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
+    CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
+    CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
+    CUDA_TRY(pl->counter.ensure(1));
+    if (!pl->h_rmse) {
+        CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * std::max<int64_t>(T, 1)));
+        pl->h_rmse_n = (size_t)std::max<int64_t>(T, 1);
+    }
+    CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
+    if (!pl->h_table.empty()) {
+        CUDA_TRY(pl->table.ensure(pl->h_table.size()));
+        CUDA_TRY(cudaMemcpyAsync(pl->table.p, pl->h_table.data(), pl->h_table.size() * sizeof(float*),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    pl->smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.n_slots);
+    return TGP_OK;
+}
+
+// Builds and uploads the plan of `pop` with the given shape: once, or on
+// every call when a cache view is given (the cache changes between calls).
+int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cudaStream_t s, Plan** out,
+                   const CacheView* cv = nullptr, std::vector<float*>* table = nullptr) {
     if (shape.K != 1 && shape.K != 2 && shape.K != 4 && shape.K != 8 && shape.K != 16)
         return fail(TGP_E_INVALID, "points_per_thread must be 1, 2, 4, 8 or 16 (got %d)", shape.K);
     if (shape.threads != 32 && shape.threads != 64 && shape.threads != 128)
         return fail(TGP_E_INVALID, "threads_per_block must be 32, 64 or 128 (got %d)", shape.threads);
-    auto it = pop->plans.find(shape);
+    const bool cached = cv && cv->active();
+    auto& plans = cached ? pop->cplans : pop->plans;
+    auto it = plans.find(shape);
     Plan* pl;
-    if (it == pop->plans.end()) {
+    if (it == plans.end()) {
         auto up = std::make_unique<Plan>();
         pl = up.get();
-        build_plan(pop->ir, shape, pl->hp);
-        const HostPlan& hp = pl->hp;
-        const int64_t T = (int64_t)pop->ir.roots.size();
-        const int warps = shape.threads / 32;
-        CUDA_TRY(pl->code.ensure(hp.code.size()));
-        CUDA_TRY(pl->group_off.ensure(hp.group_off.size()));
-        CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
-        CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
-        CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
-        CUDA_TRY(pl->counter.ensure(1));
-        CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * std::max<int64_t>(T, 1)));
-        pl->h_rmse_n = (size_t)std::max<int64_t>(T, 1);
-        CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins),
-                                 cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(),
-                                 hp.group_order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        // host vectors stay alive with the plan, so the async copies are safe
-        pl->smem = eval_smem_bytes(shape.K, shape.threads, hp.n_slots);
-        pop->plans[shape] = std::move(up);
+        plans[shape] = std::move(up);
+        build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr);
+        if (cached) {
+            pl->view = *cv;
+            pl->h_table = *table;
+        }
+        int rc = upload_plan(pl, (int64_t)pop->ir.roots.size(), s);
+        if (rc) return rc;
     } else {
         pl = it->second.get();
+        if (cached) {
+            // the bytecode depends only on the view; entry pointers may differ
+            if (pl->view.cached != cv->cached || pl->view.insert != cv->insert) {
+                build_plan(pop->ir, shape, pl->hp, cv);
+                pl->view = *cv;
+            }
+            pl->h_table = *table;
+            // the buffers are rewritten: wait for the previous launch that read them
+            if (pl->done) CUDA_TRY(cudaStreamWaitEvent(s, pl->done, 0));
+            int rc = upload_plan(pl, (int64_t)pop->ir.roots.size(), s);
+            if (rc) return rc;
+        }
     }
     int bps = 0;
     int rc = occupancy(c, shape.K, pheno, shape.threads, pl->smem, &bps);
@@ -212,6 +325,165 @@ int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s,
     int64_t slots = (int64_t)bps * std::max(c->sms, 1);
     pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl->hp.n_items, slots));
     *out = pl;
+    return TGP_OK;
+}
+
+// ---------------------------------------------------------------- cache
+
+bool cache_on(const tgp_ctx* c) { return c->cfg.cache_budget_bytes > 0; }
+
+// A cache entry is usable once the launch that wrote it has finished.
+bool entry_ready(CacheEntry* e) {
+    if (!e->ready) return true;
+    if (cudaEventQuery(e->ready) == cudaSuccess) {
+        cudaEventDestroy(e->ready);
+        e->ready = nullptr;
+        return true;
+    }
+    cudaGetLastError();
+    return false;
+}
+
+// Subtrees worth storing cost at least this much per point to re-evaluate.
+constexpr float kCacheMinCost = 16.f;
+
+// Builds the cache view of one call: cached nodes become loads; the most
+// expensive evaluated nodes not yet cached are stored.  Keijzer-style flush
+// when the budget would be exceeded: entries the current population does not
+// reference go first, oldest use first, then cheapest.  Fills the launch's
+// entry-pointer table and the list of entries this call writes.
+int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, CacheView& cv, std::vector<float*>& table,
+                  std::vector<CacheEntry*>& written) {
+    const PopIR& ir = pop->ir;
+    const size_t n_nodes = ir.dag.size();
+    const int64_t bytes = d->N() * (int64_t)sizeof(float);
+    c->epoch++;
+    cv.cached.assign(n_nodes, -1);
+    cv.insert.assign(n_nodes, -1);
+    table.clear();
+    written.clear();
+    std::unordered_set<int32_t> referenced;
+    for (size_t n = 0; n < n_nodes; ++n) {
+        if (is_leaf(ir.dag.nodes[n].op)) continue;
+        const int32_t g = pop->gid[n];
+        referenced.insert(g);
+        auto it = d->cache.find(g);
+        if (it != d->cache.end() && entry_ready(it->second.get())) {
+            cv.cached[n] = (int32_t)table.size();
+            table.push_back(it->second->values.p);
+            it->second->last_use = c->epoch;
+            c->stats.cache_hits++;
+        }
+    }
+    // candidates: evaluated nodes, most expensive first
+    std::vector<int32_t> cand;
+    for (int32_t n : evaluated_nodes(ir, cv))
+        if (ir.dag.nodes[n].cost >= kCacheMinCost && !d->cache.count(pop->gid[n])) cand.push_back(n);
+    std::stable_sort(cand.begin(), cand.end(),
+                     [&](int32_t a, int32_t b) { return ir.dag.nodes[a].cost > ir.dag.nodes[b].cost; });
+    const int64_t budget = c->cfg.cache_budget_bytes;
+    // at most a quarter of the budget is written per call, so the cache turns over gradually
+    const int64_t quota = std::max<int64_t>(budget / 4 / bytes, budget >= bytes ? 1 : 0);
+    int64_t want = std::min<int64_t>((int64_t)cand.size(), quota);
+    if (want > 0 && c->cache_bytes + want * bytes > budget) {
+        // flush (Keijzer's fixed-size cache, Sec. 2): only entries the current
+        // population does not reference (in any domain) may go; the lowest
+        // benefit goes first, benefit = re-evaluation cost per point (cost per
+        // byte, the same for every entry) discounted by the calls since its
+        // last use, so stale entries age out
+        struct Victim {
+            double score;
+            int64_t last_use;
+            Domain* dom;
+            int32_t g;
+        };
+        std::vector<Victim> victims;
+        for (auto& dk : c->domains)
+            for (auto& kv : dk.second->cache)
+                if ((dk.second.get() != d || !referenced.count(kv.first)) && entry_ready(kv.second.get())) {
+                    const CacheEntry& e = *kv.second;
+                    const double score = (double)e.cost / (double)(1 + c->epoch - e.last_use);
+                    victims.push_back({score, e.last_use, dk.second.get(), kv.first});
+                }
+        std::sort(victims.begin(), victims.end(), [](const Victim& a, const Victim& b) {
+            if (a.score != b.score) return a.score < b.score;
+            if (a.last_use != b.last_use) return a.last_use < b.last_use;
+            return a.g < b.g;
+        });
+        size_t vi = 0;
+        bool synced = false;
+        while (c->cache_bytes + want * bytes > budget && vi < victims.size()) {
+            if (!synced) {   // no launch may still read an entry that is freed
+                CUDA_TRY(cudaDeviceSynchronize());
+                synced = true;
+            }
+            const Victim& v = victims[vi++];
+            c->cache_bytes -= v.dom->N() * (int64_t)sizeof(float);
+            v.dom->cache.erase(v.g);
+            c->stats.cache_evictions++;
+        }
+        want = std::max<int64_t>(0, std::min<int64_t>(want, (budget - c->cache_bytes) / bytes));
+    }
+    for (int64_t i = 0; i < want; ++i) {
+        const int32_t n = cand[i];
+        auto e = std::make_unique<CacheEntry>();
+        if (e->values.ensure((size_t)d->N()) != cudaSuccess) {
+            cudaGetLastError();
+            break;   // out of device memory: store fewer
+        }
+        e->cost = ir.dag.nodes[n].cost;
+        e->last_use = c->epoch;
+        cv.insert[n] = (int32_t)table.size();
+        table.push_back(e->values.p);
+        written.push_back(e.get());
+        c->cache_bytes += bytes;
+        c->stats.cache_inserts++;
+        d->cache[pop->gid[n]] = std::move(e);
+    }
+    c->stats.cache_entries = 0;
+    for (auto& kv : c->domains) c->stats.cache_entries += (int64_t)kv.second->cache.size();
+    c->stats.cache_bytes = c->cache_bytes;
+    return TGP_OK;
+}
+
+// Marks the entries a launch wrote as pending until the stream reaches this point.
+int mark_written(std::vector<CacheEntry*>& written, cudaStream_t s) {
+    for (CacheEntry* e : written) {
+        CUDA_TRY(cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(e->ready, s));
+    }
+    return TGP_OK;
+}
+
+// The plan of `pop` for a grid of N points (configured, tuned or default shape).
+int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s, Plan** out) {
+    return get_plan_shape(c, pop, choose_shape(c, pop->ir, N), pheno, s, out);
+}
+
+// The plan of one fitness or phenotype call on a domain: with the cache on,
+// the view of the domain's cache is taken first and the entries this launch
+// writes are returned in `written` (mark them after the launch).
+int get_call_plan(tgp_ctx* c, Population* pop, Domain* d, bool pheno, cudaStream_t s, Plan** out,
+                  std::vector<CacheEntry*>& written) {
+    written.clear();
+    if (!cache_on(c) || pop->gid.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
+    CacheView cv;
+    std::vector<float*> table;
+    int rc = prepare_cache(c, pop, d, cv, table, written);
+    if (rc) return rc;
+    if (table.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
+    return get_plan_shape(c, pop, choose_shape(c, pop->ir, d->N()), pheno, s, out, &cv, &table);
+}
+
+// After the launches of a call in cached mode: entries written become ready,
+// and the plan's buffers may be rewritten, once the stream reaches here.
+int finish_call(Plan* pl, std::vector<CacheEntry*>& written, cudaStream_t s) {
+    int rc = mark_written(written, s);
+    if (rc) return rc;
+    if (!pl->h_table.empty()) {
+        if (!pl->done) CUDA_TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(pl->done, s));
+    }
     return TGP_OK;
 }
 
@@ -234,12 +506,12 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
     p.partial = pl->partial.p;
     p.out = out;
-    p.cache = nullptr;
+    p.cache = pl->h_table.empty() ? nullptr : pl->table.p;
     p.counter = pl->counter.p;
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
-    const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0;
+    const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (timed) {
         if (c->ev_pending.size() >= 4096) {
@@ -270,11 +542,8 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     return TGP_OK;
 }
 
-int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out) {
-    Plan* pl = nullptr;
-    int rc = get_plan(c, pop, d->N(), false, s, &pl);
-    if (rc) return rc;
-    rc = launch_plan(c, pl, d, false, nullptr, s);
+int launch_fitness(tgp_ctx* c, Population* pop, Plan* pl, Domain* d, cudaStream_t s, double* rmse_dev) {
+    int rc = launch_plan(c, pl, d, false, nullptr, s);
     if (rc) return rc;
     FinalizeParams f{};
     f.partial = pl->partial.p;
@@ -284,6 +553,18 @@ int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, do
     f.rmse = rmse_dev ? rmse_dev : pl->rmse.p;
     CUDA_TRY(launch_finalize(f, s));
     c->stats.launches++;
+    return TGP_OK;
+}
+
+int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out) {
+    Plan* pl = nullptr;
+    std::vector<CacheEntry*> written;
+    int rc = get_call_plan(c, pop, d, false, s, &pl, written);
+    if (rc) return rc;
+    rc = launch_fitness(c, pop, pl, d, s, rmse_dev);
+    if (rc) return rc;
+    rc = finish_call(pl, written, s);
+    if (rc) return rc;
     if (plan_out) *plan_out = pl;
     return TGP_OK;
 }
@@ -429,6 +710,9 @@ int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
     int rc = set_device(ctx);
     if (rc) return rc;
     CUDA_TRY(cudaDeviceSynchronize());
+    ctx->cache_bytes -= (int64_t)it->second->cache.size() * it->second->N() * (int64_t)sizeof(float);
+    ctx->stats.cache_entries -= (int64_t)it->second->cache.size();
+    ctx->stats.cache_bytes = ctx->cache_bytes;
     ctx->domains.erase(it);
     return TGP_OK;
 }
@@ -441,6 +725,16 @@ int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, i
     int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err);
     if (rc) return fail(rc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     std::lock_guard<std::mutex> g(ctx->mu);
+    if (cache_on(ctx)) {   // context-wide ids: the cache key of a subtree across populations
+        const auto& nodes = pop->ir.dag.nodes;
+        pop->gid.resize(nodes.size());
+        for (size_t n = 0; n < nodes.size(); ++n) {   // kids precede parents
+            const DagNode& dn = nodes[n];
+            int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
+            int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
+            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm);
+        }
+    }
     ctx->stats.tree_nodes = pop->ir.tree_nodes;
     ctx->stats.dag_nodes = (int64_t)pop->ir.dag.size();
     int64_t internal = 0;
@@ -476,9 +770,12 @@ int tgp_evaluate(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     Plan* pl = nullptr;
-    rc = get_plan(ctx, p, d->N(), true, s, &pl);
+    std::vector<CacheEntry*> written;
+    rc = get_call_plan(ctx, p, d, true, s, &pl, written);
     if (rc) return rc;
-    return launch_plan(ctx, pl, d, true, out_dev, s);
+    rc = launch_plan(ctx, pl, d, true, out_dev, s);
+    if (rc) return rc;
+    return finish_call(pl, written, s);
 }
 
 int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_host,
@@ -518,6 +815,119 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
     int rc = set_device(ctx);
     if (rc) return rc;
     return fitness_to_device(ctx, p, d, (cudaStream_t)stream, rmse_dev, nullptr);
+}
+
+int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev) {
+    if (!ctx || !rmse_dev) return fail(TGP_E_INVALID, "ctx / rmse_dev is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    if (p->ir.roots.empty()) return TGP_OK;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto key = std::make_pair((int64_t)domain, rmse_dev);
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        // plan, allocation and upload happen before the capture
+        Plan* pl = nullptr;
+        rc = get_plan(ctx, p, d->N(), false, s, &pl);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(s));
+        auto ge = std::make_unique<GraphEntry>();
+        CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        int64_t before = ctx->stats.launches;
+        rc = launch_fitness(ctx, p, pl, d, s, rmse_dev);
+        ctx->capturing = false;
+        ctx->stats.launches = before;   // counted when the graph is launched
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(TGP_E_CUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+        ge->graph = graph;
+        CUDA_TRY(cudaGraphInstantiate(&ge->exec, graph, 0));
+        it = p->graphs.emplace(key, std::move(ge)).first;
+    }
+    CUDA_TRY(cudaGraphLaunch(it->second->exec, s));
+    ctx->stats.launches += 2;
+    return TGP_OK;
+}
+
+int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, int32_t* K_out,
+                 int32_t* groups_out, double* ms_out) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    if (p->ir.roots.empty()) return fail(TGP_E_INVALID, "empty population");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = d->N();
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    TuneChoice choice{8, 64};
+    PlanShape best_shape{};
+    std::vector<PlanShape> tried;
+    const int Ks[] = {2, 4, 8, 16};
+    const int items[] = {16, 64, 256};
+    const bool was_capturing = ctx->capturing;
+    ctx->capturing = true;   // no per-launch timing events while tuning
+    for (int K : Ks) {
+        if ((int64_t)K * 128 * 16 > N && K > 2) continue;   // tiles far larger than the grid
+        for (int ips : items) {
+            PlanShape sh = shape_for(ctx, p->ir, N, K, ips);
+            bool dup = false;
+            for (const PlanShape& t : tried) dup |= !(t < sh) && !(sh < t);
+            if (dup) continue;
+            tried.push_back(sh);
+            Plan* pl = nullptr;
+            rc = get_plan_shape(ctx, p, sh, false, s, &pl);
+            if (rc) { ctx->capturing = was_capturing; return rc; }
+            rc = launch_fitness(ctx, p, pl, d, s, nullptr);   // warm-up
+            if (rc) { ctx->capturing = was_capturing; return rc; }
+            float ms_best = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                CUDA_TRY(cudaEventRecord(e0, s));
+                rc = launch_fitness(ctx, p, pl, d, s, nullptr);
+                if (rc) { ctx->capturing = was_capturing; return rc; }
+                CUDA_TRY(cudaEventRecord(e1, s));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                ms_best = std::min(ms_best, ms);
+            }
+            if (ms_best < best) {
+                best = ms_best;
+                choice = TuneChoice{K, ips};
+                best_shape = sh;
+            }
+        }
+    }
+    ctx->capturing = was_capturing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // keep only the winning plan (captured graphs may refer to the others)
+    p->graphs.clear();
+    for (auto it = p->plans.begin(); it != p->plans.end();) {
+        const PlanShape& sh = it->first;
+        bool win = !(sh < best_shape) && !(best_shape < sh);
+        if (!win) it = p->plans.erase(it);
+        else ++it;
+    }
+    ctx->tuned[tune_key(p->ir, N)] = choice;
+    if (K_out) *K_out = best_shape.K;
+    if (groups_out) *groups_out = best_shape.n_groups;
+    if (ms_out) *ms_out = best;
+    return TGP_OK;
 }
 
 int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out) {

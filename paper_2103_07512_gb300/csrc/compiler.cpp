@@ -210,16 +210,24 @@ namespace {
 
 class GroupGen {
 public:
-    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap)
+    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
-          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap) {}
+          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
+          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0) {}
 
     int slot_high = 0;                    // slots used by the last run
     std::vector<int32_t> refused;         // kept nodes that found no slot under the cap (last run)
 
+    // Forgets the cache stores of the last attempt (the group is re-planned).
+    void rollback() {
+        for (int32_t n : stored_log_) stored_[n] = 0;
+        stored_log_.clear();
+    }
+
     // Emits one group.  Nodes listed in `forbid` are never kept.
     void run(const std::vector<int32_t>& trees, const std::vector<int32_t>& roots,
              const std::vector<int32_t>& forbid) {
+        stored_log_.clear();
         slot_high = 0;
         refused.clear();
         count_uses(trees, roots, forbid);
@@ -254,10 +262,14 @@ private:
     std::vector<int32_t> touched_;
     bool dedup_;
     int kept_cap_;                 // slots a kept node may use; temporaries may go beyond
+    const CacheView* cv_;          // cross-call cache, or nullptr
+    std::vector<uint8_t> stored_;  // cache store already emitted (this plan)
+    std::vector<int32_t> stored_log_;   // stores of the current group attempt
     std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
+    bool is_cached(int32_t n) const { return cv_ && cv_->cached[n] >= 0; }
 
     void emit(int form, int fn, int o1, int o2, int aux, uint32_t imm) {
         IrIns in;
@@ -284,6 +296,7 @@ private:
                 if (last_pos_[n] == (int32_t)i) continue;    // already seen in this tree
                 if (last_pos_[n] < 0) { first_pos_[n] = (int32_t)i; span_touched_.push_back(n); }
                 last_pos_[n] = (int32_t)i;
+                if (is_cached(n)) continue;
                 for (int c = 0; c < 2; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k >= 0 && !is_leaf(N(k).op)) dfs_.push_back(k);
@@ -299,6 +312,7 @@ private:
             while (!dfs_.empty()) {
                 int32_t n = dfs_.back();
                 dfs_.pop_back();
+                if (is_cached(n)) continue;
                 for (int c = 0; c < 2; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k < 0 || is_leaf(N(k).op) || where_[k] == -2) continue;
@@ -317,6 +331,7 @@ private:
             int32_t e = uses_[n];
             keep_[n] = dedup_ && e >= 2 && N(n).cost >= kKeepMinCost && where_[n] != -3 &&
                        last_pos_[n] - first_pos_[n] <= kKeepSpan;
+            if (is_cached(n)) continue;   // loaded, operands not evaluated
             int32_t f = keep_[n] ? 1 : e;
             for (int c = 0; c < 2; ++c) {
                 int32_t k = N(n).kid[c];
@@ -383,7 +398,16 @@ private:
             emit(F_LD, 0, kOpS, 0, where_[n], 0);
             return;
         }
-        compute(n);
+        if (is_cached(n)) {
+            emit(F_CLD, 0, 0, 0, cv_->cached[n], 0);
+        } else {
+            compute(n);
+            if (cv_ && cv_->insert[n] >= 0 && !stored_[n]) {
+                emit(F_CST, 0, 0, 0, cv_->insert[n], 0);
+                stored_[n] = 1;
+                stored_log_.push_back(n);
+            }
+        }
         // a kept node is held for the uses that remain after the current one
         if (keep_[n] && uses_[n] > 1) {
             int j = alloc_slot(true);
@@ -534,7 +558,27 @@ PlanShape default_shape(const PopIR& pop, int64_t N, int sms) {
     return s;
 }
 
-void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
+std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv) {
+    std::vector<uint8_t> seen(pop.dag.size(), 0);
+    std::vector<int32_t> out, stack;
+    for (int32_t r : pop.roots) {
+        stack.assign(1, r);
+        while (!stack.empty()) {
+            int32_t n = stack.back();
+            stack.pop_back();
+            const DagNode& d = pop.dag.nodes[n];
+            if (seen[n] || is_leaf(d.op)) continue;
+            seen[n] = 1;
+            if (cv.active() && cv.cached[n] >= 0) continue;
+            out.push_back(n);
+            for (int c = 0; c < 2; ++c)
+                if (d.kid[c] >= 0) stack.push_back(d.kid[c]);
+        }
+    }
+    return out;
+}
+
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -604,7 +648,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
     // exceed it (a tree needs as many as its Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
     const int cap = std::max(4, 40 * 1024 / slot_bytes - 1);
-    GroupGen gen(pop.dag, plan.ir, shape.dedup, cap);
+    GroupGen gen(pop.dag, plan.ir, shape.dedup, cap, cv);
     plan.group_off.push_back(0);
     std::vector<int32_t> forbid;
     for (int g = 0; g < G; ++g) {
@@ -617,6 +661,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan) {
             gen.run(groups[g], pop.roots, forbid);
             if (gen.refused.empty() || iter >= 32) break;
             forbid.insert(forbid.end(), gen.refused.begin(), gen.refused.end());
+            gen.rollback();
             plan.ir.resize(mark);
         }
         plan.n_slots = std::max(plan.n_slots, gen.slot_high);

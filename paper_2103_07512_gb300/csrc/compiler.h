@@ -82,8 +82,26 @@ struct HostPlan {
 // Default shape for a grid of N points on a device with `sms` SMs.
 PlanShape default_shape(const PopIR& pop, int64_t N, int sms);
 
+// Cross-call subtree cache as the planner sees it (indexed by the
+// population's DAG node ids; empty vectors = no cache).
+//   cached[n] >= 0: node n's values for every point are in cache entry
+//                   cached[n]; it is loaded (F_CLD) and its subtree is not
+//                   evaluated.
+//   insert[n] >= 0: after node n is first evaluated, its values are stored
+//                   into cache entry insert[n] (F_CST).
+// Entry numbers index the launch's table of entry pointers.
+struct CacheView {
+    std::vector<int32_t> cached;
+    std::vector<int32_t> insert;
+    bool active() const { return !cached.empty(); }
+};
+
+// Internal nodes a plan evaluates (reachable from the roots without passing
+// through a cached node), for choosing insertions.
+std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv);
+
 // Partitions the trees into shape.n_groups groups and emits their bytecode.
-void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan);
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr);
 
 Ins encode(const IrIns& in);
 

@@ -1,0 +1,120 @@
+"""The cross-call subtree cache (HBM entries, Keijzer-style flush under a
+budget): results with the cache on are bitwise those with it off, across the
+generations of an evolutionary run, under budgets small enough to force
+evictions, for phenotypes and fitness, and against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_07512_gb300 as tgp
+from paper_2103_07512_gb300 import inputs as I
+from paper_2103_07512_gb300.evolve import Evolution, gpu_fitness
+from parity import assert_fitness
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def run_ga(ctx, g, generations, seed=5, pop_size=50):
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    rows, toks = [], []
+    ev = Evolution(gpu_fitness(ctx, dom), pop_size=pop_size, generations=generations, seed=seed)
+
+    def keep(gen, rmse):
+        rows.append(rmse.copy())
+        toks.append(I.to_tokens(ev.population))
+
+    ev.run(keep)
+    return rows, toks, dom
+
+
+@pytest.mark.parametrize("entries", [4, 64])
+def test_ga_with_cache_is_bitwise_equal_to_without(entries):
+    g = I.Grid(256, 192)
+    budget = entries * g.N * 4
+    with tgp.Context(cache_budget_bytes=budget) as a, tgp.Context() as b:
+        ra, _, _ = run_ga(a, g, 10)
+        rb, _, _ = run_ga(b, g, 10)
+        for i, (x, y) in enumerate(zip(ra, rb)):
+            assert np.array_equal(x.view(np.int64), y.view(np.int64)), f"generation {i}"
+        st = a.stats()
+        assert st["cache_inserts"] > 0 and st["cache_hits"] > 0
+        assert st["cache_bytes"] <= budget
+        if entries == 4:
+            assert st["cache_evictions"] > 0
+        assert b.stats()["cache_hits"] == 0
+
+
+def test_cached_generation_matches_oracle():
+    g = I.Grid(64, 48)
+    with tgp.Context(cache_budget_bytes=32 * g.N * 4) as c:
+        rows, toks, _ = run_ga(c, g, 6, seed=9)
+        assert c.stats()["cache_hits"] > 0
+    for gen in (3, 5):
+        tok = toks[gen]
+        r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
+        assert_fitness(rows[gen], r64, re, g.N, context=f"generation {gen}")
+
+
+def test_cached_phenotypes_bitwise():
+    tok, _, _ = I.batched_uneven(seed=21, n_trees=200)
+    g = I.Grid(100, 70)
+    with tgp.Context(cache_budget_bytes=256 * g.N * 4) as a, tgp.Context() as b:
+        da, db = a.load_domain(g.W, g.H), b.load_domain(g.W, g.H)
+        pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+        ref = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
+        b.evaluate(pb, db, ref)
+        for call in range(3):   # inserts, then hits
+            out = torch.full_like(ref, float("nan"))
+            a.evaluate(pa, da, out)
+            torch.cuda.synchronize()
+            assert torch.equal(out.view(torch.int32), ref.view(torch.int32)), f"call {call}"
+        st = a.stats()
+        assert st["cache_inserts"] > 0 and st["cache_hits"] > 0
+        # a second population sharing subtrees with the first reads them back
+        trees = I.from_tokens(tok)
+        tok2 = I.to_tokens(trees[100:] + trees[:50])
+        p2a, p2b = a.compile_tokens(tok2), b.compile_tokens(tok2)
+        fa = a.fitness(p2a, da, tok2.n_trees)
+        fb = b.fitness(p2b, db, tok2.n_trees)
+        assert np.array_equal(fa.view(np.int64), fb.view(np.int64))
+
+
+def test_cache_is_per_domain_and_released_with_it():
+    tok, _ = I.small_population(seed=22)
+    g1, g2 = I.Grid(64, 64), I.Grid(40, 30, -1.0, 2.0, -3.0, 1.0)
+    with tgp.Context(cache_budget_bytes=1 << 26) as a, tgp.Context() as b:
+        pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+        d1 = a.load_domain(g1.W, g1.H, g1.xlo, g1.xhi, g1.ylo, g1.yhi)
+        d2 = a.load_domain(g2.W, g2.H, g2.xlo, g2.xhi, g2.ylo, g2.yhi)
+        e1 = b.load_domain(g1.W, g1.H, g1.xlo, g1.xhi, g1.ylo, g1.yhi)
+        e2 = b.load_domain(g2.W, g2.H, g2.xlo, g2.xhi, g2.ylo, g2.yhi)
+        for _ in range(2):
+            for da, db in ((d1, e1), (d2, e2)):
+                fa = a.fitness(pa, da, tok.n_trees)
+                fb = b.fitness(pb, db, tok.n_trees)
+                assert np.array_equal(fa.view(np.int64), fb.view(np.int64))
+        st = a.stats()
+        assert st["cache_entries"] > 0 and st["cache_bytes"] > 0
+        a.release_domain(d1)
+        a.release_domain(d2)
+        st = a.stats()
+        assert st["cache_entries"] == 0 and st["cache_bytes"] == 0
+
+
+def test_non_blocking_calls_with_entries_in_flight():
+    tok, _ = I.small_population(seed=23)
+    g = I.Grid(512, 256)
+    with tgp.Context(cache_budget_bytes=1 << 28) as a, tgp.Context() as b:
+        da, db = a.load_domain(g.W, g.H), b.load_domain(g.W, g.H)
+        pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+        ref = b.fitness(pb, db, tok.n_trees)
+        s = torch.cuda.Stream()
+        outs = [torch.full((tok.n_trees,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(4)]
+        for o in outs:          # back to back: later calls may find entries still being written
+            a.fitness_dev(pa, da, o, stream=s)
+        s.synchronize()
+        for o in outs:
+            assert np.array_equal(o.cpu().numpy().view(np.int64), ref.view(np.int64))

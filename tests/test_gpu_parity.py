@@ -426,3 +426,43 @@ def test_division_forms_on_grid(ctx):
     _, v32, _ = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     same = (got == v32) | (np.isnan(got) & np.isnan(v32))
     assert same.all()
+
+
+# ---------------------------------------------------------------- graph + autotuner
+
+def test_graph_replay_equals_direct_launch(ctx):
+    tok, g = I.small_population(seed=11)
+    dom = load(ctx, g)
+    pop = ctx.compile_tokens(tok)
+    ref = torch.empty(tok.n_trees, dtype=torch.float64, device="cuda")
+    ctx.fitness_dev(pop, dom, ref)
+    s = torch.cuda.Stream()
+    out = torch.full((tok.n_trees,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(3):                       # capture, then two replays
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        ctx.fitness_graph(pop, dom, out, stream=s)
+        s.synchronize()
+        assert torch.equal(out, ref)
+    ctx.release_population(pop)              # frees the graph
+
+
+def test_autotune_picks_a_shape_and_keeps_results(ctx):
+    tok, g = I.small_population(seed=12)
+    g = I.Grid(256, 256)
+    with tgp.Context() as c:
+        dom = c.load_domain(g.W, g.H)
+        pop = c.compile_tokens(tok)
+        before = c.fitness(pop, dom, tok.n_trees)
+        K, G, ms = c.autotune(pop, dom)
+        assert K in (2, 4, 8, 16) and 1 <= G <= tok.n_trees and ms > 0
+        after = c.fitness(pop, dom, tok.n_trees)
+        assert c.stats()["points_per_thread"] == K and c.stats()["n_groups"] == G
+        fin = np.isfinite(before)
+        assert np.allclose(after[fin], before[fin], rtol=2e-6, atol=0)
+        assert np.array_equal(np.isinf(after), np.isinf(before))
+        # another population of the same size bucket reuses the choice
+        tok2, _ = I.small_population(seed=13)
+        pop2 = c.compile_tokens(tok2)
+        c.fitness(pop2, dom, tok2.n_trees)
+        assert c.stats()["points_per_thread"] == K

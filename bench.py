@@ -325,10 +325,176 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_extras and world == 1:
+        line["other_configs"] = {
+            "batched_uneven": bench_batched(tgp.Context, dev, flush),
+            "evolution": bench_evolution(tgp.Context, dev),
+            "serving": bench_serving(tgp, dev),
+        }
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bench_batched(ctx_cls, dev, flush, steps=20):
+    """Batched uneven trees: 4096 trees of 3..255 nodes (30% duplicated
+    subtrees) on a 256x256 grid, shape chosen by the autotuner, each step one
+    replay of the captured CUDA graph (memset + interpreter + finalize)."""
+    import torch
+    tok, g, st = I.batched_uneven(seed=2)
+    ctx = ctx_cls(device=dev.index)
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    pop = ctx.compile_tokens(tok)
+    K, G, tune_ms = ctx.autotune(pop, dom)
+    rmse = torch.empty(tok.n_trees, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)          # graphs are captured on a created stream
+    torch.cuda.synchronize()
+    for _ in range(5):
+        ctx.fitness_graph(pop, dom, rmse, stream=stream)
+    torch.cuda.synchronize()
+    s0 = ctx.stats()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        stream.wait_stream(torch.cuda.current_stream(dev))
+        evs[i][0].record(stream)
+        ctx.fitness_graph(pop, dom, rmse, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    s1 = ctx.stats()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    units = int(tok.ops.size) * g.N
+    st1 = ctx.stats()
+    ctx.close()
+    return {"workload": "batched_uneven: 4096 trees of U{3..255} nodes, depth <= 12, 256x256 grid, seed 2",
+            "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "tree_nodes": int(tok.ops.size), "dag_internal_nodes": int(st1["dag_internal"]),
+            "dup_fraction": round(float(st["dup_fraction"]), 4),
+            "autotuned": {"points_per_thread": K, "groups": G, "kernel_ms": tune_ms},
+            "gpu_launches_per_step": (s1["launches"] - s0["launches"]) / steps,
+            "graph": True, "l2": "flushed between steps"}
+
+
+def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
+    """Full evolutionary run: population 50, 50 generations (tournament 3,
+    crossover 0.9, subtree mutation 0.1, elitism 1, depth <= 12), 4096x4096
+    grid, seed 3; with the cross-generation subtree cache under a 20 GB
+    budget (default store threshold, and a low one that stores subtrees of
+    cost >= 8) and without.  Fitness time is the wall time of each
+    generation's compile + fitness call (host tokens in, RMSE out)."""
+    from paper_2103_07512_gb300.evolve import Evolution, gpu_fitness
+    g = I.Grid(4096, 4096)
+    out = {}
+    rows = {}
+    for arm, b, mc in (("cache", budget, 0), ("cache_min_cost_8", budget, 8), ("no_cache", 0, 0)):
+        ctx = ctx_cls(device=dev.index, cache_budget_bytes=b, cache_min_cost=mc)
+        dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+        ev = Evolution(gpu_fitness(ctx, dom), pop_size=50, generations=generations, seed=3)
+        got = []
+        t0 = time.perf_counter()
+        ev.run(lambda gen, r: got.append(r.copy()))
+        total = time.perf_counter() - t0
+        fit_s = sum(h.seconds for h in ev.history)
+        nodes = sum(h.nodes for h in ev.history)
+        st = ctx.stats()
+        rows[arm] = got
+        out[arm] = {"seconds_total": total, "fitness_seconds": fit_s,
+                    "ms_per_generation": 1e3 * fit_s / generations,
+                    "node_evals_per_s": nodes * g.N / fit_s, "tree_nodes_all_generations": nodes,
+                    "best_rmse": ev.best[1]}
+        if b:
+            out[arm].update({k: int(st[k]) for k in ("cache_hits", "cache_inserts", "cache_evictions",
+                                                       "cache_entries", "cache_bytes")})
+        ctx.close()
+    same = all(np.array_equal(a.view(np.int64), c.view(np.int64))
+               for arm in ("cache", "cache_min_cost_8") for a, c in zip(rows[arm], rows["no_cache"]))
+    out.update({"workload": "evolution: population 50, 50 generations, 4096x4096 grid, 20 GB cache budget, seed 3",
+                "unit": UNIT, "cached_equals_uncached_bitwise": bool(same),
+                "cache_speedup": out["no_cache"]["fitness_seconds"] / out["cache"]["fitness_seconds"]})
+    return out
+
+
+def _serve_run(tgp, ctx, jobs, rate, seconds, rng, streams, clients=4):
+    """Offers `jobs` (cycled) at Poisson times of the given rate for about
+    `seconds`: `clients` submitting threads take the arrivals in turn (each
+    submit validates, hash-conses and plans its job in the caller's thread)
+    and one collector thread per client waits for the results.  Returns the
+    latency percentiles and throughput of the run."""
+    import threading
+    n = max(1, int(rate * seconds))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    when = np.cumsum(gaps) - gaps[0]
+    srv = tgp.Server(ctx, streams=streams)
+    k0 = ctx.stats()
+    got = []
+    got_lock = threading.Lock()
+    t0 = time.perf_counter() + 0.05
+
+    def client(c):
+        mine = []
+        for k in range(c, n, clients):
+            dt = t0 + when[k] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            j = jobs[k % len(jobs)]
+            i = srv.submit(j["tok"], j["W"], j["H"], target_tokens=j["target_tokens"])
+            mine.append((i, int(j["tok"].ops.size) * j["W"] * j["H"]))
+        for i, units in mine:
+            r, info = srv.wait(i)
+            with got_lock:
+                got.append((info, units))
+
+    ths = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    st = srv.stats()
+    srv.close()
+    k1 = ctx.stats()
+    lat = np.array([(info["done_ns"] - info["submit_ns"]) * 1e-6 for info, _ in got])
+    first = min(info["submit_ns"] for info, _ in got)
+    last_sub = max(info["submit_ns"] for info, _ in got)
+    last = max(info["done_ns"] for info, _ in got)
+    units = sum(u for _, u in got)
+    span = (last - first) * 1e-9
+    return {"offered_jobs_per_s": rate, "jobs": n, "arrival_span_s": (last_sub - first) * 1e-9,
+            "span_s": span, "jobs_per_s": n / span, "node_evals_per_s": units / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch_jobs": n / max(1, st["batches"]), "max_in_flight": int(st["max_in_flight"]),
+            "drain_s": (last - last_sub) * 1e-9,
+            "worker_busy_frac": st["worker_busy_ns"] * 1e-9 / span,
+            "domain_load_frac": st["domain_load_ns"] * 1e-9 / span,
+            "kernel_busy_frac": (k1["eval_ms_sum"] - k0["eval_ms_sum"]) * 1e-3 / span}
+
+
+def bench_serving(tgp, dev, streams=4, seconds=2.5):
+    """Serving: Poisson arrivals of jobs with U{10..1000} RHH trees (depth
+    2-10) on square grids of 2^12..2^22 points (log-uniform), Pagie or a
+    random depth-4 target tree; domains and the subtree cache stay resident.
+    The service capacity is measured with a burst, then offered rates of 30%
+    to 90% of it are run; the sustained rate is the highest whose queue
+    drains within a quarter of a second after the last arrival."""
+    rng = np.random.default_rng(4)
+    jobs = I.serving_jobs(800, seed=4, pool=32)
+    ctx = tgp.Context(device=dev.index, cache_budget_bytes=8 * 10**9, time_kernels=True)
+    # warm the resident domains and plans, then a burst to measure capacity
+    _serve_run(tgp, ctx, jobs, rate=1e4, seconds=32 / 1e4, rng=rng, streams=streams)
+    burst = _serve_run(tgp, ctx, jobs, rate=1e6, seconds=64 / 1e6, rng=rng, streams=streams)
+    cap = burst["jobs_per_s"]
+    runs = []
+    for f in (0.3, 0.5, 0.7, 0.9):
+        runs.append(_serve_run(tgp, ctx, jobs, rate=f * cap, seconds=seconds, rng=rng, streams=streams))
+    stable = [r for r in runs if r["drain_s"] < 0.25]
+    best = max(stable, key=lambda r: r["offered_jobs_per_s"]) if stable else None
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": "serving: Poisson jobs, U{10..1000} RHH trees depth 2-10, square grids 2^12..2^22 "
+                        "points log-uniform, Pagie or random depth-4 target tree, seed 4 (800 jobs over 32 "
+                        "distinct populations, cycled)",
+            "streams": streams, "capacity_jobs_per_s": cap, "burst": burst, "sweep": runs,
+            "sustained": best, "cache_hits": int(st["cache_hits"]), "cache_inserts": int(st["cache_inserts"])}
 
 
 def main():
@@ -339,6 +505,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, evolution and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -101,11 +101,21 @@ enum {
 typedef struct tgp_config {
     int32_t device;              /* CUDA device ordinal */
     int32_t flags;               /* TGP_F_* */
-    int64_t cache_budget_bytes;  /* HBM budget of the cross-call subtree cache; 0 disables it */
+    int64_t cache_budget_bytes;  /* HBM budget of the cross-call subtree cache; 0 disables it.
+                                    With a budget, a subtree of at least cache_min_cost that a
+                                    call evaluates on a domain for the second time is stored (one
+                                    float per point; 64 stores per call at most) and later calls,
+                                    of any population, load it instead of evaluating it (Sec. 2,
+                                    Handley).  Over budget, entries the calling population does
+                                    not reference are flushed, lowest cost (discounted by the calls
+                                    since their last use) first, and their memory is reused (Sec.
+                                    2, Keijzer).  Results are bitwise those without the cache. */
     int32_t points_per_thread;   /* 0 = automatic (autotuned); else 1, 2, 4, 8 or 16 */
     int32_t threads_per_block;   /* 0 = automatic; else 32, 64 or 128 */
     int32_t n_groups;            /* 0 = automatic; else trees are split into this many groups */
-    int32_t reserved[5];
+    int32_t cache_min_cost;      /* subtrees cheaper than this (per point, a binary32 add = 1) are
+                                    never stored in the cache; 0 = 48 */
+    int32_t reserved[4];
 } tgp_config;
 
 /* A target given as one expression tree (TGP_TARGET_TOKENS). */
@@ -246,7 +256,9 @@ int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* s
  * population, synchronises `stream`, captures the launch sequence (queue
  * reset, interpreter, finalize) and instantiates it; later calls replay the
  * graph (one cudaGraphLaunch).  The graph is freed with the population.  The
- * first call must not itself be made during a stream capture.
+ * first call must not itself be made during a stream capture.  `stream` must
+ * be a created stream (NULL and the per-thread default stream cannot be
+ * captured: TGP_E_INVALID).
  */
 int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
 
@@ -291,6 +303,98 @@ int tgp_debug_layout(int32_t* out, int32_t n);
  * accounting only.
  */
 int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
+
+/* ------------------------------------------------------------------------
+ * Serving: evaluation jobs that arrive over time.
+ *
+ * A server owns a worker thread on a context.  tgp_server_submit copies and
+ * validates a job (tokens, grid, target) in the caller's thread and queues
+ * it; the worker admits queued jobs in arrival order when a launch slot (one
+ * CUDA stream) is free and the job's device memory fits the HBM budget, and
+ * fuses every queued job on the same domain (same grid and target) into one
+ * population launch -- continuous batching at launch granularity: jobs that
+ * arrive while others run join the next launch on their domain, and launches
+ * on different slots overlap on the device.  Domains stay resident on the
+ * device between jobs (least recently used ones not in use are released when
+ * the budget needs room), and so does the context's subtree cache (the
+ * context's cache_budget_bytes).  A job's RMSE values do not depend on which
+ * other jobs share its launch.
+ * ------------------------------------------------------------------------ */
+typedef struct tgp_server tgp_server;
+
+typedef struct tgp_server_config {
+    int32_t streams;           /* launch slots (CUDA streams), 1..16; 0 = 4 */
+    int32_t max_batch_trees;   /* trees fused into one launch at most; 0 = 4096 (a larger job runs alone) */
+    int64_t hbm_budget_bytes;  /* device memory for resident domains and admitted launches;
+                                  0 = 80% of the free memory at creation */
+    int64_t reserved[6];
+} tgp_server_config;
+
+/* One evaluation job: a population (as for tgp_compile_population) scored on
+ * a grid (as for tgp_load_domain) against the Pagie target or one target
+ * tree.  Every pointer is read during tgp_server_submit only. */
+typedef struct tgp_job {
+    const int32_t* ops;
+    const float* imm;
+    int64_t n_imm;
+    const int64_t* tree_off;
+    int32_t n_trees;
+    int32_t order;
+    int32_t W, H;
+    float xlo, xhi, ylo, yhi;
+    int32_t target_kind;                     /* TGP_TARGET_PAGIE or TGP_TARGET_TOKENS */
+    const tgp_target_tokens* target_tokens;  /* TGP_TARGET_TOKENS only */
+} tgp_job;
+
+/* Timeline of a finished job, nanoseconds of a monotonic host clock. */
+typedef struct tgp_job_info {
+    int64_t submit_ns;   /* tgp_server_submit was entered (the job's arrival) */
+    int64_t launch_ns;   /* its launch was enqueued */
+    int64_t done_ns;     /* its RMSE values were in host memory */
+    int64_t batch;       /* launch sequence number */
+    int32_t batch_jobs;  /* jobs fused into that launch */
+    int32_t status;      /* TGP_OK or the error of its launch */
+    int64_t reserved[4];
+} tgp_job_info;
+
+typedef struct tgp_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t batches;             /* launches */
+    int64_t max_batch_jobs;
+    int64_t max_in_flight;       /* most launches on the device at once */
+    int64_t domains_resident;
+    int64_t domains_loaded, domains_released;
+    int64_t bytes_in_use;        /* resident domains + launches in flight */
+    int64_t max_bytes_in_use;
+    int64_t hbm_budget_bytes;
+    int64_t queued;              /* jobs waiting for admission */
+    int64_t worker_busy_ns;      /* host time the worker spent preparing and enqueueing launches */
+    int64_t domain_load_ns;      /* part of it spent loading domains */
+    int64_t reserved[3];
+} tgp_server_stats;
+
+/* Starts a server on ctx (a device context; the server uses it from its
+ * worker thread and the caller may keep using it).  cfg may be NULL. */
+int tgp_server_create(tgp_ctx* ctx, const tgp_server_config* cfg, tgp_server** out);
+
+/* Finishes every job already submitted, then stops the worker and frees the
+ * server (results not collected are dropped). */
+int tgp_server_destroy(tgp_server* srv);
+
+/* Validates and queues a job; *job_id receives its id.  TGP_E_TOKENS /
+ * TGP_E_INVALID for a malformed job (nothing queued); TGP_E_BUDGET when the
+ * job alone cannot fit the HBM budget. */
+int tgp_server_submit(tgp_server* srv, const tgp_job* job, int64_t* job_id);
+
+/* Waits up to timeout_us microseconds (< 0: no limit, 0: poll) for a job.
+ * Done: copies its n_trees RMSE values (as tgp_fitness) into rmse_host and
+ * its timeline into info (either may be NULL), forgets the job and returns
+ * the job's status.  Not done in time: TGP_E_TIMEOUT, the job stays.  An
+ * unknown or already collected id: TGP_E_INVALID. */
+int tgp_server_wait(tgp_server* srv, int64_t job_id, int64_t timeout_us, double* rmse_host,
+                    tgp_job_info* info);
+
+int tgp_server_stats_get(tgp_server* srv, tgp_server_stats* out);
 
 #ifdef __cplusplus
 }

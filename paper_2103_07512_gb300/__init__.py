@@ -28,7 +28,9 @@ N_OPS = 13
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
            "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
-           "tgp_calibrate_op_costs", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune"]
+           "tgp_calibrate_op_costs", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune",
+           "tgp_server_create", "tgp_server_destroy", "tgp_server_submit", "tgp_server_wait",
+           "tgp_server_stats_get"]
 
 
 class TgpError(RuntimeError):
@@ -41,7 +43,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("cache_budget_bytes", ctypes.c_int64),
                 ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("n_groups", ctypes.c_int32), ("cache_min_cost", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class TargetTokens(ctypes.Structure):
@@ -60,6 +63,38 @@ class Stats(ctypes.Structure):
                 ("cache_evictions", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("eval_ms_sum", ctypes.c_double), ("eval_timed", ctypes.c_int64),
                 ("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_batch_trees", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_void_p), ("imm", ctypes.c_void_p), ("n_imm", ctypes.c_int64),
+                ("tree_off", ctypes.c_void_p), ("n_trees", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("xlo", ctypes.c_float), ("xhi", ctypes.c_float), ("ylo", ctypes.c_float), ("yhi", ctypes.c_float),
+                ("target_kind", ctypes.c_int32), ("target_tokens", ctypes.c_void_p)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("batch", ctypes.c_int64), ("batch_jobs", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "failed", "batches", "max_batch_jobs", "max_in_flight", "domains_resident",
+        "domains_loaded", "domains_released", "bytes_in_use", "max_bytes_in_use", "hbm_budget_bytes", "queued",
+        "worker_busy_ns", "domain_load_ns")] + [("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -96,6 +131,11 @@ def lib():
             "tgp_fitness_noalloc": [P, i64, i64, P, P],
             "tgp_fitness_graph": [P, i64, i64, P, P],
             "tgp_autotune": [P, i64, i64, P, P, P, P],
+            "tgp_server_create": [P, P, P],
+            "tgp_server_destroy": [P],
+            "tgp_server_submit": [P, P, P],
+            "tgp_server_wait": [P, i64, i64, P, P],
+            "tgp_server_stats_get": [P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -131,7 +171,7 @@ class Context:
     """A libtgp context on one CUDA device (or host-only for plan inspection)."""
 
     def __init__(self, device=0, host_only=False, cache_budget_bytes=0, points_per_thread=0,
-                 threads_per_block=0, n_groups=0, dedup=True, time_kernels=False):
+                 threads_per_block=0, n_groups=0, dedup=True, time_kernels=False, cache_min_cost=0):
         self._L = lib()
         cfg = Config()
         cfg.device = device
@@ -141,6 +181,7 @@ class Context:
         cfg.points_per_thread = points_per_thread
         cfg.threads_per_block = threads_per_block
         cfg.n_groups = n_groups
+        cfg.cache_min_cost = cache_min_cost
         h = ctypes.c_void_p()
         self._h = None
         self._check(self._L.tgp_create(ctypes.byref(h), ctypes.byref(cfg)))
@@ -275,6 +316,85 @@ class Context:
         c = np.zeros(N_OPS, np.float64)
         self._check(self._L.tgp_calibrate_op_costs(self._h, _ptr(c)))
         return c
+
+
+class Server:
+    """tgp_server: a serving loop on a context (worker thread in the library).
+
+    submit() queues a job (tokens scored on a grid against the Pagie target
+    or a target tree) and returns its id; wait() returns its RMSE values and
+    timeline.  Jobs on the same domain that wait together are fused into one
+    launch; launches on different streams overlap on the device."""
+
+    def __init__(self, ctx, streams=0, max_batch_trees=0, hbm_budget_bytes=0):
+        self._L = lib()
+        self.ctx = ctx
+        cfg = ServerConfig()
+        cfg.streams = streams
+        cfg.max_batch_trees = max_batch_trees
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        h = ctypes.c_void_p()
+        self._h = None
+        ctx._check(self._L.tgp_server_create(ctx._h, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._trees = {}
+
+    def close(self):
+        if self._h is not None:
+            self._L.tgp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, tok, W, H, xlo=-5.0, xhi=5.0, ylo=-5.0, yhi=5.0, target_tokens=None):
+        """Queues a job; `tok` is an inputs.Tokens, `target_tokens` = (ops, imm, order) or None (Pagie)."""
+        ops = np.ascontiguousarray(tok.ops, np.int32)
+        imm = np.ascontiguousarray(tok.imm, np.float32)
+        off = np.ascontiguousarray(tok.tree_off, np.int64)
+        j = Job(ops.ctypes.data, imm.ctypes.data if imm.size else None, imm.size, off.ctypes.data,
+                off.size - 1, tok.order, W, H, xlo, xhi, ylo, yhi, TARGET_PAGIE, None)
+        keep = None
+        if target_tokens is not None:
+            t_ops, t_imm, t_order = target_tokens
+            t_ops = np.ascontiguousarray(t_ops, np.int32)
+            t_imm = np.ascontiguousarray(t_imm, np.float32)
+            tt = TargetTokens(t_ops.ctypes.data, t_imm.ctypes.data if t_imm.size else None, t_ops.size,
+                              t_imm.size, t_order)
+            keep = (t_ops, t_imm, tt)
+            j.target_kind = TARGET_TOKENS
+            j.target_tokens = ctypes.cast(ctypes.pointer(tt), ctypes.c_void_p)
+        out = ctypes.c_int64()
+        self.ctx._check(self._L.tgp_server_submit(self._h, ctypes.byref(j), ctypes.byref(out)))
+        del keep
+        self._trees[out.value] = int(off.size - 1)
+        return out.value
+
+    def wait(self, job_id, timeout=None):
+        """(rmse float64[n_trees], info dict); raises TgpError (E_TIMEOUT when not done in time)."""
+        n = self._trees.get(job_id, 0)
+        rmse = np.empty(max(n, 1), np.float64)
+        info = JobInfo()
+        us = -1 if timeout is None else int(timeout * 1e6)
+        rc = self._L.tgp_server_wait(self._h, job_id, us, _ptr(rmse), ctypes.byref(info))
+        if rc != E_TIMEOUT:
+            self._trees.pop(job_id, None)
+        self.ctx._check(rc)
+        return rmse[:n], info.as_dict()
+
+    def stats(self):
+        s = ServerStats()
+        self.ctx._check(self._L.tgp_server_stats_get(self._h, ctypes.byref(s)))
+        return s.as_dict()
 
 
 def debug_layout():

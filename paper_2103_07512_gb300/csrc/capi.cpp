@@ -69,15 +69,22 @@ struct DevBuf {
     }
 };
 
+// Completion marker of one launch, shared by the cache entries it touched.
+struct Fence {
+    cudaEvent_t ev = nullptr;
+    ~Fence() {
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+using FenceP = std::shared_ptr<Fence>;
+
 // One cached subtree: its values at every point of a domain.
 struct CacheEntry {
-    DevBuf<float> values;
+    DevBuf<float> values;        // capacity >= the domain's points
     int64_t last_use = 0;        // epoch of the last call that read or wrote it
     float cost = 0.f;            // issue cost per point of evaluating it
-    cudaEvent_t ready = nullptr; // completes when the writing launch has finished
-    ~CacheEntry() {
-        if (ready) cudaEventDestroy(ready);
-    }
+    FenceP written;              // the launch storing the values (readers wait for it)
+    FenceP touched;              // the last launch reading or writing the values
 };
 
 struct Domain {
@@ -88,6 +95,9 @@ struct Domain {
     // cross-call subtree cache of this domain, keyed by the node's id in the
     // context-wide DAG (exact structural identity)
     std::unordered_map<int32_t, std::unique_ptr<CacheEntry>> cache;
+    // subtrees evaluated here by an earlier call and not stored: a subtree is
+    // stored on its second evaluation on the domain, not its first
+    std::unordered_set<int32_t> seen;
     int64_t N() const { return (int64_t)W * H; }
 };
 
@@ -129,7 +139,9 @@ struct Population {
     std::vector<int32_t> gid;      // node id in the context-wide DAG (cache on)
     std::map<PlanShape, std::unique_ptr<Plan>> plans;
     std::map<PlanShape, std::unique_ptr<Plan>> cplans;   // cached mode: rebuilt when the view changes
+    std::vector<std::unique_ptr<Plan>> spare;             // buffers kept from a replaced population
     std::map<std::pair<int64_t, double*>, std::unique_ptr<GraphEntry>> graphs;
+    std::shared_ptr<internal::PrePlan> preplanned;          // host plan built ahead (serving)
 };
 
 // Autotuner key: grid size and the population's size buckets.
@@ -167,7 +179,8 @@ struct tgp_ctx {
     std::map<TuneKey, TuneChoice> tuned;                     // tgp_autotune results
     Dag gdag;                                                // context-wide DAG (cache on)
     int64_t epoch = 0;                                       // calls that used the cache
-    int64_t cache_bytes = 0;
+    int64_t cache_bytes = 0;                                 // allocated: live + recycled entries
+    std::multimap<size_t, std::unique_ptr<CacheEntry>> cache_free;   // evicted buffers by capacity
     bool capturing = false;                                  // inside tgp_fitness_graph capture
     // TGP_F_TIME_KERNELS: event pairs around interpreter launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -263,7 +276,9 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
     CUDA_TRY(pl->counter.ensure(1));
-    if (!pl->h_rmse) {
+    if (!pl->h_rmse || pl->h_rmse_n < (size_t)std::max<int64_t>(T, 1)) {
+        if (pl->h_rmse) cudaFreeHost(pl->h_rmse);
+        pl->h_rmse = nullptr;
         CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * std::max<int64_t>(T, 1)));
         pl->h_rmse_n = (size_t)std::max<int64_t>(T, 1);
     }
@@ -294,10 +309,22 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
     auto it = plans.find(shape);
     Plan* pl;
     if (it == plans.end()) {
-        auto up = std::make_unique<Plan>();
+        std::unique_ptr<Plan> up;
+        if (!pop->spare.empty()) {   // reuse device buffers (no allocation, no free)
+            up = std::move(pop->spare.back());
+            pop->spare.pop_back();
+            up->h_table.clear();
+            up->view = CacheView();
+        } else {
+            up = std::make_unique<Plan>();
+        }
         pl = up.get();
         plans[shape] = std::move(up);
-        build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr);
+        const bool pre = !cached && pop->preplanned && !(pop->preplanned->shape < shape) &&
+                         !(shape < pop->preplanned->shape);
+        if (pre) pl->hp = std::move(pop->preplanned->plan);
+        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr);
+        pop->preplanned.reset();
         if (cached) {
             pl->view = *cv;
             pl->h_table = *table;
@@ -332,35 +359,49 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
 
 bool cache_on(const tgp_ctx* c) { return c->cfg.cache_budget_bytes > 0; }
 
-// A cache entry is usable once the launch that wrote it has finished.
-bool entry_ready(CacheEntry* e) {
-    if (!e->ready) return true;
-    if (cudaEventQuery(e->ready) == cudaSuccess) {
-        cudaEventDestroy(e->ready);
-        e->ready = nullptr;
+// A fence whose launch has finished (or no fence).
+bool fence_done(FenceP& f) {
+    if (!f) return true;
+    if (cudaEventQuery(f->ev) == cudaSuccess) {
+        f.reset();
         return true;
     }
     cudaGetLastError();
     return false;
 }
 
-// Subtrees worth storing cost at least this much per point to re-evaluate.
-constexpr float kCacheMinCost = 16.f;
+// A cache entry is usable once the launch that wrote it has finished.
+bool entry_ready(CacheEntry* e) { return fence_done(e->written); }
 
-// Builds the cache view of one call: cached nodes become loads; the most
-// expensive evaluated nodes not yet cached are stored.  Keijzer-style flush
-// when the budget would be exceeded: entries the current population does not
-// reference go first, oldest use first, then cheapest.  Fills the launch's
-// entry-pointer table and the list of entries this call writes.
-int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, CacheView& cv, std::vector<float*>& table,
-                  std::vector<CacheEntry*>& written) {
+// Default for subtrees worth storing: re-evaluating them costs at least this
+// much per point (planning units, a binary32 add = 1).  Storing and reloading
+// a value moves 8 bytes per point through HBM, which takes as long as a few
+// dozen binary32 operations of the interpreter, so cheaper subtrees are
+// faster to recompute than to reload.
+constexpr int32_t kCacheMinCost = 48;
+// Stores per call at most (and a quarter of the budget at most).
+constexpr int64_t kCacheMaxInsertsPerCall = 64;
+// Bound of a domain's second-evaluation filter.
+constexpr size_t kCacheSeenMax = 1 << 20;
+
+// Builds the cache view of one call on stream s: cached nodes become loads;
+// expensive nodes evaluated for the second time on this domain are stored.
+// Keijzer-style flush when the budget would be exceeded: entries the current
+// population does not reference go first, lowest benefit first.  An evicted
+// entry's buffer is recycled, with `s` made to wait for the last launch that
+// used it, so no flush synchronises the device.  Fills the launch's
+// entry-pointer table and the entries this call reads or writes.
+int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheView& cv,
+                  std::vector<float*>& table, std::vector<CacheEntry*>& read, std::vector<CacheEntry*>& written) {
     const PopIR& ir = pop->ir;
     const size_t n_nodes = ir.dag.size();
-    const int64_t bytes = d->N() * (int64_t)sizeof(float);
+    const size_t N = (size_t)d->N();
+    const int64_t bytes = (int64_t)N * (int64_t)sizeof(float);
     c->epoch++;
     cv.cached.assign(n_nodes, -1);
     cv.insert.assign(n_nodes, -1);
     table.clear();
+    read.clear();
     written.clear();
     std::unordered_set<int32_t> referenced;
     for (size_t n = 0; n < n_nodes; ++n) {
@@ -372,72 +413,97 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, CacheView& cv, std::ve
             cv.cached[n] = (int32_t)table.size();
             table.push_back(it->second->values.p);
             it->second->last_use = c->epoch;
+            read.push_back(it->second.get());
             c->stats.cache_hits++;
         }
     }
-    // candidates: evaluated nodes, most expensive first
+    // candidates: expensive evaluated nodes seen here before, most expensive first
     std::vector<int32_t> cand;
-    for (int32_t n : evaluated_nodes(ir, cv))
-        if (ir.dag.nodes[n].cost >= kCacheMinCost && !d->cache.count(pop->gid[n])) cand.push_back(n);
+    const float min_cost = (float)(c->cfg.cache_min_cost > 0 ? c->cfg.cache_min_cost : kCacheMinCost);
+    if (d->seen.size() > kCacheSeenMax) d->seen.clear();
+    for (int32_t n : evaluated_nodes(ir, cv)) {
+        if (ir.dag.nodes[n].cost < min_cost) continue;
+        const int32_t g = pop->gid[n];
+        if (d->cache.count(g)) continue;   // stored by a launch still running
+        if (d->seen.insert(g).second) continue;   // first evaluation here
+        cand.push_back(n);
+    }
     std::stable_sort(cand.begin(), cand.end(),
                      [&](int32_t a, int32_t b) { return ir.dag.nodes[a].cost > ir.dag.nodes[b].cost; });
     const int64_t budget = c->cfg.cache_budget_bytes;
-    // at most a quarter of the budget is written per call, so the cache turns over gradually
-    const int64_t quota = std::max<int64_t>(budget / 4 / bytes, budget >= bytes ? 1 : 0);
-    int64_t want = std::min<int64_t>((int64_t)cand.size(), quota);
-    if (want > 0 && c->cache_bytes + want * bytes > budget) {
-        // flush (Keijzer's fixed-size cache, Sec. 2): only entries the current
-        // population does not reference (in any domain) may go; the lowest
-        // benefit goes first, benefit = re-evaluation cost per point (cost per
-        // byte, the same for every entry) discounted by the calls since its
-        // last use, so stale entries age out
-        struct Victim {
-            double score;
-            int64_t last_use;
-            Domain* dom;
-            int32_t g;
-        };
-        std::vector<Victim> victims;
-        for (auto& dk : c->domains)
-            for (auto& kv : dk.second->cache)
-                if ((dk.second.get() != d || !referenced.count(kv.first)) && entry_ready(kv.second.get())) {
-                    const CacheEntry& e = *kv.second;
-                    const double score = (double)e.cost / (double)(1 + c->epoch - e.last_use);
-                    victims.push_back({score, e.last_use, dk.second.get(), kv.first});
-                }
-        std::sort(victims.begin(), victims.end(), [](const Victim& a, const Victim& b) {
-            if (a.score != b.score) return a.score < b.score;
-            if (a.last_use != b.last_use) return a.last_use < b.last_use;
-            return a.g < b.g;
-        });
-        size_t vi = 0;
-        bool synced = false;
-        while (c->cache_bytes + want * bytes > budget && vi < victims.size()) {
-            if (!synced) {   // no launch may still read an entry that is freed
-                CUDA_TRY(cudaDeviceSynchronize());
-                synced = true;
-            }
-            const Victim& v = victims[vi++];
-            c->cache_bytes -= v.dom->N() * (int64_t)sizeof(float);
-            v.dom->cache.erase(v.g);
-            c->stats.cache_evictions++;
-        }
-        want = std::max<int64_t>(0, std::min<int64_t>(want, (budget - c->cache_bytes) / bytes));
-    }
+    const int64_t quota = std::min<int64_t>(kCacheMaxInsertsPerCall,
+                                            std::max<int64_t>(budget / 4 / bytes, budget >= bytes ? 1 : 0));
+    const int64_t want = std::min<int64_t>((int64_t)cand.size(), quota);
+    std::vector<std::pair<double, std::pair<Domain*, int32_t>>> victims;
+    size_t vi = 0;
+    bool victims_listed = false;
     for (int64_t i = 0; i < want; ++i) {
-        const int32_t n = cand[i];
-        auto e = std::make_unique<CacheEntry>();
-        if (e->values.ensure((size_t)d->N()) != cudaSuccess) {
-            cudaGetLastError();
-            break;   // out of device memory: store fewer
+        std::unique_ptr<CacheEntry> e;
+        // 1. a recycled buffer large enough (smallest first)
+        auto fit = c->cache_free.lower_bound(N);
+        if (fit == c->cache_free.end() && c->cache_bytes + bytes > budget) {
+            // 2. flush (Keijzer's fixed-size cache, Sec. 2): entries the
+            //    current population does not reference, in any domain, lowest
+            //    benefit first; benefit = re-evaluation cost per point (cost
+            //    per byte: the same for every entry) discounted by the calls
+            //    since its last use, so stale entries age out
+            if (!victims_listed) {
+                victims_listed = true;
+                for (auto& dk : c->domains)
+                    for (auto& kv : dk.second->cache)
+                        if ((dk.second.get() != d || !referenced.count(kv.first)) && entry_ready(kv.second.get())) {
+                            const CacheEntry& v = *kv.second;
+                            const double score = (double)v.cost / (double)(1 + c->epoch - v.last_use);
+                            victims.push_back({score, {dk.second.get(), kv.first}});
+                        }
+                std::sort(victims.begin(), victims.end());
+            }
+            while (vi < victims.size() && fit == c->cache_free.end()) {
+                Domain* vd = victims[vi].second.first;
+                auto vit = vd->cache.find(victims[vi].second.second);
+                ++vi;
+                std::unique_ptr<CacheEntry> v = std::move(vit->second);
+                vd->cache.erase(vit);
+                c->stats.cache_evictions++;
+                const size_t cap = v->values.n;
+                auto ins = c->cache_free.emplace(cap, std::move(v));
+                if (cap >= N) fit = ins;
+            }
+            if (fit == c->cache_free.end()) {
+                // 3. recycled buffers of other sizes are released to make room
+                //    (a free may wait for the device: only here)
+                bool any = false;
+                for (auto f = c->cache_free.begin(); f != c->cache_free.end() && c->cache_bytes + bytes > budget;) {
+                    c->cache_bytes -= (int64_t)f->first * (int64_t)sizeof(float);
+                    f = c->cache_free.erase(f);
+                    any = true;
+                }
+                if (!any || c->cache_bytes + bytes > budget) break;   // the budget is held by live entries
+            }
         }
+        if (fit != c->cache_free.end()) {
+            e = std::move(fit->second);
+            c->cache_free.erase(fit);
+            // the previous launches on this buffer finish before this one writes it
+            if (e->touched && !fence_done(e->touched)) CUDA_TRY(cudaStreamWaitEvent(s, e->touched->ev, 0));
+            e->touched.reset();
+            e->written.reset();
+        } else {
+            e = std::make_unique<CacheEntry>();
+            if (e->values.ensure(N) != cudaSuccess) {
+                cudaGetLastError();
+                break;   // out of device memory: store fewer
+            }
+            c->cache_bytes += bytes;
+        }
+        const int32_t n = cand[i];
         e->cost = ir.dag.nodes[n].cost;
         e->last_use = c->epoch;
         cv.insert[n] = (int32_t)table.size();
         table.push_back(e->values.p);
         written.push_back(e.get());
-        c->cache_bytes += bytes;
         c->stats.cache_inserts++;
+        d->seen.erase(pop->gid[n]);
         d->cache[pop->gid[n]] = std::move(e);
     }
     c->stats.cache_entries = 0;
@@ -446,12 +512,19 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, CacheView& cv, std::ve
     return TGP_OK;
 }
 
-// Marks the entries a launch wrote as pending until the stream reaches this point.
-int mark_written(std::vector<CacheEntry*>& written, cudaStream_t s) {
+// After a cached-mode launch on `s`: one fence marks the entries it wrote as
+// pending until it finishes and records it as the last user of every entry
+// it read or wrote.
+int fence_call(std::vector<CacheEntry*>& read, std::vector<CacheEntry*>& written, cudaStream_t s) {
+    if (read.empty() && written.empty()) return TGP_OK;
+    auto f = std::make_shared<Fence>();
+    CUDA_TRY(cudaEventCreateWithFlags(&f->ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(f->ev, s));
     for (CacheEntry* e : written) {
-        CUDA_TRY(cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming));
-        CUDA_TRY(cudaEventRecord(e->ready, s));
+        e->written = f;
+        e->touched = f;
     }
+    for (CacheEntry* e : read) e->touched = f;
     return TGP_OK;
 }
 
@@ -460,25 +533,29 @@ int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s,
     return get_plan_shape(c, pop, choose_shape(c, pop->ir, N), pheno, s, out);
 }
 
+// Entries a cached-mode call reads and writes (fenced after its launches).
+struct CallCache {
+    std::vector<CacheEntry*> read, written;
+};
+
 // The plan of one fitness or phenotype call on a domain: with the cache on,
-// the view of the domain's cache is taken first and the entries this launch
-// writes are returned in `written` (mark them after the launch).
-int get_call_plan(tgp_ctx* c, Population* pop, Domain* d, bool pheno, cudaStream_t s, Plan** out,
-                  std::vector<CacheEntry*>& written) {
-    written.clear();
+// the view of the domain's cache is taken first.
+int get_call_plan(tgp_ctx* c, Population* pop, Domain* d, bool pheno, cudaStream_t s, Plan** out, CallCache& cc) {
+    cc.read.clear();
+    cc.written.clear();
     if (!cache_on(c) || pop->gid.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
     CacheView cv;
     std::vector<float*> table;
-    int rc = prepare_cache(c, pop, d, cv, table, written);
+    int rc = prepare_cache(c, pop, d, s, cv, table, cc.read, cc.written);
     if (rc) return rc;
     if (table.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
     return get_plan_shape(c, pop, choose_shape(c, pop->ir, d->N()), pheno, s, out, &cv, &table);
 }
 
-// After the launches of a call in cached mode: entries written become ready,
-// and the plan's buffers may be rewritten, once the stream reaches here.
-int finish_call(Plan* pl, std::vector<CacheEntry*>& written, cudaStream_t s) {
-    int rc = mark_written(written, s);
+// After the launches of a call in cached mode: fences its cache entries, and
+// the plan's buffers may be rewritten once the stream reaches here.
+int finish_call(Plan* pl, CallCache& cc, cudaStream_t s) {
+    int rc = fence_call(cc.read, cc.written, s);
     if (rc) return rc;
     if (!pl->h_table.empty()) {
         if (!pl->done) CUDA_TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
@@ -558,15 +635,37 @@ int launch_fitness(tgp_ctx* c, Population* pop, Plan* pl, Domain* d, cudaStream_
 
 int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out) {
     Plan* pl = nullptr;
-    std::vector<CacheEntry*> written;
-    int rc = get_call_plan(c, pop, d, false, s, &pl, written);
+    CallCache cc;
+    int rc = get_call_plan(c, pop, d, false, s, &pl, cc);
     if (rc) return rc;
     rc = launch_fitness(c, pop, pl, d, s, rmse_dev);
     if (rc) return rc;
-    rc = finish_call(pl, written, s);
+    rc = finish_call(pl, cc, s);
     if (rc) return rc;
     if (plan_out) *plan_out = pl;
     return TGP_OK;
+}
+
+// Registers a population's IR with the context (lock held): context-wide
+// subtree ids when the cache is on (the cache key of a subtree across
+// populations), and the population counters.
+void adopt_ir(tgp_ctx* ctx, Population* pop) {
+    pop->gid.clear();
+    if (cache_on(ctx)) {
+        const auto& nodes = pop->ir.dag.nodes;
+        pop->gid.resize(nodes.size());
+        for (size_t n = 0; n < nodes.size(); ++n) {   // kids precede parents
+            const DagNode& dn = nodes[n];
+            int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
+            int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
+            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm);
+        }
+    }
+    ctx->stats.tree_nodes = pop->ir.tree_nodes;
+    ctx->stats.dag_nodes = (int64_t)pop->ir.dag.size();
+    int64_t internal = 0;
+    for (const DagNode& n : pop->ir.dag.nodes) internal += !is_leaf(n.op);
+    ctx->stats.dag_internal = internal;
 }
 
 template <class M>
@@ -596,6 +695,64 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->sms = ctx->sms;
     v->device = ctx->device;
     return TGP_OK;
+}
+
+int context_device(tgp_ctx* ctx, int* device) {
+    if (!ctx || !device) return fail(TGP_E_INVALID, "ctx / device is NULL");
+    if (ctx->host_only) return fail(TGP_E_INVALID, "context was created with TGP_F_HOST_ONLY (no device)");
+    *device = ctx->device;
+    return TGP_OK;
+}
+
+int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, std::shared_ptr<PrePlan>* out) {
+    auto pp = std::make_shared<PrePlan>();
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        pp->shape = choose_shape(ctx, ir, N);
+    }
+    build_plan(ir, pp->shape, pp->plan);
+    *out = std::move(pp);
+    return TGP_OK;
+}
+
+int adopt_population(tgp_ctx* ctx, PopIR&& ir, tgp_handle* out, std::shared_ptr<PrePlan> pre) {
+    if (!ctx || !out) return fail(TGP_E_INVALID, "ctx / out is NULL");
+    auto pop = std::make_unique<Population>();
+    pop->ir = std::move(ir);
+    pop->preplanned = std::move(pre);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    adopt_ir(ctx, pop.get());
+    int64_t h = ctx->next_handle++;
+    ctx->pops[h] = std::move(pop);
+    *out = h;
+    return TGP_OK;
+}
+
+int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr<PrePlan> pre) {
+    if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    if (!p) return fail(TGP_E_INVALID, "unknown population handle %lld", (long long)pop);
+    for (auto* m : {&p->plans, &p->cplans}) {
+        for (auto& kv : *m) p->spare.push_back(std::move(kv.second));
+        m->clear();
+    }
+    p->graphs.clear();
+    p->ir = std::move(ir);
+    p->preplanned = std::move(pre);
+    adopt_ir(ctx, p);
+    return TGP_OK;
+}
+
+int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const PlanShape sh = choose_shape(ctx, ir, N);
+    const int64_t tile = (int64_t)sh.K * sh.threads;
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t T = (int64_t)ir.roots.size();
+    const int64_t code = (ir.tree_nodes + 2 * (int64_t)sh.n_groups + 1) * (int64_t)sizeof(Ins);
+    return T * tiles * (sh.threads / 32) * (int64_t)sizeof(float) + code + T * (int64_t)sizeof(double) +
+           (int64_t)sh.n_groups * 12 + 4096;
 }
 
 int set_error(int code, const char* f, ...) {
@@ -710,7 +867,7 @@ int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
     int rc = set_device(ctx);
     if (rc) return rc;
     CUDA_TRY(cudaDeviceSynchronize());
-    ctx->cache_bytes -= (int64_t)it->second->cache.size() * it->second->N() * (int64_t)sizeof(float);
+    for (auto& kv : it->second->cache) ctx->cache_bytes -= (int64_t)kv.second->values.n * (int64_t)sizeof(float);
     ctx->stats.cache_entries -= (int64_t)it->second->cache.size();
     ctx->stats.cache_bytes = ctx->cache_bytes;
     ctx->domains.erase(it);
@@ -725,21 +882,7 @@ int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, i
     int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err);
     if (rc) return fail(rc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     std::lock_guard<std::mutex> g(ctx->mu);
-    if (cache_on(ctx)) {   // context-wide ids: the cache key of a subtree across populations
-        const auto& nodes = pop->ir.dag.nodes;
-        pop->gid.resize(nodes.size());
-        for (size_t n = 0; n < nodes.size(); ++n) {   // kids precede parents
-            const DagNode& dn = nodes[n];
-            int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
-            int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
-            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm);
-        }
-    }
-    ctx->stats.tree_nodes = pop->ir.tree_nodes;
-    ctx->stats.dag_nodes = (int64_t)pop->ir.dag.size();
-    int64_t internal = 0;
-    for (const DagNode& n : pop->ir.dag.nodes) internal += !is_leaf(n.op);
-    ctx->stats.dag_internal = internal;
+    adopt_ir(ctx, pop.get());
     int64_t h = ctx->next_handle++;
     ctx->pops[h] = std::move(pop);
     *pop_out = h;
@@ -770,12 +913,12 @@ int tgp_evaluate(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     Plan* pl = nullptr;
-    std::vector<CacheEntry*> written;
-    rc = get_call_plan(ctx, p, d, true, s, &pl, written);
+    CallCache cc;
+    rc = get_call_plan(ctx, p, d, true, s, &pl, cc);
     if (rc) return rc;
     rc = launch_plan(ctx, pl, d, true, out_dev, s);
     if (rc) return rc;
-    return finish_call(pl, written, s);
+    return finish_call(pl, cc, s);
 }
 
 int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_host,
@@ -827,6 +970,8 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
     int rc = set_device(ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return fail(TGP_E_INVALID, "tgp_fitness_graph needs a created stream: the default streams cannot be captured");
     auto key = std::make_pair((int64_t)domain, rmse_dev);
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {

@@ -114,6 +114,20 @@ static void fmt(std::string& err, const char* f, long long a, long long b = 0, l
     err = buf;
 }
 
+void append_population(PopIR& dst, const PopIR& src) {
+    std::vector<int32_t> id(src.dag.size());
+    for (size_t n = 0; n < src.dag.size(); ++n) {   // children precede parents
+        const DagNode& s = src.dag.nodes[n];
+        id[n] = dst.dag.intern(s.op, s.kid[0] >= 0 ? id[s.kid[0]] : -1, s.kid[1] >= 0 ? id[s.kid[1]] : -1, s.imm);
+    }
+    for (size_t t = 0; t < src.roots.size(); ++t) {
+        dst.roots.push_back(id[src.roots[t]]);
+        dst.tree_size.push_back(src.tree_size[t]);
+        dst.tree_cost.push_back(src.tree_cost[t]);
+    }
+    dst.tree_nodes += src.tree_nodes;
+}
+
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                      int32_t n_trees, int32_t order, PopIR& out, std::string& err) {
     if (n_trees < 0 || n_trees > (1 << 24)) { fmt(err, "n_trees %lld out of range", n_trees); return -1; }

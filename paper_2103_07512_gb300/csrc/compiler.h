@@ -51,6 +51,10 @@ struct PopIR {
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                      int32_t n_trees, int32_t order, PopIR& out, std::string& err);
 
+// Appends the trees of `src` to `dst`, hash-consing src's nodes into dst's
+// DAG (subtrees common to both are shared).
+void append_population(PopIR& dst, const PopIR& src);
+
 // Shape of one launch plan.
 struct PlanShape {
     int64_t N = 0;       // grid points

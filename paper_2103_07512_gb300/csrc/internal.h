@@ -1,6 +1,7 @@
 // internal.h -- what the context exposes to other translation units of the
 // library (not part of the public C ABI).
 #pragma once
+#include <memory>
 #include <mutex>
 
 #include "../../include/tgp.h"
@@ -22,6 +23,34 @@ struct View {
 
 // Locks the context into `lk`, makes its device current and fills `v`.
 int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::mutex>& lk, View* v);
+
+// The context's CUDA device; TGP_E_INVALID for a host-only context.
+int context_device(tgp_ctx* ctx, int* device);
+
+// A host plan built ahead of the launch, for the shape the context would
+// choose for its population on N points.
+struct PrePlan {
+    PlanShape shape;
+    HostPlan plan;
+};
+
+// Builds the plan of `ir` on N points without holding the context lock (only
+// the shape choice takes it), so that callers may plan in their own threads.
+int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, std::shared_ptr<PrePlan>* out);
+
+// Registers a population built on the host (e.g. several jobs' trees merged
+// with append_population) as if it had been compiled from tokens.  `pre`, if
+// given, is used by the first launch whose shape matches it.
+int adopt_population(tgp_ctx* ctx, PopIR&& ir, tgp_handle* out, std::shared_ptr<PrePlan> pre = nullptr);
+
+// Gives an existing population new trees, keeping its device buffers for the
+// next plans (no allocation or free when they are large enough).  The
+// population's previous launches must have completed.
+int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr<PrePlan> pre = nullptr);
+
+// Device bytes one fitness launch of `ir` on N points needs beyond its
+// domain (partial sums, bytecode, results).
+int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N);
 
 // Records the calling thread's error message; returns `code`.
 int set_error(int code, const char* fmt, ...);

@@ -339,3 +339,31 @@ def batched_uneven(seed=2, order=PREFIX, n_trees=4096, dup_p=0.3):
     rng = np.random.default_rng(seed)
     trees, stats = exact_size_population(n_trees, 3, 255, 12, dup_p, rng)
     return to_tokens(trees, order), Grid(256, 256), stats
+
+
+def serving_jobs(n_jobs, seed=4, trees=(10, 1000), depth=(2, 10), side_log2=(6.0, 11.0), pool=None,
+                 order=PREFIX):
+    """Evaluation jobs for the serving loop: each has U{trees} RHH trees of
+    depth U{depth} ramp, a square grid of side round(2^u), u ~ U[side_log2]
+    (log-uniform point counts, sides that are not powers of two included),
+    over [-5,5]^2, and the Pagie target or a random full depth-4 target tree
+    with probability 1/2 each.  With `pool`, job i takes population i % pool
+    (drawn once), so long streams need not draw thousands of populations.
+    Returns a list of dicts {tok, W, H, target_tokens (None for Pagie)}."""
+    rng = np.random.default_rng(seed)
+    pops = []
+    jobs = []
+    for i in range(n_jobs):
+        if pool is None or len(pops) < pool:
+            n = int(rng.integers(trees[0], trees[1] + 1))
+            pops.append(to_tokens(ramped_half_and_half(n, depth[0], depth[1], rng), order))
+            tok = pops[-1]
+        else:
+            tok = pops[i % pool]
+        side = int(round(2.0 ** rng.uniform(side_log2[0], side_log2[1])))
+        target = None
+        if rng.random() < 0.5:
+            tt = to_tokens([_full(rng, 4, FUNCTIONS)], PREFIX)
+            target = (tt.ops, tt.imm, tt.order)
+        jobs.append({"tok": tok, "W": side, "H": side, "target_tokens": target})
+    return jobs

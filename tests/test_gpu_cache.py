@@ -29,18 +29,19 @@ def run_ga(ctx, g, generations, seed=5, pop_size=50):
     return rows, toks, dom
 
 
-@pytest.mark.parametrize("entries", [4, 64])
-def test_ga_with_cache_is_bitwise_equal_to_without(entries):
+@pytest.mark.parametrize("entries,min_cost", [(4, 4), (64, 4), (64, 0)])
+def test_ga_with_cache_is_bitwise_equal_to_without(entries, min_cost):
     g = I.Grid(256, 192)
     budget = entries * g.N * 4
-    with tgp.Context(cache_budget_bytes=budget) as a, tgp.Context() as b:
+    with tgp.Context(cache_budget_bytes=budget, cache_min_cost=min_cost) as a, tgp.Context() as b:
         ra, _, _ = run_ga(a, g, 10)
         rb, _, _ = run_ga(b, g, 10)
         for i, (x, y) in enumerate(zip(ra, rb)):
             assert np.array_equal(x.view(np.int64), y.view(np.int64)), f"generation {i}"
         st = a.stats()
-        assert st["cache_inserts"] > 0 and st["cache_hits"] > 0
         assert st["cache_bytes"] <= budget
+        if min_cost:   # with the default threshold the run may store nothing
+            assert st["cache_inserts"] > 0 and st["cache_hits"] > 0
         if entries == 4:
             assert st["cache_evictions"] > 0
         assert b.stats()["cache_hits"] == 0
@@ -48,7 +49,7 @@ def test_ga_with_cache_is_bitwise_equal_to_without(entries):
 
 def test_cached_generation_matches_oracle():
     g = I.Grid(64, 48)
-    with tgp.Context(cache_budget_bytes=32 * g.N * 4) as c:
+    with tgp.Context(cache_budget_bytes=32 * g.N * 4, cache_min_cost=4) as c:
         rows, toks, _ = run_ga(c, g, 6, seed=9)
         assert c.stats()["cache_hits"] > 0
     for gen in (3, 5):
@@ -61,12 +62,12 @@ def test_cached_generation_matches_oracle():
 def test_cached_phenotypes_bitwise():
     tok, _, _ = I.batched_uneven(seed=21, n_trees=200)
     g = I.Grid(100, 70)
-    with tgp.Context(cache_budget_bytes=256 * g.N * 4) as a, tgp.Context() as b:
+    with tgp.Context(cache_budget_bytes=256 * g.N * 4, cache_min_cost=4) as a, tgp.Context() as b:
         da, db = a.load_domain(g.W, g.H), b.load_domain(g.W, g.H)
         pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
         ref = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
         b.evaluate(pb, db, ref)
-        for call in range(3):   # inserts, then hits
+        for call in range(4):   # seen, stored, then loaded
             out = torch.full_like(ref, float("nan"))
             a.evaluate(pa, da, out)
             torch.cuda.synchronize()
@@ -85,13 +86,13 @@ def test_cached_phenotypes_bitwise():
 def test_cache_is_per_domain_and_released_with_it():
     tok, _ = I.small_population(seed=22)
     g1, g2 = I.Grid(64, 64), I.Grid(40, 30, -1.0, 2.0, -3.0, 1.0)
-    with tgp.Context(cache_budget_bytes=1 << 26) as a, tgp.Context() as b:
+    with tgp.Context(cache_budget_bytes=1 << 26, cache_min_cost=4) as a, tgp.Context() as b:
         pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
         d1 = a.load_domain(g1.W, g1.H, g1.xlo, g1.xhi, g1.ylo, g1.yhi)
         d2 = a.load_domain(g2.W, g2.H, g2.xlo, g2.xhi, g2.ylo, g2.yhi)
         e1 = b.load_domain(g1.W, g1.H, g1.xlo, g1.xhi, g1.ylo, g1.yhi)
         e2 = b.load_domain(g2.W, g2.H, g2.xlo, g2.xhi, g2.ylo, g2.yhi)
-        for _ in range(2):
+        for _ in range(3):
             for da, db in ((d1, e1), (d2, e2)):
                 fa = a.fitness(pa, da, tok.n_trees)
                 fb = b.fitness(pb, db, tok.n_trees)
@@ -107,7 +108,7 @@ def test_cache_is_per_domain_and_released_with_it():
 def test_non_blocking_calls_with_entries_in_flight():
     tok, _ = I.small_population(seed=23)
     g = I.Grid(512, 256)
-    with tgp.Context(cache_budget_bytes=1 << 28) as a, tgp.Context() as b:
+    with tgp.Context(cache_budget_bytes=1 << 28, cache_min_cost=4) as a, tgp.Context() as b:
         da, db = a.load_domain(g.W, g.H), b.load_domain(g.W, g.H)
         pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
         ref = b.fitness(pb, db, tok.n_trees)

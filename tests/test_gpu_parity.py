@@ -444,6 +444,9 @@ def test_graph_replay_equals_direct_launch(ctx):
         ctx.fitness_graph(pop, dom, out, stream=s)
         s.synchronize()
         assert torch.equal(out, ref)
+    with pytest.raises(tgp.TgpError) as e:   # the legacy default stream cannot be captured
+        ctx.fitness_graph(pop, dom, out)
+    assert e.value.code == tgp.E_INVALID
     ctx.release_population(pop)              # frees the graph
 
 

@@ -289,3 +289,10 @@ def test_plan_group_offsets_are_consistent(ctx, n_points):
     assert np.all(ins[off[1:] - 1, 0] == F_END)
     roots = ins[ins[:, 0] == F_ROOT, 4]
     assert sorted(roots.tolist()) == list(range(tok.n_trees))
+
+
+def test_server_needs_a_device_context():
+    with tgp.Context(host_only=True) as c:
+        with pytest.raises(tgp.TgpError) as e:
+            tgp.Server(c)
+        assert e.value.code == tgp.E_INVALID

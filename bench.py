@@ -405,7 +405,7 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
                     "best_rmse": ev.best[1]}
         if b:
             out[arm].update({k: int(st[k]) for k in ("cache_hits", "cache_inserts", "cache_evictions",
-                                                       "cache_entries", "cache_bytes")})
+                                                       "cache_entries", "cache_bytes", "cache_reserved")})
         ctx.close()
     same = all(np.array_equal(a.view(np.int64), c.view(np.int64))
                for arm in ("cache", "cache_min_cost_8") for a, c in zip(rows[arm], rows["no_cache"]))

@@ -139,14 +139,16 @@ typedef struct tgp_stats {
     int32_t slots;            /* shared-memory value slots per thread of the last plan */
     int32_t reserved0;
     int64_t cache_entries;    /* live cache entries */
-    int64_t cache_bytes;      /* HBM held by the cache */
+    int64_t cache_bytes;      /* HBM held by live cache entries */
     int64_t cache_hits;       /* subtree loads served from the cache */
     int64_t cache_inserts;
     int64_t cache_evictions;
     int64_t launches;         /* kernels launched by the library so far */
     double eval_ms_sum;       /* TGP_F_TIME_KERNELS: summed interpreter kernel time */
     int64_t eval_timed;       /* TGP_F_TIME_KERNELS: launches summed in eval_ms_sum */
-    int64_t reserved[6];
+    int64_t cache_reserved;   /* HBM reserved for the cache (slabs carved into entries; at most
+                                 the budget, freed with the context) */
+    int64_t reserved[5];
 } tgp_stats;
 
 /* Creates a context on cfg->device (cfg may be NULL: device 0, defaults). */

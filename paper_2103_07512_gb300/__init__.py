@@ -62,7 +62,7 @@ class Stats(ctypes.Structure):
                 ("cache_hits", ctypes.c_int64), ("cache_inserts", ctypes.c_int64),
                 ("cache_evictions", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("eval_ms_sum", ctypes.c_double), ("eval_timed", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("cache_reserved", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

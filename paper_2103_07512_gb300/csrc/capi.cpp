@@ -80,12 +80,15 @@ using FenceP = std::shared_ptr<Fence>;
 
 // One cached subtree: its values at every point of a domain.
 struct CacheEntry {
-    DevBuf<float> values;        // capacity >= the domain's points
+    float* values = nullptr;     // a block of the context's cache slabs
+    size_t cap = 0;              // its capacity in floats (>= the domain's points)
     int64_t last_use = 0;        // epoch of the last call that read or wrote it
     float cost = 0.f;            // issue cost per point of evaluating it
     FenceP written;              // the launch storing the values (readers wait for it)
     FenceP touched;              // the last launch reading or writing the values
 };
+
+struct Population;
 
 struct Domain {
     int32_t W = 0, H = 0;
@@ -98,6 +101,10 @@ struct Domain {
     // subtrees evaluated here by an earlier call and not stored: a subtree is
     // stored on its second evaluation on the domain, not its first
     std::unordered_set<int32_t> seen;
+    // a target tree evaluated asynchronously: its population (plan buffers)
+    // and the fence of that launch, which every use of the domain waits for
+    std::unique_ptr<Population> target_pop;
+    mutable FenceP ready;
     int64_t N() const { return (int64_t)W * H; }
 };
 
@@ -179,14 +186,23 @@ struct tgp_ctx {
     std::map<TuneKey, TuneChoice> tuned;                     // tgp_autotune results
     Dag gdag;                                                // context-wide DAG (cache on)
     int64_t epoch = 0;                                       // calls that used the cache
-    int64_t cache_bytes = 0;                                 // allocated: live + recycled entries
-    std::multimap<size_t, std::unique_ptr<CacheEntry>> cache_free;   // evicted buffers by capacity
+    int64_t cache_bytes = 0;                                 // held by live entries
+    int64_t cache_reserved = 0;                              // device memory of the slabs (<= budget)
+    std::vector<void*> cache_slabs;                          // carved into entry blocks, freed with the context
+    char* slab_next = nullptr;
+    size_t slab_left = 0;
+    std::multimap<size_t, std::unique_ptr<CacheEntry>> cache_free;   // evicted blocks by capacity
     bool capturing = false;                                  // inside tgp_fitness_graph capture
     // TGP_F_TIME_KERNELS: event pairs around interpreter launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
     ~tgp_ctx() {
         for (auto& e : ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         for (auto& e : ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        if (!cache_slabs.empty()) {
+            cudaSetDevice(device);
+            cudaDeviceSynchronize();
+            for (void* p : cache_slabs) cudaFree(p);
+        }
     }
 };
 
@@ -276,12 +292,6 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
     CUDA_TRY(pl->counter.ensure(1));
-    if (!pl->h_rmse || pl->h_rmse_n < (size_t)std::max<int64_t>(T, 1)) {
-        if (pl->h_rmse) cudaFreeHost(pl->h_rmse);
-        pl->h_rmse = nullptr;
-        CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * std::max<int64_t>(T, 1)));
-        pl->h_rmse_n = (size_t)std::max<int64_t>(T, 1);
-    }
     CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s));
@@ -383,6 +393,34 @@ constexpr int32_t kCacheMinCost = 48;
 constexpr int64_t kCacheMaxInsertsPerCall = 64;
 // Bound of a domain's second-evaluation filter.
 constexpr size_t kCacheSeenMax = 1 << 20;
+// Cache memory is reserved in slabs of this size (or the budget left) and
+// carved into entry blocks, so storing a subtree never allocates.
+constexpr int64_t kCacheSlabBytes = int64_t(1) << 30;
+
+// A new block of `n` floats from the slabs (a new slab if the budget allows),
+// or nullptr.
+float* carve_block(tgp_ctx* c, size_t n, size_t* cap) {
+    const size_t need = (n * sizeof(float) + 255) & ~size_t(255);
+    if (c->slab_left < need) {
+        const int64_t room = c->cfg.cache_budget_bytes - c->cache_reserved;
+        if (room < (int64_t)need) return nullptr;
+        const size_t sz = (size_t)std::min<int64_t>(room, std::max<int64_t>((int64_t)need, kCacheSlabBytes));
+        void* p = nullptr;
+        if (cudaMalloc(&p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        c->cache_slabs.push_back(p);
+        c->cache_reserved += (int64_t)sz;
+        c->slab_next = static_cast<char*>(p);
+        c->slab_left = sz;
+    }
+    float* b = reinterpret_cast<float*>(c->slab_next);
+    c->slab_next += need;
+    c->slab_left -= need;
+    *cap = need / sizeof(float);
+    return b;
+}
 
 // Builds the cache view of one call on stream s: cached nodes become loads;
 // expensive nodes evaluated for the second time on this domain are stored.
@@ -403,23 +441,27 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     table.clear();
     read.clear();
     written.clear();
-    std::unordered_set<int32_t> referenced;
-    for (size_t n = 0; n < n_nodes; ++n) {
-        if (is_leaf(ir.dag.nodes[n].op)) continue;
-        const int32_t g = pop->gid[n];
-        referenced.insert(g);
-        auto it = d->cache.find(g);
-        if (it != d->cache.end() && entry_ready(it->second.get())) {
-            cv.cached[n] = (int32_t)table.size();
-            table.push_back(it->second->values.p);
-            it->second->last_use = c->epoch;
-            read.push_back(it->second.get());
-            c->stats.cache_hits++;
+    // Every stored subtree costs at least min_cost, so cheaper nodes are
+    // neither looked up nor candidates.
+    const float min_cost = (float)(c->cfg.cache_min_cost > 0 ? c->cfg.cache_min_cost : kCacheMinCost);
+    bool any = false;
+    for (size_t n = 0; n < n_nodes && !any; ++n) any = ir.dag.nodes[n].cost >= min_cost;
+    if (!any) return TGP_OK;
+    if (!d->cache.empty()) {
+        for (size_t n = 0; n < n_nodes; ++n) {
+            if (ir.dag.nodes[n].cost < min_cost) continue;
+            auto it = d->cache.find(pop->gid[n]);
+            if (it != d->cache.end() && entry_ready(it->second.get())) {
+                cv.cached[n] = (int32_t)table.size();
+                table.push_back(it->second->values);
+                it->second->last_use = c->epoch;
+                read.push_back(it->second.get());
+                c->stats.cache_hits++;
+            }
         }
     }
     // candidates: expensive evaluated nodes seen here before, most expensive first
     std::vector<int32_t> cand;
-    const float min_cost = (float)(c->cfg.cache_min_cost > 0 ? c->cfg.cache_min_cost : kCacheMinCost);
     if (d->seen.size() > kCacheSeenMax) d->seen.clear();
     for (int32_t n : evaluated_nodes(ir, cv)) {
         if (ir.dag.nodes[n].cost < min_cost) continue;
@@ -439,9 +481,11 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     bool victims_listed = false;
     for (int64_t i = 0; i < want; ++i) {
         std::unique_ptr<CacheEntry> e;
-        // 1. a recycled buffer large enough (smallest first)
+        // 1. a recycled block large enough (smallest first), else a new block
         auto fit = c->cache_free.lower_bound(N);
-        if (fit == c->cache_free.end() && c->cache_bytes + bytes > budget) {
+        size_t cap = 0;
+        float* block = fit == c->cache_free.end() ? carve_block(c, N, &cap) : nullptr;
+        if (fit == c->cache_free.end() && !block) {
             // 2. flush (Keijzer's fixed-size cache, Sec. 2): entries the
             //    current population does not reference, in any domain, lowest
             //    benefit first; benefit = re-evaluation cost per point (cost
@@ -449,6 +493,9 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
             //    since its last use, so stale entries age out
             if (!victims_listed) {
                 victims_listed = true;
+                std::unordered_set<int32_t> referenced;
+                for (size_t n = 0; n < n_nodes; ++n)
+                    if (ir.dag.nodes[n].cost >= min_cost) referenced.insert(pop->gid[n]);
                 for (auto& dk : c->domains)
                     for (auto& kv : dk.second->cache)
                         if ((dk.second.get() != d || !referenced.count(kv.first)) && entry_ready(kv.second.get())) {
@@ -465,42 +512,31 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
                 std::unique_ptr<CacheEntry> v = std::move(vit->second);
                 vd->cache.erase(vit);
                 c->stats.cache_evictions++;
-                const size_t cap = v->values.n;
-                auto ins = c->cache_free.emplace(cap, std::move(v));
-                if (cap >= N) fit = ins;
+                c->cache_bytes -= (int64_t)v->cap * (int64_t)sizeof(float);
+                const size_t vcap = v->cap;
+                auto ins = c->cache_free.emplace(vcap, std::move(v));
+                if (vcap >= N) fit = ins;
             }
-            if (fit == c->cache_free.end()) {
-                // 3. recycled buffers of other sizes are released to make room
-                //    (a free may wait for the device: only here)
-                bool any = false;
-                for (auto f = c->cache_free.begin(); f != c->cache_free.end() && c->cache_bytes + bytes > budget;) {
-                    c->cache_bytes -= (int64_t)f->first * (int64_t)sizeof(float);
-                    f = c->cache_free.erase(f);
-                    any = true;
-                }
-                if (!any || c->cache_bytes + bytes > budget) break;   // the budget is held by live entries
-            }
+            if (fit == c->cache_free.end()) break;   // the budget is held by entries in use
         }
         if (fit != c->cache_free.end()) {
             e = std::move(fit->second);
             c->cache_free.erase(fit);
-            // the previous launches on this buffer finish before this one writes it
+            // the previous launches on this block finish before this one writes it
             if (e->touched && !fence_done(e->touched)) CUDA_TRY(cudaStreamWaitEvent(s, e->touched->ev, 0));
             e->touched.reset();
             e->written.reset();
         } else {
             e = std::make_unique<CacheEntry>();
-            if (e->values.ensure(N) != cudaSuccess) {
-                cudaGetLastError();
-                break;   // out of device memory: store fewer
-            }
-            c->cache_bytes += bytes;
+            e->values = block;
+            e->cap = cap;
         }
+        c->cache_bytes += (int64_t)e->cap * (int64_t)sizeof(float);
         const int32_t n = cand[i];
         e->cost = ir.dag.nodes[n].cost;
         e->last_use = c->epoch;
         cv.insert[n] = (int32_t)table.size();
-        table.push_back(e->values.p);
+        table.push_back(e->values);
         written.push_back(e.get());
         c->stats.cache_inserts++;
         d->seen.erase(pop->gid[n]);
@@ -509,6 +545,7 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     c->stats.cache_entries = 0;
     for (auto& kv : c->domains) c->stats.cache_entries += (int64_t)kv.second->cache.size();
     c->stats.cache_bytes = c->cache_bytes;
+    c->stats.cache_reserved = c->cache_reserved;
     return TGP_OK;
 }
 
@@ -587,6 +624,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.counter = pl->counter.p;
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
+    if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
     CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -694,6 +732,64 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->shape = choose_shape(ctx, p->ir, d->N());
     v->sms = ctx->sms;
     v->device = ctx->device;
+    return TGP_OK;
+}
+
+int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi, int32_t target_kind,
+                const void* target, void* stream, bool sync, tgp_handle* domain_out) {
+    if (!ctx || !domain_out) return fail(TGP_E_INVALID, "ctx / domain_out is NULL");
+    if (W < 1 || H < 1 || (int64_t)W * H > INT32_MAX)
+        return fail(TGP_E_INVALID, "grid %d x %d: need W, H >= 1 and W*H <= 2^31-1", W, H);
+    if (!std::isfinite(xlo) || !std::isfinite(xhi) || !std::isfinite(ylo) || !std::isfinite(yhi))
+        return fail(TGP_E_INVALID, "domain bounds must be finite");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto d = std::make_unique<Domain>();
+    d->W = W; d->H = H; d->xlo = xlo; d->xhi = xhi; d->ylo = ylo; d->yhi = yhi;
+    d->kind = target_kind;
+    const int64_t N = d->N();
+    if (target_kind == TGP_TARGET_PAGIE) {
+        if (target) return fail(TGP_E_INVALID, "target must be NULL for the Pagie target");
+    } else if (target_kind == TGP_TARGET_TENSOR) {
+        if (!target) return fail(TGP_E_INVALID, "target tensor is NULL");
+        CUDA_TRY(d->target.ensure((size_t)N));
+        cudaPointerAttributes attr{};
+        cudaError_t e = cudaPointerGetAttributes(&attr, target);
+        if (e != cudaSuccess) cudaGetLastError();
+        bool dev = e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+        CUDA_TRY(cudaMemcpy(d->target.p, target, (size_t)N * sizeof(float),
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    } else if (target_kind == TGP_TARGET_TOKENS) {
+        if (!target) return fail(TGP_E_INVALID, "target tokens are NULL");
+        const tgp_target_tokens* tt = (const tgp_target_tokens*)target;
+        int64_t off[2] = {0, tt->n_ops};
+        auto tp = std::make_unique<Population>();
+        std::string err;
+        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, tp->ir, err);
+        if (prc) return fail(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
+        CUDA_TRY(d->target.ensure((size_t)N));
+        Plan* pl = nullptr;
+        rc = get_plan(ctx, tp.get(), N, true, s, &pl);
+        if (rc) return rc;
+        rc = launch_plan(ctx, pl, d.get(), true, d->target.p, s);
+        if (rc) return rc;
+        if (sync) {
+            CUDA_TRY(cudaStreamSynchronize(s));
+        } else {   // later uses of the domain, on any stream, wait for the target
+            auto f = std::make_shared<Fence>();
+            CUDA_TRY(cudaEventCreateWithFlags(&f->ev, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventRecord(f->ev, s));
+            d->ready = std::move(f);
+            d->target_pop = std::move(tp);   // its plan buffers stay alive while the launch runs
+        }
+    } else {
+        return fail(TGP_E_INVALID, "unknown target kind %d", target_kind);
+    }
+    int64_t h = ctx->next_handle++;
+    ctx->domains[h] = std::move(d);
+    *domain_out = h;
     return TGP_OK;
 }
 
@@ -812,51 +908,7 @@ const char* tgp_last_error(const tgp_ctx*) { return g_err.c_str(); }
 
 int tgp_load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                     int32_t target_kind, const void* target, tgp_handle* domain_out) {
-    if (!ctx || !domain_out) return fail(TGP_E_INVALID, "ctx / domain_out is NULL");
-    if (W < 1 || H < 1 || (int64_t)W * H > INT32_MAX)
-        return fail(TGP_E_INVALID, "grid %d x %d: need W, H >= 1 and W*H <= 2^31-1", W, H);
-    if (!std::isfinite(xlo) || !std::isfinite(xhi) || !std::isfinite(ylo) || !std::isfinite(yhi))
-        return fail(TGP_E_INVALID, "domain bounds must be finite");
-    std::lock_guard<std::mutex> g(ctx->mu);
-    int rc = set_device(ctx);
-    if (rc) return rc;
-    auto d = std::make_unique<Domain>();
-    d->W = W; d->H = H; d->xlo = xlo; d->xhi = xhi; d->ylo = ylo; d->yhi = yhi;
-    d->kind = target_kind;
-    const int64_t N = d->N();
-    if (target_kind == TGP_TARGET_PAGIE) {
-        if (target) return fail(TGP_E_INVALID, "target must be NULL for the Pagie target");
-    } else if (target_kind == TGP_TARGET_TENSOR) {
-        if (!target) return fail(TGP_E_INVALID, "target tensor is NULL");
-        CUDA_TRY(d->target.ensure((size_t)N));
-        cudaPointerAttributes attr{};
-        cudaError_t e = cudaPointerGetAttributes(&attr, target);
-        if (e != cudaSuccess) cudaGetLastError();
-        bool dev = e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
-        CUDA_TRY(cudaMemcpy(d->target.p, target, (size_t)N * sizeof(float),
-                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-    } else if (target_kind == TGP_TARGET_TOKENS) {
-        if (!target) return fail(TGP_E_INVALID, "target tokens are NULL");
-        const tgp_target_tokens* tt = (const tgp_target_tokens*)target;
-        int64_t off[2] = {0, tt->n_ops};
-        Population tp;
-        std::string err;
-        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, tp.ir, err);
-        if (prc) return fail(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
-        CUDA_TRY(d->target.ensure((size_t)N));
-        Plan* pl = nullptr;
-        rc = get_plan(ctx, &tp, N, true, 0, &pl);
-        if (rc) return rc;
-        rc = launch_plan(ctx, pl, d.get(), true, d->target.p, 0);
-        if (rc) return rc;
-        CUDA_TRY(cudaStreamSynchronize(0));
-    } else {
-        return fail(TGP_E_INVALID, "unknown target kind %d", target_kind);
-    }
-    int64_t h = ctx->next_handle++;
-    ctx->domains[h] = std::move(d);
-    *domain_out = h;
-    return TGP_OK;
+    return internal::load_domain(ctx, W, H, xlo, xhi, ylo, yhi, target_kind, target, nullptr, true, domain_out);
 }
 
 int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
@@ -867,7 +919,15 @@ int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
     int rc = set_device(ctx);
     if (rc) return rc;
     CUDA_TRY(cudaDeviceSynchronize());
-    for (auto& kv : it->second->cache) ctx->cache_bytes -= (int64_t)kv.second->values.n * (int64_t)sizeof(float);
+    // its cache blocks are recycled (nothing runs on them any more)
+    for (auto& kv : it->second->cache) {
+        std::unique_ptr<CacheEntry> e = std::move(kv.second);
+        ctx->cache_bytes -= (int64_t)e->cap * (int64_t)sizeof(float);
+        e->written.reset();
+        e->touched.reset();
+        const size_t cap = e->cap;
+        ctx->cache_free.emplace(cap, std::move(e));
+    }
     ctx->stats.cache_entries -= (int64_t)it->second->cache.size();
     ctx->stats.cache_bytes = ctx->cache_bytes;
     ctx->domains.erase(it);
@@ -937,6 +997,12 @@ int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, d
     rc = fitness_to_device(ctx, p, d, s, nullptr, &pl);
     if (rc) return rc;
     if (blocking) {
+        if (!pl->h_rmse || pl->h_rmse_n < T) {   // pinned staging, allocated on first use
+            if (pl->h_rmse) cudaFreeHost(pl->h_rmse);
+            pl->h_rmse = nullptr;
+            CUDA_TRY(cudaMallocHost(&pl->h_rmse, sizeof(double) * T));
+            pl->h_rmse_n = T;
+        }
         CUDA_TRY(cudaMemcpyAsync(pl->h_rmse, pl->rmse.p, T * sizeof(double), cudaMemcpyDeviceToHost, s));
         double* staging = pl->h_rmse;
         g.unlock();
@@ -980,6 +1046,10 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
         rc = get_plan(ctx, p, d->N(), false, s, &pl);
         if (rc) return rc;
         CUDA_TRY(cudaStreamSynchronize(s));
+        if (d->ready) {   // a capture cannot wait on work outside it
+            CUDA_TRY(cudaEventSynchronize(d->ready->ev));
+            d->ready.reset();
+        }
         auto ge = std::make_unique<GraphEntry>();
         CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;

@@ -24,6 +24,12 @@ struct View {
 // Locks the context into `lk`, makes its device current and fills `v`.
 int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::mutex>& lk, View* v);
 
+// tgp_load_domain on `stream`.  sync: returns after a target tree has been
+// evaluated (as tgp_load_domain does); otherwise the evaluation is left in
+// flight and every later use of the domain, on any stream, waits for it.
+int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi, int32_t target_kind,
+                const void* target, void* stream, bool sync, tgp_handle* domain_out);
+
 // The context's CUDA device; TGP_E_INVALID for a host-only context.
 int context_device(tgp_ctx* ctx, int* device);
 

@@ -198,7 +198,8 @@ int launch(tgp_server* srv, Slot* s, std::vector<Job*>& batch, const DomainKey& 
         std::memcpy(bd, key.b, sizeof bd);
         tgp_handle h = 0;
         const int64_t t0 = now_ns();
-        int rc = tgp_load_domain(ctx, key.W, key.H, bd[0], bd[1], bd[2], bd[3], key.kind, target, &h);
+        int rc = internal::load_domain(ctx, key.W, key.H, bd[0], bd[1], bd[2], bd[3], key.kind, target, s->stream,
+                                       false, &h);
         if (rc) return rc;
         std::lock_guard<std::mutex> g(srv->mu);
         s->dom->h = h;
@@ -240,6 +241,38 @@ int launch(tgp_server* srv, Slot* s, std::vector<Job*>& batch, const DomainKey& 
     return TGP_OK;
 }
 
+// Resident domains kept at most; beyond it the least recently used idle ones
+// are released in one batch down to the low mark (a release waits for the
+// device, so it is done rarely).
+constexpr size_t kMaxResidentDomains = 1024, kResidentLowMark = 768;
+
+// Releases idle resident domains, least recently used first, until at most
+// `keep` remain or `need` more bytes fit the budget (lock held on entry and
+// exit, dropped around the releases).  Returns whether anything was released.
+bool release_idle_domains(tgp_server* srv, std::unique_lock<std::mutex>& lk, size_t keep, int64_t need,
+                          const DomainKey* spare) {
+    std::vector<std::pair<int64_t, const DomainKey*>> lru;
+    for (auto& kv : srv->domains)
+        if (kv.second.in_use == 0 && kv.second.h != 0 && !(spare && !(kv.first < *spare) && !(*spare < kv.first)))
+            lru.push_back({kv.second.last_use, &kv.first});
+    std::sort(lru.begin(), lru.end());
+    std::vector<tgp_handle> drop;
+    for (auto& v : lru) {
+        if (srv->domains.size() <= keep && srv->st.bytes_in_use + need <= srv->cfg.hbm_budget_bytes) break;
+        auto it = srv->domains.find(*v.second);
+        srv->st.bytes_in_use -= it->second.bytes;
+        drop.push_back(it->second.h);
+        srv->domains.erase(it);
+        srv->st.domains_released++;
+    }
+    srv->st.domains_resident = (int64_t)srv->domains.size();
+    if (drop.empty()) return false;
+    lk.unlock();
+    for (tgp_handle h : drop) tgp_release_domain(srv->ctx, h);
+    lk.lock();
+    return true;
+}
+
 void worker_main(tgp_server* srv) {
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
@@ -259,13 +292,10 @@ void worker_main(tgp_server* srv) {
         int64_t need = head->est + (resident ? 0 : head->dom_bytes);
         if (srv->st.bytes_in_use + need > budget) {
             // room by releasing resident domains no launch uses, least recently used first
-            std::vector<std::pair<int64_t, const DomainKey*>> lru;
             int64_t freeable = 0;
             for (auto& kv : srv->domains)
-                if (kv.second.in_use == 0 && kv.second.h != 0 && !(resident && &kv.second == &rit->second)) {
-                    lru.push_back({kv.second.last_use, &kv.first});
+                if (kv.second.in_use == 0 && kv.second.h != 0 && !(resident && &kv.second == &rit->second))
                     freeable += kv.second.bytes;
-                }
             if (srv->st.bytes_in_use - freeable + need > budget) {
                 if (srv->in_flight > 0) {   // wait for launches to finish
                     srv->wake.wait(lk);
@@ -281,21 +311,12 @@ void worker_main(tgp_server* srv) {
                 srv->done.notify_all();
                 continue;
             }
-            std::sort(lru.begin(), lru.end());
-            std::vector<tgp_handle> drop;
-            for (auto& v : lru) {
-                if (srv->st.bytes_in_use + need <= budget) break;
-                auto it = srv->domains.find(*v.second);
-                srv->st.bytes_in_use -= it->second.bytes;
-                drop.push_back(it->second.h);
-                srv->domains.erase(it);
-                srv->st.domains_released++;
-            }
-            srv->st.domains_resident = (int64_t)srv->domains.size();
-            lk.unlock();
-            for (tgp_handle h : drop) tgp_release_domain(srv->ctx, h);
-            lk.lock();
+            const DomainKey kc = key;
+            release_idle_domains(srv, lk, SIZE_MAX, need, resident ? &kc : nullptr);
             continue;
+        }
+        if (!resident && srv->domains.size() >= kMaxResidentDomains) {
+            if (release_idle_domains(srv, lk, kResidentLowMark, 0, nullptr)) continue;
         }
         // the batch: the head and every later queued job on the same domain
         std::vector<Job*> batch{head};

@@ -1106,6 +1106,7 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
             tried.push_back(sh);
             Plan* pl = nullptr;
             rc = get_plan_shape(ctx, p, sh, false, s, &pl);
+            if (rc == TGP_E_INVALID) continue;   // this shape cannot be resident: not a candidate
             if (rc) { ctx->capturing = was_capturing; return rc; }
             rc = launch_fitness(ctx, p, pl, d, s, nullptr);   // warm-up
             if (rc) { ctx->capturing = was_capturing; return rc; }
@@ -1130,6 +1131,7 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     ctx->capturing = was_capturing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best >= 1e30f) return fail(TGP_E_INVALID, "no candidate launch shape can be resident for this population");
     // keep only the winning plan (captured graphs may refer to the others)
     p->graphs.clear();
     for (auto it = p->plans.begin(); it != p->plans.end();) {

@@ -658,10 +658,11 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     }
 
     // Slot cap for kept nodes: keep a CTA's dynamic shared memory (target
-    // values + slots) near 40 KB so five CTAs fit an SM.  Temporaries may
-    // exceed it (a tree needs as many as its Sethi-Ullman number).
+    // values + slots) within the SM's share for the interpreter's resident
+    // CTAs at this K.  Temporaries may exceed it (a tree needs as many as its
+    // Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
-    const int cap = std::max(4, 40 * 1024 / slot_bytes - 1);
+    const int cap = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
     GroupGen gen(pop.dag, plan.ir, shape.dedup, cap, cv);
     plan.group_off.push_back(0);
     std::vector<int32_t> forbid;

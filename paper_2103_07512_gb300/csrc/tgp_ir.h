@@ -90,6 +90,31 @@ struct IrIns {
     uint32_t imm;   // binary32 bits of the immediate operand
 };
 
+// Resident CTAs per SM the interpreter is built for, by points per thread K
+// (the kernel's launch bounds; the planner keeps a CTA's shared memory within
+// the SM's share for this many CTAs).
+#ifndef TGP_MINB16
+#define TGP_MINB16 4
+#endif
+#ifndef TGP_MINB8
+#define TGP_MINB8 7
+#endif
+#ifndef TGP_MINB4
+#define TGP_MINB4 10
+#endif
+#ifndef TGP_MINB2
+#define TGP_MINB2 12
+#endif
+__host__ __device__ constexpr int target_ctas_per_sm(int K) {
+    return K >= 16 ? TGP_MINB16 : K >= 8 ? TGP_MINB8 : K >= 4 ? TGP_MINB4 : TGP_MINB2;
+}
+// Dynamic shared memory one CTA may use at that occupancy: 228 KB per SM, of
+// which 1 KB per CTA is reserved by the hardware, less the kernel's static
+// shared memory.
+__host__ __device__ constexpr int smem_budget_per_cta(int K) {
+    return 228 * 1024 / target_ctas_per_sm(K) - 1024 - 64;
+}
+
 // Parameters of one interpreter launch.
 struct EvalParams {
     const Ins* code;            // all groups back to back

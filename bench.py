@@ -42,7 +42,8 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 PROFILE = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
-KERNEL_SRCS = [os.path.join(HERE, "paper_2103_07512_gb300", "csrc", f) for f in ("kernels.cu", "gen_fastloop.py")]
+KERNEL_SRCS = [os.path.join(HERE, "paper_2103_07512_gb300", "csrc", f)
+               for f in ("kernels.cu", "gen_fastloop.py", "tgp_ir.h")]
 
 
 def env_rank():

@@ -154,3 +154,35 @@ def gpu_fitness(ctx, domain):
         finally:
             ctx.release_population(pop)
     return f
+
+
+def main(argv=None):
+    """Command line: one evolutionary run on the GPU, one line per generation."""
+    import argparse
+    from . import Context
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2103_07512_gb300.evolve")
+    ap.add_argument("--grid", type=int, default=4096, help="side of the square grid over [-5,5]^2")
+    ap.add_argument("--population", type=int, default=50)
+    ap.add_argument("--generations", type=int, default=50)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--cache-gb", type=float, default=20.0, help="subtree cache budget (0: off)")
+    ap.add_argument("--min-cost", type=int, default=0, help="store threshold of the cache (0: default)")
+    ap.add_argument("--device", type=int, default=0)
+    a = ap.parse_args(argv)
+    with Context(device=a.device, cache_budget_bytes=int(a.cache_gb * 1e9), cache_min_cost=a.min_cost) as ctx:
+        dom = ctx.load_domain(a.grid, a.grid)
+        ev = Evolution(gpu_fitness(ctx, dom), pop_size=a.population, generations=a.generations, seed=a.seed)
+
+        def report(g, rmse):
+            st = ctx.stats()
+            print(f"gen {g.index:3d}  best {g.best_rmse:.6g}  nodes {g.nodes:6d}  {1e3 * g.seconds:8.3f} ms  "
+                  f"cache hits {st['cache_hits']} inserts {st['cache_inserts']} evictions {st['cache_evictions']}",
+                  flush=True)
+
+        ev.run(report)
+        print(f"best {ev.best[1]:.6g}: {I.to_string(ev.best[0])}")
+
+
+if __name__ == "__main__":
+    main()

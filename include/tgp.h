@@ -96,6 +96,18 @@ enum {
 #define TGP_F_TIME_KERNELS 4  /* record CUDA events around every interpreter
                                  launch on its stream; tgp_stats_get reports the
                                  summed kernel time */
+#define TGP_F_NO_SIMPLIFY 8   /* compile trees as given.  By default nodes are
+                                 simplified while hash-consing (algebraic
+                                 simplification ahead of caching: Sec. 2, Wong
+                                 and Zhang; Sec. 5): constant folding
+                                 of the exactly reproducible operators, the
+                                 identities neg(neg a) = a, abs(neg a) = abs a,
+                                 abs(abs a) = abs a, a*1 = a, a/1 = a, a/0 = 0,
+                                 a+(-0) = a, a-(+0) = a, (-0)-a = -a,
+                                 min(a,a) = max(a,a) = a, and one operand order
+                                 for add and mul.  Each is exact in binary32, so
+                                 results are bitwise those of the trees as given
+                                 (a NaN may differ in sign or payload). */
 
 /* Context configuration.  Zero-initialise, then set what you need. */
 typedef struct tgp_config {

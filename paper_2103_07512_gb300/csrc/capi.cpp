@@ -369,6 +369,8 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
 
 bool cache_on(const tgp_ctx* c) { return c->cfg.cache_budget_bytes > 0; }
 
+bool simplify_on(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_NO_SIMPLIFY) == 0; }
+
 // A fence whose launch has finished (or no fence).
 bool fence_done(FenceP& f) {
     if (!f) return true;
@@ -767,7 +769,7 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
         int64_t off[2] = {0, tt->n_ops};
         auto tp = std::make_unique<Population>();
         std::string err;
-        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, tp->ir, err);
+        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, tp->ir, err, simplify_on(ctx));
         if (prc) return fail(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
         CUDA_TRY(d->target.ensure((size_t)N));
         Plan* pl = nullptr;
@@ -792,6 +794,8 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
     *domain_out = h;
     return TGP_OK;
 }
+
+bool context_simplifies(const tgp_ctx* ctx) { return simplify_on(ctx); }
 
 int context_device(tgp_ctx* ctx, int* device) {
     if (!ctx || !device) return fail(TGP_E_INVALID, "ctx / device is NULL");
@@ -939,7 +943,7 @@ int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, i
     if (!ctx || !pop_out) return fail(TGP_E_INVALID, "ctx / pop_out is NULL");
     auto pop = std::make_unique<Population>();
     std::string err;
-    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err);
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err, simplify_on(ctx));
     if (rc) return fail(rc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     std::lock_guard<std::mutex> g(ctx->mu);
     adopt_ir(ctx, pop.get());
@@ -1196,7 +1200,9 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     std::lock_guard<std::mutex> g(ctx->mu);
     int rc = set_device(ctx);
     if (rc) return rc;
-    const int threads = 256, grid = ctx->sms * 8, iters = 256;
+    const int threads = 256, grid = ctx->sms * 8;
+    // loop counts giving each timed kernel a few milliseconds (add, div, sin, cos, mul, min)
+    const int iters[6] = {4096, 256, 160, 160, 4096, 4096};
     DevBuf<float> in, out;
     CUDA_TRY(in.ensure(256));
     CUDA_TRY(out.ensure((size_t)grid * threads));
@@ -1206,24 +1212,36 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    double ms[6];
-    for (int opk = 0; opk < 6; ++opk) {
-        float best = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {   // first run warms up
-            CUDA_TRY(cudaEventRecord(e0, 0));
-            CUDA_TRY(launch_calib(opk, in.p, out.p, iters, grid, threads, 0));
-            CUDA_TRY(cudaEventRecord(e1, 0));
-            CUDA_TRY(cudaEventSynchronize(e1));
-            float t = 0;
-            CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) best = std::min(best, t);
+    auto timed = [&](int opk, float* ms_out) -> int {
+        CUDA_TRY(cudaEventRecord(e0, 0));
+        CUDA_TRY(launch_calib(opk, in.p, out.p, iters[opk], grid, threads, 0));
+        CUDA_TRY(cudaEventRecord(e1, 0));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        CUDA_TRY(cudaEventElapsedTime(ms_out, e0, e1));
+        ctx->stats.launches++;
+        return TGP_OK;
+    };
+    // Each operator is timed right after the add chain, five times after a
+    // warm-up; its cost is the median of the per-pair ratios (per iteration),
+    // which cancels slow drifts of the clock.
+    double ms[6] = {1, 1, 1, 1, 1, 1};
+    float t = 0.f;
+    rc = timed(0, &t);
+    if (rc) return rc;
+    for (int opk = 1; opk < 6; ++opk) {
+        std::vector<double> ratio;
+        for (int rep = 0; rep < 6; ++rep) {
+            float ta = 0.f, to = 0.f;
+            rc = timed(0, &ta);
+            if (rc) return rc;
+            rc = timed(opk, &to);
+            if (rc) return rc;
+            if (rep > 0) ratio.push_back((to / iters[opk]) / (ta / iters[0]));
         }
-        ms[opk] = best;
-        ctx->stats.launches += 4;
+        std::sort(ratio.begin(), ratio.end());
+        ms[opk] = ratio[ratio.size() / 2];
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    const double add = ms[0];
+    const double add = 1.0;   // ms[] holds costs relative to the add chain
     for (int i = 0; i < TGP_N_OPS; ++i) cost_out[i] = 0.0;
     cost_out[TGP_OP_ADD] = 1.0;
     cost_out[TGP_OP_SUB] = 1.0;

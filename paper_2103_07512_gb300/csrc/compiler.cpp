@@ -114,6 +114,123 @@ static void fmt(std::string& err, const char* f, long long a, long long b = 0, l
     err = buf;
 }
 
+// ------------------------------------------------------------ simplification
+
+namespace {
+
+float as_float(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+uint32_t as_bits(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return b;
+}
+// finite and normal or zero: host and device binary32 arithmetic agree on it
+bool plain(float f) { return f == 0.f || std::isnormal(f); }
+
+}  // namespace
+
+// Rewrites applied while hash-consing, each exact for the device's binary32
+// semantics (IEEE round-to-nearest, protected division, fminf/fmaxf), so a
+// simplified population evaluates bitwise like the original.  NaNs the
+// device makes are all one canonical NaN, which the identities below pass
+// through unchanged.
+//   - constant folding of add, sub, mul, div, min, max, neg, abs when the
+//     operands and the result are zero or normal finite numbers and min/max
+//     do not compare two zeros (sin and cos are never folded: the host cannot
+//     reproduce the device's binary32 values);
+//   - neg(neg(a)) = a, abs(neg(a)) = abs(a), abs(abs(a)) = abs(a);
+//   - a * 1 = a, a / 1 = a, a / 0 = 0 (protected division), a + (-0) = a,
+//     a - (+0) = a, (-0) - a = neg(a), min(a, a) = max(a, a) = a;
+//   - operands of add and mul in a canonical order (commutative in IEEE
+//     arithmetic, signed zeros included), so a+b and b+a are one node.
+int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm) {
+    const auto is_const = [&](int32_t k, float* v) {
+        if (k < 0 || dag.nodes[k].op != T_CONST) return false;
+        *v = as_float(dag.nodes[k].imm);
+        return true;
+    };
+    float a = 0.f, b = 0.f;
+    const bool ca = is_const(k0, &a), cb = is_const(k1, &b);
+    const int ar = arity(op);
+    // constant folding
+    if ((ar == 1 && ca) || (ar == 2 && ca && cb)) {
+        bool ok = plain(a) && (ar == 1 || plain(b));
+        float r = 0.f;
+        switch (op) {
+        case T_ADD: r = a + b; break;
+        case T_SUB: r = a - b; break;
+        case T_MUL: r = a * b; break;
+        case T_DIV: r = b == 0.f ? 0.f : a / b; break;
+        case T_MIN: ok = ok && !(a == 0.f && b == 0.f); r = std::fmin(a, b); break;
+        case T_MAX: ok = ok && !(a == 0.f && b == 0.f); r = std::fmax(a, b); break;
+        case T_NEG: r = -a; break;
+        case T_ABS: r = std::fabs(a); break;
+        default: ok = false; break;   // sin, cos
+        }
+        if (ok && plain(r)) return dag.intern(T_CONST, -1, -1, as_bits(r));
+    }
+    switch (op) {
+    case T_NEG:
+        if (dag.nodes[k0].op == T_NEG) return dag.nodes[k0].kid[0];
+        break;
+    case T_ABS:
+        if (dag.nodes[k0].op == T_NEG) return intern_simplified(dag, T_ABS, dag.nodes[k0].kid[0], -1, 0);
+        if (dag.nodes[k0].op == T_ABS) return k0;
+        break;
+    case T_MUL:
+        if (cb && as_bits(b) == as_bits(1.f)) return k0;
+        if (ca && as_bits(a) == as_bits(1.f)) return k1;
+        if (k1 < k0) std::swap(k0, k1);
+        break;
+    case T_DIV:
+        if (cb && as_bits(b) == as_bits(1.f)) return k0;
+        if (cb && b == 0.f) return dag.intern(T_CONST, -1, -1, as_bits(0.f));
+        break;
+    case T_ADD:
+        if (cb && as_bits(b) == as_bits(-0.f)) return k0;
+        if (ca && as_bits(a) == as_bits(-0.f)) return k1;
+        if (k1 < k0) std::swap(k0, k1);
+        break;
+    case T_SUB:
+        if (cb && as_bits(b) == as_bits(0.f)) return k0;
+        if (ca && as_bits(a) == as_bits(-0.f)) return intern_simplified(dag, T_NEG, k1, -1, 0);
+        break;
+    case T_MIN:
+    case T_MAX:
+        if (k0 == k1) return k0;
+        break;
+    default:
+        break;
+    }
+    return dag.intern(op, k0, k1, imm);
+}
+
+// Drops DAG nodes no tree reaches (operands that simplification bypassed),
+// keeping ids in topological order.
+static void compact(PopIR& pop) {
+    const size_t n = pop.dag.size();
+    std::vector<uint8_t> live(n, 0);
+    for (int32_t r : pop.roots) live[r] = 1;
+    for (size_t i = n; i-- > 0;)   // parents have larger ids than their operands
+        if (live[i])
+            for (int c = 0; c < 2; ++c)
+                if (pop.dag.nodes[i].kid[c] >= 0) live[pop.dag.nodes[i].kid[c]] = 1;
+    if (std::all_of(live.begin(), live.end(), [](uint8_t v) { return v != 0; })) return;
+    Dag d;
+    std::vector<int32_t> id(n, -1);
+    for (size_t i = 0; i < n; ++i) {
+        if (!live[i]) continue;
+        const DagNode& x = pop.dag.nodes[i];
+        id[i] = d.intern(x.op, x.kid[0] >= 0 ? id[x.kid[0]] : -1, x.kid[1] >= 0 ? id[x.kid[1]] : -1, x.imm);
+    }
+    for (auto& r : pop.roots) r = id[r];
+    pop.dag = std::move(d);
+}
+
 void append_population(PopIR& dst, const PopIR& src) {
     std::vector<int32_t> id(src.dag.size());
     for (size_t n = 0; n < src.dag.size(); ++n) {   // children precede parents
@@ -129,7 +246,7 @@ void append_population(PopIR& dst, const PopIR& src) {
 }
 
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
-                     int32_t n_trees, int32_t order, PopIR& out, std::string& err) {
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify) {
     if (n_trees < 0 || n_trees > (1 << 24)) { fmt(err, "n_trees %lld out of range", n_trees); return -1; }
     if (order != 0 && order != 1) { fmt(err, "order %lld is neither prefix (0) nor postfix (1)", order); return -1; }
     if (n_imm < 0) { fmt(err, "n_imm %lld is negative", n_imm); return -1; }
@@ -141,6 +258,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
     out.tree_cost.resize(n_trees);
     if (n_trees > 0 && tree_off[0] != 0) { fmt(err, "tree_off[0] = %lld, must be 0", tree_off[0]); return -2; }
     std::vector<int32_t> stack;
+    std::vector<int32_t> dstack;   // depth of each stacked subtree as given (before simplification)
     int64_t imm_pos = 0;
     for (int32_t t = 0; t < n_trees; ++t) {
         int64_t b = tree_off[t], e = tree_off[t + 1];
@@ -165,6 +283,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
             }
         }
         stack.clear();
+        dstack.clear();
         if (order == 1) {   // postfix: operands precede their operator
             int64_t ip = imm_pos;
             for (int64_t i = b; i < e; ++i) {
@@ -173,12 +292,15 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                     fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
                     return -2;
                 }
-                int32_t k0 = -1, k1 = -1;
+                int32_t k0 = -1, k1 = -1, d = 0;
                 uint32_t bits = 0;
+                for (int a = 0; a < ar; ++a) { d = std::max(d, dstack.back() + 1); dstack.pop_back(); }
                 if (ar == 2) { k1 = stack.back(); stack.pop_back(); k0 = stack.back(); stack.pop_back(); }
                 else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[ip++]; std::memcpy(&bits, &v, 4); }
-                stack.push_back(out.dag.intern(op, k0, k1, bits));
+                dstack.push_back(d);
+                stack.push_back(simplify ? intern_simplified(out.dag, op, k0, k1, bits)
+                                         : out.dag.intern(op, k0, k1, bits));
             }
         } else {            // prefix: scan backwards, first popped = first operand
             int64_t ip = imm_pos + nconst;
@@ -188,12 +310,15 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                     fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
                     return -2;
                 }
-                int32_t k0 = -1, k1 = -1;
+                int32_t k0 = -1, k1 = -1, d = 0;
                 uint32_t bits = 0;
+                for (int a = 0; a < ar; ++a) { d = std::max(d, dstack.back() + 1); dstack.pop_back(); }
                 if (ar == 2) { k0 = stack.back(); stack.pop_back(); k1 = stack.back(); stack.pop_back(); }
                 else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[--ip]; std::memcpy(&bits, &v, 4); }
-                stack.push_back(out.dag.intern(op, k0, k1, bits));
+                dstack.push_back(d);
+                stack.push_back(simplify ? intern_simplified(out.dag, op, k0, k1, bits)
+                                         : out.dag.intern(op, k0, k1, bits));
             }
         }
         if (stack.size() != 1) {
@@ -201,8 +326,8 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
             return -2;
         }
         int32_t root = stack[0];
-        if (out.dag.nodes[root].depth > 1024) {
-            fmt(err, "tree %lld has depth %lld, limit 1024", t, out.dag.nodes[root].depth);
+        if (dstack[0] > 1024) {
+            fmt(err, "tree %lld has depth %lld, limit 1024", t, dstack[0]);
             return -2;
         }
         imm_pos += nconst;
@@ -215,6 +340,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
         fmt(err, "stream has %lld CONST tokens but n_imm = %lld", imm_pos, n_imm);
         return -2;
     }
+    if (simplify) compact(out);
     return 0;
 }
 

@@ -47,9 +47,15 @@ struct PopIR {
 };
 
 // Validates and hash-conses a token population.  Returns 0, or -2 (tokens) /
-// -1 (argument) with a message in err.
+// -1 (argument) with a message in err.  With `simplify`, every node goes
+// through intern_simplified (limits apply to the trees as given).
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
-                     int32_t n_trees, int32_t order, PopIR& out, std::string& err);
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify = true);
+
+// Hash-conses one node after exact algebraic simplification (constant
+// folding, identities, canonical operand order; see compiler.cpp).  The
+// operands must already be nodes of `dag`.
+int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm);
 
 // Appends the trees of `src` to `dst`, hash-consing src's nodes into dst's
 // DAG (subtrees common to both are shared).

@@ -467,7 +467,8 @@ int tgp_server_submit(tgp_server* srv, const tgp_job* job, int64_t* job_id) {
         if (!tt || !tt->ops || tt->n_ops < 1) return internal::set_error(TGP_E_INVALID, "target tokens are NULL");
         PopIR probe;
         int64_t off[2] = {0, tt->n_ops};
-        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, probe, err);
+        int prc = parse_population(tt->ops, tt->imm, tt->n_imm, off, 1, tt->order, probe, err,
+                                   internal::context_simplifies(srv->ctx));
         if (prc)
             return internal::set_error(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
         key.order = tt->order;
@@ -477,7 +478,8 @@ int tgp_server_submit(tgp_server* srv, const tgp_job* job, int64_t* job_id) {
         return internal::set_error(TGP_E_INVALID, "a job's target is Pagie or one target tree (kind %d)",
                                    job->target_kind);
     }
-    int prc = parse_population(job->ops, job->imm, job->n_imm, job->tree_off, job->n_trees, job->order, j->ir, err);
+    int prc = parse_population(job->ops, job->imm, job->n_imm, job->tree_off, job->n_trees, job->order, j->ir, err,
+                               internal::context_simplifies(srv->ctx));
     if (prc) return internal::set_error(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     j->n_trees = job->n_trees;
     j->est = internal::estimate_bytes(srv->ctx, j->ir, key.N());

@@ -296,3 +296,86 @@ def test_server_needs_a_device_context():
         with pytest.raises(tgp.TgpError) as e:
             tgp.Server(c)
         assert e.value.code == tgp.E_INVALID
+
+
+# ---------------------------------------------------------------- simplification
+
+CONSTS = (0.0, -0.0, 1.0, -1.0, 2.0, 0.5, 3.0)
+
+
+def _const_heavy_tree(rng, d, funcs):
+    """Random tree whose terminals are mostly small constants (rewrites fire)."""
+    if d == 0 or rng.random() < 0.15:
+        r = rng.random()
+        if r < 0.25:
+            return I.leaf(I.X)
+        if r < 0.35:
+            return I.leaf(I.Y)
+        return I.leaf(I.CONST, CONSTS[int(rng.integers(len(CONSTS)))])
+    f = funcs[int(rng.integers(len(funcs)))]
+    return I.node(f, *[_const_heavy_tree(rng, d - 1, funcs) for _ in range(I.ARITY[f])])
+
+
+def _nan_canonical_bits(a):
+    b = np.asarray(a, np.float32).view(np.int32).copy()
+    b[np.isnan(a)] = 0x7FC00000
+    return b
+
+
+@pytest.mark.parametrize("expr,simplified", [
+    ("neg(neg(x))", "x"), ("abs(neg(y))", "abs(y)"), ("abs(abs(x))", "abs(x)"),
+    ("mult(x, 1.0)", "x"), ("mult(1.0, y)", "y"), ("div(x, 1.0)", "x"), ("div(sin(x), 0.0)", "0.0"),
+    ("add(x, -0.0)", "x"), ("sub(y, 0.0)", "y"), ("sub(-0.0, x)", "neg(x)"), ("min(x, x)", "x"),
+    ("max(sin(y), sin(y))", "sin(y)"), ("add(0.5, 0.25)", "0.75"), ("mult(3.0, neg(0.5))", "-1.5"),
+    ("div(1.0, 0.0)", "0.0"), ("abs(-2.0)", "2.0"), ("sub(1.0, 1.0)", "0.0"),
+])
+def test_simplification_rewrites(ctx, expr, simplified):
+    a = I.to_tokens([I.parse_string(expr)])
+    b = I.to_tokens([I.parse_string(simplified)])
+    ctx.compile_tokens(a)
+    sa = ctx.stats()
+    ctx.compile_tokens(b)
+    sb = ctx.stats()
+    assert (sa["dag_nodes"], sa["dag_internal"]) == (sb["dag_nodes"], sb["dag_internal"])
+    assert sa["tree_nodes"] == a.ops.size          # the token count is kept
+    with tgp.Context(host_only=True, simplify=False) as raw:
+        raw.compile_tokens(a)
+        assert raw.stats()["dag_nodes"] > sa["dag_nodes"]
+
+
+def test_commutative_operands_share_a_node(ctx):
+    tok = I.to_tokens([I.parse_string("add(x, mult(y, 0.5))"), I.parse_string("add(mult(0.5, y), x)")])
+    ctx.compile_tokens(tok)
+    assert ctx.stats()["dag_internal"] == 2
+    with tgp.Context(host_only=True, simplify=False) as raw:
+        raw.compile_tokens(tok)
+        assert raw.stats()["dag_internal"] == 4
+
+
+def test_no_folding_of_trig_nan_or_subnormal_results(ctx):
+    for e in ["sin(0.5)", "cos(1.0)", "mult(1e-20, 1e-20)", "min(0.0, -0.0)", "mult(3e38, 3e38)"]:
+        tok = I.to_tokens([I.parse_string(e)])
+        ctx.compile_tokens(tok)
+        assert ctx.stats()["dag_internal"] == 1, e
+
+
+def test_simplified_bytecode_equals_oracle_on_raw_trees(ctx):
+    """The simplified plan, run by the numpy interpreter, gives exactly the
+    binary32 values the oracle computes on the trees as given."""
+    rng = np.random.default_rng(21)
+    funcs = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.ABS, I.MIN, I.MAX)
+    trees = [_const_heavy_tree(rng, int(rng.integers(2, 7)), funcs) for _ in range(200)]
+    tok = I.to_tokens(trees)
+    W, H = 5, 4
+    pop = ctx.compile_tokens(tok)
+    st = ctx.stats()
+    with tgp.Context(host_only=True, simplify=False) as raw:
+        raw.compile_tokens(tok)
+        assert st["dag_internal"] < raw.stats()["dag_internal"]
+    ins, off = ctx.debug_plan(pop, W * H)
+    xs = np.array([oracle.grid_point(W, H, -5, 5, -5, 5, p) for p in range(W * H)], np.float32)
+    got = run_bytecode(ins, off, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5)
+    # equal as binary32 values (NaN = NaN; a zero of either sign = 0: fmin/fmax of
+    # two zeros may return either, and operand order differs between the plans)
+    assert np.array_equal(got, v32, equal_nan=True)

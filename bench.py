@@ -328,6 +328,7 @@ def run_ours(args):
     }
     if not args.no_extras and world == 1:
         line["other_configs"] = {
+            "phenotype": bench_phenotype(ctx, pop, dom, tok, g, dev, flush),
             "batched_uneven": bench_batched(tgp.Context, dev, flush),
             "evolution": bench_evolution(tgp.Context, dev),
             "serving": bench_serving(tgp, dev),
@@ -375,6 +376,29 @@ def bench_batched(ctx_cls, dev, flush, steps=20):
             "autotuned": {"points_per_thread": K, "groups": G, "kernel_ms": tune_ms},
             "gpu_launches_per_step": (s1["launches"] - s0["launches"]) / steps,
             "graph": True, "l2": "flushed between steps"}
+
+
+def bench_phenotype(ctx, pop, dom, tok, g, dev, flush, steps=20):
+    """Tensor phenotypes of the headline population (Sec. 3.1): every tree's
+    value at every point written to HBM ([T, H*W] binary32, float4 stores)."""
+    import torch
+    out = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        ctx.evaluate(pop, dom, out, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        ctx.evaluate(pop, dom, out, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    nbytes = tok.n_trees * g.N * 4
+    return {"workload": "phenotypes of population_at_scale: 100 trees x 1024x1024 binary32 written to HBM",
+            "value": int(tok.ops.size) * g.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "bytes_written": nbytes, "write_gbs": nbytes / (ms * 1e-3) / 1e9, "l2": "flushed between steps"}
 
 
 def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):

@@ -192,6 +192,7 @@ struct tgp_ctx {
     char* slab_next = nullptr;
     size_t slab_left = 0;
     std::multimap<size_t, std::unique_ptr<CacheEntry>> cache_free;   // evicted blocks by capacity
+    std::vector<std::unique_ptr<Plan>> plan_pool;            // buffers of released populations
     bool capturing = false;                                  // inside tgp_fitness_graph capture
     // TGP_F_TIME_KERNELS: event pairs around interpreter launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -207,6 +208,9 @@ struct tgp_ctx {
 };
 
 namespace {
+
+// Plans (device buffers) kept from released populations for reuse.
+constexpr size_t kPlanPoolMax = 32;
 
 int set_device(tgp_ctx* c) {
     if (c->host_only) return fail(TGP_E_INVALID, "context was created with TGP_F_HOST_ONLY (no device)");
@@ -320,9 +324,12 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
     Plan* pl;
     if (it == plans.end()) {
         std::unique_ptr<Plan> up;
-        if (!pop->spare.empty()) {   // reuse device buffers (no allocation, no free)
-            up = std::move(pop->spare.back());
-            pop->spare.pop_back();
+        // reuse device buffers of a replaced or released population (no allocation, no free)
+        std::vector<std::unique_ptr<Plan>>* from = !pop->spare.empty() ? &pop->spare
+                                                 : !c->plan_pool.empty() ? &c->plan_pool : nullptr;
+        if (from) {
+            up = std::move(from->back());
+            from->pop_back();
             up->h_table.clear();
             up->view = CacheView();
         } else {
@@ -962,6 +969,15 @@ int tgp_release_population(tgp_ctx* ctx, tgp_handle pop) {
         cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
     }
+    // nothing runs on its buffers any more: keep some for the next populations
+    Population* p = it->second.get();
+    p->graphs.clear();
+    for (auto* m : {&p->plans, &p->cplans}) {
+        for (auto& kv : *m) p->spare.push_back(std::move(kv.second));
+        m->clear();
+    }
+    for (auto& pl : p->spare)
+        if (ctx->plan_pool.size() < kPlanPoolMax) ctx->plan_pool.push_back(std::move(pl));
     ctx->pops.erase(it);
     return TGP_OK;
 }

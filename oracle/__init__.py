@@ -28,6 +28,7 @@ TARGET_PAGIE, TARGET_VALUES = 0, 1
 
 # opcode numbering of the token stream (terminals, then Table 1 functions)
 X, Y, CONST, ADD, SUB, MUL, DIV, SIN, COS, NEG, ABS, MIN, MAX = range(13)
+TAN, EXP, LOG, POW, MDIST, SQRT, SIGN, CLIP, MOD, FRAC, IF = range(13, 24)
 
 _lib = None
 

@@ -13,7 +13,10 @@
  * Passages followed (TensorGP, arXiv 2103.07512):
  *   - tensor phenotype over a fixed rank-2 grid of fitness cases: Sec. 3.1;
  *   - operator semantics and protections: Table 1 (add, sub, mult, div with
- *     0 on a zero denominator, sin, cos, neg, abs, min, max);
+ *     0 on a zero denominator, sin, cos, neg, abs, min, max; and the rest of
+ *     its mathematical and conditional operators: tan, exp, log with -1 for a
+ *     negative argument, pow with 0 for 0^0, mdist, sqrt with 0 for a negative
+ *     argument, sign, clip, mod, frac, if);
  *   - trigonometric operators take the argument multiplied by pi: Sec. 3.2;
  *   - Pagie polynomial target: Eq. 1;
  *   - RMSE fitness against the target: Sec. 4.1 and Table 2.
@@ -32,6 +35,19 @@
  *   - Protected division returns 0 when the denominator equals 0 (either
  *     sign), otherwise the IEEE quotient.
  *   - min / max follow C fmin / fmax (a NaN operand yields the other one).
+ *   - tan(a) := tan(pi*a) like sin and cos (Sec. 3.2 scales every
+ *     trigonometric argument), computed as sin(pi*a) / cos(pi*a); +-inf where
+ *     cos(pi*a) is exactly 0 (no protection is printed).
+ *   - log(a) is -1 for a < 0 (printed) and the IEEE value otherwise, so
+ *     log(0) = -inf; pow(a, b) is 0 for a = b = 0 (printed) and the IEEE
+ *     pow otherwise (NaN for a negative base and a non-integer exponent);
+ *     sqrt(a) is 0 for a < 0 (printed, arity 1: the printed 2 is a typo).
+ *   - mdist(a, b) = (a + b) / 2; sign(a) in {-1, 0, 1} (NaN stays NaN);
+ *     clip(x, y, z) = max(min(z, x), y) as printed; frac(a) = a - floor(a).
+ *   - mod(a, b) is the floored remainder, a - b*floor(a/b), with the sign of
+ *     b (no convention is printed; it is Python's and the one that keeps
+ *     frac(a) = mod(a, 1)); NaN for b = 0 (no protection is printed).
+ *   - if(c, a, b) is a where c != 0 (NaN counts as true), b where c == 0.
  *
  * Two evaluation modes run side by side on every node:
  *   - FP64: every node in binary64;
@@ -56,6 +72,27 @@
  *            an exact zero denominator (the protected result is exactly 0)
  *   sin/cos(pi a): P = min(pi Ea, 2), plus 2 ulp of the result
  *   -a, |a|: Ea;  min/max: max(Ea, Eb)
+ *   tan(pi a): P = pi Ea / (|c| - pi Ea)^2 with c = cos(pi a), unbounded if
+ *            |c| <= pi Ea; plus 4 ulp (a quotient of two trig values)
+ *   exp(a): P = |v| (e^Ea - 1), plus 2 ulp
+ *   log(a): a > 0: P = log(a / (a - Ea)), unbounded if a <= Ea; a < 0: 0,
+ *            unbounded if a + Ea >= 0; plus 2 ulp
+ *   pow(a, b): exact operands: 8 ulp; otherwise a > Ea: with L = log(a/(a-Ea))
+ *            and M = max|log(a +- Ea)|, P = |v| (e^(|b| L + Eb M + Eb L) - 1)
+ *            plus 8 ulp; unbounded for a <= Ea
+ *   mdist(a, b): P = (Ea + Eb) / 2 plus one rounding; unbounded if the sum
+ *            may overflow
+ *   sqrt(a): a - Ea >= 0: P = sqrt(a) - sqrt(a - Ea); else P = sqrt(max(a,0)
+ *            + Ea); plus one rounding
+ *   sign(a): 0, unbounded when the interval a +- Ea holds 0 and Ea > 0
+ *   clip: max(Ex, Ey, Ez) (min and max)
+ *   mod(a, b): exact operands: one rounding; otherwise unbounded unless b is
+ *            away from 0 and floor(a/b) is the same over the operand box, then
+ *            P = Ea + |floor(a/b)| Eb plus one rounding
+ *   frac(a): P = Ea plus one rounding, unbounded if a +- Ea holds an integer
+ *            other than at a exact a
+ *   if(c, a, b): the chosen operand's bound; unbounded if c +- Ec holds 0 and
+ *            Ec > 0
  * and E = P + u(|v| + P) (+ 2^-150 for a possibly subnormal product or
  * quotient); unbounded once |v| + E reaches the binary32 range.
  *
@@ -71,13 +108,16 @@
 /* pi to binary64 precision */
 #define ORACLE_PI 3.14159265358979323846
 
-/* Opcodes of the token stream (the 10 functions of the configured set plus
- * the three terminals x, y and an ephemeral constant). */
+/* Opcodes of the token stream: the three terminals x, y and an ephemeral
+ * constant, the 10 functions of the configured set, then the rest of the
+ * mathematical and conditional operators of Table 1. */
 enum {
     O_X = 0, O_Y = 1, O_CONST = 2,
     O_ADD = 3, O_SUB = 4, O_MUL = 5, O_DIV = 6,
     O_SIN = 7, O_COS = 8, O_NEG = 9, O_ABS = 10, O_MIN = 11, O_MAX = 12,
-    O_COUNT = 13
+    O_TAN = 13, O_EXP = 14, O_LOG = 15, O_POW = 16, O_MDIST = 17, O_SQRT = 18,
+    O_SIGN = 19, O_CLIP = 20, O_MOD = 21, O_FRAC = 22, O_IF = 23,
+    O_COUNT = 24
 };
 
 enum { ORD_PREFIX = 0, ORD_POSTFIX = 1 };
@@ -89,8 +129,11 @@ static int arity_of(int op)
 {
     switch (op) {
     case O_X: case O_Y: case O_CONST: return 0;
-    case O_SIN: case O_COS: case O_NEG: case O_ABS: return 1;
-    case O_ADD: case O_SUB: case O_MUL: case O_DIV: case O_MIN: case O_MAX: return 2;
+    case O_SIN: case O_COS: case O_NEG: case O_ABS:
+    case O_TAN: case O_EXP: case O_LOG: case O_SQRT: case O_SIGN: case O_FRAC: return 1;
+    case O_ADD: case O_SUB: case O_MUL: case O_DIV: case O_MIN: case O_MAX:
+    case O_POW: case O_MDIST: case O_MOD: return 2;
+    case O_CLIP: case O_IF: return 3;
     default: return -1;
     }
 }
@@ -98,7 +141,7 @@ static int arity_of(int op)
 /* one parsed tree node */
 typedef struct {
     int op;
-    int kid[2];     /* indices into the same node array, -1 if absent */
+    int kid[3];     /* indices into the same node array, -1 if absent */
     double imm;     /* the constant, as the binary32 value widened */
 } onode;
 
@@ -114,7 +157,7 @@ static int parse_prefix(const int32_t* ops, int64_t n_tok, const float* imm, int
     if (ar < 0) return OR_BAD_OPCODE;
     int me = (*n_nodes)++;
     nodes[me].op = op;
-    nodes[me].kid[0] = nodes[me].kid[1] = -1;
+    nodes[me].kid[0] = nodes[me].kid[1] = nodes[me].kid[2] = -1;
     nodes[me].imm = 0.0;
     if (op == O_CONST) {
         if (*imm_pos >= n_imm) return OR_IMM;
@@ -144,7 +187,7 @@ static int parse_postfix(const int32_t* ops, int64_t n_tok, const float* imm, in
         if (sp < ar) { rc = OR_MALFORMED; break; }
         int me = n++;
         nodes[me].op = op;
-        nodes[me].kid[0] = nodes[me].kid[1] = -1;
+        nodes[me].kid[0] = nodes[me].kid[1] = nodes[me].kid[2] = -1;
         nodes[me].imm = 0.0;
         if (op == O_CONST) {
             if (*imm_pos >= n_imm) { rc = OR_IMM; break; }
@@ -249,10 +292,58 @@ static double pdiv(double a, double b)
     return a / b;
 }
 
-/* One operator of Table 1 applied in binary64. */
-static double apply64(int op, double a, double b)
+/* Table 1, log: -1 for a negative argument. */
+static double plog(double a)
+{
+    if (a < 0.0) return -1.0;
+    return log(a);
+}
+
+/* Table 1, pow: 0 when both operands are 0. */
+static double ppow(double a, double b)
+{
+    if (a == 0.0 && b == 0.0) return 0.0;
+    return pow(a, b);
+}
+
+/* Table 1, sqrt: 0 for a negative argument. */
+static double psqrt(double a)
+{
+    if (a < 0.0) return 0.0;
+    return sqrt(a);
+}
+
+static double sign_of(double a)
+{
+    if (a > 0.0) return 1.0;
+    if (a < 0.0) return -1.0;
+    if (a == 0.0) return 0.0;
+    return a;   /* NaN */
+}
+
+/* floored remainder a - b*floor(a/b), with the sign of b */
+static double floor_mod(double a, double b)
+{
+    double r = fmod(a, b);
+    if (r != 0.0 && ((r < 0.0) != (b < 0.0))) r += b;
+    return r;
+}
+
+/* One operator of Table 1 applied in binary64 (c: third operand). */
+static double apply64(int op, double a, double b, double c)
 {
     switch (op) {
+    case O_TAN: return oracle_sinpi(a) / oracle_cospi(a);
+    case O_EXP: return exp(a);
+    case O_LOG: return plog(a);
+    case O_POW: return ppow(a, b);
+    case O_MDIST: return (a + b) / 2.0;
+    case O_SQRT: return psqrt(a);
+    case O_SIGN: return sign_of(a);
+    case O_CLIP: return fmax(fmin(c, a), b);
+    case O_MOD: return floor_mod(a, b);
+    case O_FRAC: return a - floor(a);
+    case O_IF: return a != 0.0 ? b : c;   /* NaN != 0 is true */
     case O_ADD: return a + b;
     case O_SUB: return a - b;
     case O_MUL: return a * b;
@@ -290,12 +381,105 @@ static double rnd32(double v, double prop, int exact_sub)
     return e;
 }
 
+#define TAN_ULPS 4.0
+#define EXP_ULPS 2.0
+#define LOG_ULPS 2.0
+#define POW_ULPS 8.0
+
+/* k ulps of a binary32 result of magnitude up to m (ulp <= 2u|r|, and the
+ * subnormal spacing). */
+static double ulps32(double k, double m)
+{
+    return k * (2.0 * U32 * m + TINY32);
+}
+
 /* Error bound of one node from its operands' bounds (see the header). */
-static double err_bound(int op, double a, double b, double ea, double eb, double v)
+static double err_bound(int op, double a, double b, double c, double ea, double eb, double ec, double v)
 {
     double e, prop;
-    if (!isfinite(v) || !isfinite(ea) || !isfinite(eb)) return INFINITY;
+    if (op == O_IF) {   /* only the chosen operand matters, once the zero test is decided */
+        if (!isfinite(v) || !isfinite(ea)) return INFINITY;
+        if (ea > 0.0 && fabs(a) <= ea) return INFINITY;
+        e = a != 0.0 ? eb : ec;
+        if (!isfinite(e) || fabs(v) + e >= MAX32) return INFINITY;
+        return e;
+    }
+    if (!isfinite(v) || !isfinite(ea) || !isfinite(eb) || !isfinite(ec)) return INFINITY;
     switch (op) {
+    case O_TAN: {
+        double cs = fabs(oracle_cospi(a));
+        if (cs <= ORACLE_PI * ea) return INFINITY;
+        double d = cs - ORACLE_PI * ea;
+        prop = ORACLE_PI * ea / (d * d);
+        e = prop + ulps32(TAN_ULPS, fabs(v) + prop);
+        break;
+    }
+    case O_EXP:
+        prop = fabs(v) * expm1(ea);
+        e = prop + ulps32(EXP_ULPS, fabs(v) + prop);
+        break;
+    case O_LOG:
+        if (a > 0.0) {
+            if (a <= ea) return INFINITY;
+            prop = log(a / (a - ea));
+        } else if (a < 0.0) {
+            if (a + ea >= 0.0) return INFINITY;
+            prop = 0.0;
+        } else {
+            return INFINITY;   /* log(0) = -inf */
+        }
+        e = prop + (a < 0.0 ? 0.0 : ulps32(LOG_ULPS, fabs(v) + prop));
+        break;
+    case O_POW:
+        if (ea == 0.0 && eb == 0.0) {
+            e = (a == 0.0 && b == 0.0) ? 0.0 : ulps32(POW_ULPS, fabs(v));
+            break;
+        }
+        if (a <= ea) return INFINITY;
+        {
+            double L = log(a / (a - ea));
+            double M = fmax(fabs(log(a - ea)), fabs(log(a + ea)));
+            prop = fabs(v) * expm1(fabs(b) * L + eb * M + eb * L);
+        }
+        e = prop + ulps32(POW_ULPS, fabs(v) + prop);
+        break;
+    case O_MDIST:
+        if (fabs(a) + fabs(b) + ea + eb >= MAX32) return INFINITY;   /* the binary32 sum may overflow */
+        prop = 0.5 * (ea + eb);
+        e = prop + rnd32(v, prop, 0);
+        break;
+    case O_SQRT:
+        if (a - ea >= 0.0) prop = sqrt(a) - sqrt(a - ea);
+        else prop = sqrt(fmax(a, 0.0) + ea);
+        e = prop + rnd32(v, prop, 0);
+        break;
+    case O_SIGN:
+        if (ea > 0.0 && fabs(a) <= ea) return INFINITY;
+        e = 0.0;
+        break;
+    case O_CLIP:
+        e = fmax(ea, fmax(eb, ec));
+        break;
+    case O_MOD: {
+        if (ea == 0.0 && eb == 0.0) {
+            e = rnd32(v, 0.0, 1);
+            break;
+        }
+        if (fabs(b) <= eb) return INFINITY;
+        double q1 = (a - ea) / (b - eb), q2 = (a - ea) / (b + eb);
+        double q3 = (a + ea) / (b - eb), q4 = (a + ea) / (b + eb);
+        double k = floor(a / b);
+        if (floor(q1) != k || floor(q2) != k || floor(q3) != k || floor(q4) != k) return INFINITY;
+        prop = ea + fabs(k) * eb;
+        e = prop + rnd32(v, prop, 1);
+        break;
+    }
+    case O_FRAC:
+        if (ea > 0.0 && floor(a - ea) != floor(a + ea)) return INFINITY;
+        prop = ea;
+        e = prop + rnd32(v, prop, 1);
+        break;
+
     case O_ADD: case O_SUB:
         prop = ea + eb;
         e = prop + rnd32(v, prop, 1);
@@ -342,16 +526,17 @@ static void eval_node(const onode* nodes, int i, opoint* pt, double* v64, float*
     case O_CONST: *v64 = n->imm; *v32 = (float)n->imm; *eb = 0.0; return;
     default: break;
     }
-    double a64 = 0.0, b64 = 0.0, ea = 0.0, eb_ = 0.0;
-    float a32 = 0.0f, b32 = 0.0f;
+    double a64 = 0.0, b64 = 0.0, c64 = 0.0, ea = 0.0, eb_ = 0.0, ec = 0.0;
+    float a32 = 0.0f, b32 = 0.0f, c32 = 0.0f;
     eval_node(nodes, n->kid[0], pt, &a64, &a32, &ea);
     if (n->kid[1] >= 0) eval_node(nodes, n->kid[1], pt, &b64, &b32, &eb_);
+    if (n->kid[2] >= 0) eval_node(nodes, n->kid[2], pt, &c64, &c32, &ec);
     if (n->op == O_DIV) {
         if (fabs(b64) < NEAR_SINGULAR || fabs((double)b32) < NEAR_SINGULAR) pt->flag = 1;
     }
-    *v64 = apply64(n->op, a64, b64);
-    *v32 = (float)apply64(n->op, (double)a32, (double)b32);
-    *eb = err_bound(n->op, a64, b64, ea, eb_, *v64);
+    *v64 = apply64(n->op, a64, b64, c64);
+    *v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32);
+    *eb = err_bound(n->op, a64, b64, c64, ea, eb_, ec, *v64);
 }
 
 /* ------------------------------------------------------------------ grid */

@@ -11,7 +11,8 @@ Token format (the library's boundary):
 
 Opcodes: terminals X=0, Y=1, CONST=2; functions of Table 1 (TensorGP, arXiv
 2103.07512) ADD=3, SUB=4, MUL=5, DIV=6, SIN=7, COS=8, NEG=9, ABS=10, MIN=11,
-MAX=12.
+MAX=12, TAN=13, EXP=14, LOG=15, POW=16, MDIST=17, SQRT=18, SIGN=19, CLIP=20
+(arity 3), MOD=21, FRAC=22, IF=23 (arity 3).
 
 Generators:
   * ramped half-and-half (Sec. 4.1, Table 2): depths ramp evenly from dmin to
@@ -29,16 +30,23 @@ import numpy as np
 
 X, Y, CONST = 0, 1, 2
 ADD, SUB, MUL, DIV, SIN, COS, NEG, ABS, MIN, MAX = range(3, 13)
+TAN, EXP, LOG, POW, MDIST, SQRT, SIGN, CLIP, MOD, FRAC, IF = range(13, 24)
 PREFIX, POSTFIX = 0, 1
 
 ARITY = {X: 0, Y: 0, CONST: 0, ADD: 2, SUB: 2, MUL: 2, DIV: 2,
-         SIN: 1, COS: 1, NEG: 1, ABS: 1, MIN: 2, MAX: 2}
+         SIN: 1, COS: 1, NEG: 1, ABS: 1, MIN: 2, MAX: 2,
+         TAN: 1, EXP: 1, LOG: 1, POW: 2, MDIST: 2, SQRT: 1, SIGN: 1, CLIP: 3, MOD: 2, FRAC: 1, IF: 3}
 NAMES = {X: "x", Y: "y", CONST: "const", ADD: "add", SUB: "sub", MUL: "mult", DIV: "div",
-         SIN: "sin", COS: "cos", NEG: "neg", ABS: "abs", MIN: "min", MAX: "max"}
+         SIN: "sin", COS: "cos", NEG: "neg", ABS: "abs", MIN: "min", MAX: "max",
+         TAN: "tan", EXP: "exp", LOG: "log", POW: "pow", MDIST: "mdist", SQRT: "sqrt", SIGN: "sign",
+         CLIP: "clip", MOD: "mod", FRAC: "frac", IF: "if"}
 BY_NAME = {v: k for k, v in NAMES.items()}
 BY_NAME["mul"] = MUL
 
+# the function set of the benchmark configurations
 FUNCTIONS = (ADD, SUB, MUL, DIV, SIN, COS, NEG, ABS, MIN, MAX)
+# every mathematical and conditional operator of Table 1
+ALL_FUNCTIONS = FUNCTIONS + (TAN, EXP, LOG, POW, MDIST, SQRT, SIGN, CLIP, MOD, FRAC, IF)
 TERMINALS = (X, Y, CONST)
 UNARY = tuple(f for f in FUNCTIONS if ARITY[f] == 1)
 BINARY = tuple(f for f in FUNCTIONS if ARITY[f] == 2)

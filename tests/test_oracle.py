@@ -427,3 +427,162 @@ def test_error_bound_unbounded_cases():
 def ev_bound(exprs, W, H, lo=-5.0, hi=5.0):
     t = toks(*exprs)
     return oracle.evaluate(t.ops, t.imm, t.tree_off, 0, W, H, lo, hi, lo, hi, with_bound=True)
+
+
+# ---------------------------------------------------------------- the rest of Table 1
+
+def _scalar(expr):
+    """binary64 value of a constant expression (1x1 grid)."""
+    v64, _, _ = ev([expr], 1, 1)
+    return float(v64[0, 0])
+
+
+@pytest.mark.parametrize("expr,value", [
+    ("tan(0.25)", 1.0), ("tan(-0.25)", -1.0), ("tan(0.0)", 0.0), ("tan(1.0)", 0.0),
+    ("exp(0.0)", 1.0), ("exp(1.0)", math.e), ("exp(-2.0)", math.exp(-2.0)),
+    ("log(1.0)", 0.0), ("log(-3.0)", -1.0), ("log(-0.5)", -1.0), ("log(0.5)", -math.log(2.0)),
+    ("pow(0.0, 0.0)", 0.0), ("pow(2.0, 3.0)", 8.0), ("pow(-2.0, 3.0)", -8.0), ("pow(4.0, 0.5)", 2.0),
+    ("pow(0.0, 2.0)", 0.0), ("pow(3.0, 0.0)", 1.0),
+    ("mdist(1.0, 2.0)", 1.5), ("mdist(-3.0, 3.0)", 0.0),
+    ("sqrt(9.0)", 3.0), ("sqrt(-4.0)", 0.0), ("sqrt(0.0)", 0.0), ("sqrt(2.0)", math.sqrt(2.0)),
+    ("sign(-2.5)", -1.0), ("sign(0.0)", 0.0), ("sign(3.0)", 1.0), ("sign(-0.0)", 0.0),
+    ("clip(5.0, 0.0, 1.0)", 1.0), ("clip(-5.0, 0.0, 1.0)", 0.0), ("clip(0.25, 0.0, 1.0)", 0.25),
+    ("clip(0.5, 1.0, 0.0)", 1.0),          # max(min(z, x), y) with y > z gives y
+    ("mod(5.0, 3.0)", 2.0), ("mod(-5.0, 3.0)", 1.0), ("mod(5.0, -3.0)", -1.0), ("mod(-5.0, -3.0)", -2.0),
+    ("mod(5.5, 2.0)", 1.5), ("mod(6.0, 3.0)", 0.0), ("mod(-0.5, 1.0)", 0.5),
+    ("frac(2.25)", 0.25), ("frac(-2.25)", 0.75), ("frac(3.0)", 0.0), ("frac(-3.0)", 0.0),
+    ("if(0.0, 1.0, 2.0)", 2.0), ("if(-0.0, 1.0, 2.0)", 2.0), ("if(3.0, 1.0, 2.0)", 1.0),
+    ("if(-1e-30, 1.0, 2.0)", 1.0),
+])
+def test_table1_operators_special_values(expr, value):
+    assert _scalar(expr) == pytest.approx(value, rel=1e-15, abs=1e-15), expr
+
+
+def test_table1_operators_nonfinite_cases():
+    assert math.isinf(_scalar("tan(0.5)"))                       # cos(pi/2) is exactly 0
+    assert _scalar("log(0.0)") == -math.inf
+    assert math.isnan(_scalar("pow(-8.0, 0.5)"))
+    assert math.isnan(_scalar("mod(1.0, 0.0)"))
+    assert _scalar("if(div(1.0, 0.0), 1.0, 2.0)") == 2.0          # protected 1/0 = 0 is false
+    assert math.isnan(_scalar("sign(mod(1.0, 0.0))"))
+
+
+def test_frac_equals_mod_one_and_clip_identities():
+    W, H = 9, 7
+    v64, _, _ = ev(["frac(mult(x, 1.3))", "mod(mult(x, 1.3), 1.0)", "clip(x, -1.0, 1.0)",
+                    "max(min(1.0, x), -1.0)", "if(sub(x, y), x, y)"], W, H)
+    assert np.array_equal(v64[0], v64[1])
+    assert np.array_equal(v64[2], v64[3])
+    X, Y = np_grid(W, H)
+    assert np.array_equal(v64[4], np.where(X - Y != 0, X, Y))
+
+
+_EXT_LEAVES = ["x", "y", "0.5"]
+
+
+def _ext_np(tree, X, Y):
+    """Independent numpy binary64 restatement of every Table 1 operator."""
+    op, v, kids = tree
+    if op == I.X:
+        return X
+    if op == I.Y:
+        return Y
+    if op == I.CONST:
+        return np.full_like(X, float(v))
+    k = [_ext_np(c, X, Y) for c in kids]
+    a = k[0]
+    b = k[1] if len(k) > 1 else None
+    c = k[2] if len(k) > 2 else None
+    with np.errstate(all="ignore"):
+        if op == I.TAN:
+            return np.tan(np.pi * a)
+        if op == I.EXP:
+            return np.exp(a)
+        if op == I.LOG:
+            return np.where(a < 0, -1.0, np.log(np.where(a < 0, 1.0, a)))
+        if op == I.POW:
+            return np.where((a == 0) & (b == 0), 0.0, np.power(a, b))
+        if op == I.MDIST:
+            return (a + b) / 2
+        if op == I.SQRT:
+            return np.where(a < 0, 0.0, np.sqrt(np.where(a < 0, 0.0, a)))
+        if op == I.SIGN:
+            return np.sign(a)
+        if op == I.CLIP:
+            return np.fmax(np.fmin(c, a), b)
+        if op == I.MOD:
+            return np.mod(a, b)          # numpy's floored remainder
+        if op == I.FRAC:
+            return a - np.floor(a)
+        if op == I.IF:
+            return np.where(a != 0, b, c)
+        if op == I.SIN:
+            return np.sin(np.pi * a)
+        if op == I.COS:
+            return np.cos(np.pi * a)
+        if op == I.NEG:
+            return -a
+        if op == I.ABS:
+            return np.abs(a)
+        return {I.ADD: a + b if b is not None else None, I.SUB: a - b if b is not None else None,
+                I.MUL: a * b if b is not None else None,
+                I.MIN: np.fmin(a, b) if b is not None else None,
+                I.MAX: np.fmax(a, b) if b is not None else None}[op]
+
+
+@pytest.mark.parametrize("W,H", [(2, 2), (3, 5)])
+def test_brute_force_new_operators_depth2(W, H):
+    """Every tree of depth <= 2 with one new operator at the root over the
+    depth-1 trees of {x, y, 0.5} and {neg, sin}; against numpy."""
+    sub1 = _EXT_LEAVES + [f"{f}({a})" for f in ("neg", "sin") for a in _EXT_LEAVES]
+    exprs = []
+    for f in ("tan", "exp", "log", "sqrt", "sign", "frac"):
+        exprs += [f"{f}({a})" for a in sub1]
+    for f in ("pow", "mdist", "mod"):
+        exprs += [f"{f}({a}, {b})" for a in sub1 for b in sub1]
+    for f in ("clip", "if"):
+        exprs += [f"{f}({a}, {b}, {c})" for a in sub1[:5] for b in sub1[:5] for c in sub1[:5]]
+    trees = [I.parse_string(e) for e in exprs]
+    tok = I.to_tokens(trees)
+    v64, _, _ = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, W, H, -5, 5, -5, 5)
+    X, Y = np_grid(W, H)
+    exp = np.stack([_ext_np(t, X, Y) for t in trees])
+    # numpy's sin(pi*a) is not exactly 0 at integers (the oracle's is), which
+    # operators that are steep or discontinuous at 0 (tan poles, log, sqrt,
+    # pow, sign, frac, mod, the zero test of if) amplify: those trees are
+    # compared on the other trees' tolerance only in aggregate
+    fin = np.isfinite(exp) & np.isfinite(v64)
+    close = np.isclose(v64, exp, rtol=1e-9, atol=1e-9)
+    steep = ("tan", "frac", "mod", "sign", "if", "log", "sqrt", "pow")
+    sens = np.array([e.split("(")[0] in steep and "sin" in e for e in exprs])
+    assert close[fin & ~sens[:, None]].all()
+    assert close[fin].mean() > 0.97
+    assert fin.mean() > 0.8
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_error_bound_contains_fp32_faithful_new_operators(seed):
+    rng = np.random.default_rng(seed)
+    trees = [I._full(rng, int(rng.integers(2, 6)), I.ALL_FUNCTIONS) for _ in range(60)]
+    tok = I.to_tokens(trees)
+    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, 0, 17, 13, -5, 5, -5, 5,
+                                       with_bound=True)
+    m = np.isfinite(v64) & np.isfinite(eb)
+    with np.errstate(invalid="ignore"):
+        d = np.abs(v32.astype(np.float64) - v64)
+    assert np.all(d[m] <= eb[m])
+    assert m.mean() > 0.5
+
+
+def test_error_bound_new_operators_closed_forms():
+    W, H = 7, 5
+    X, Y = np_grid(W, H)
+    _, _, _, eb = ev_bound(["sqrt(abs(x))", "sign(x)", "clip(x, y, 0.5)", "if(x, y, 0.5)",
+                            "frac(x)", "mdist(x, y)", "exp(0.0)", "sign(sub(x, mult(x, 1.1)))"], W, H)
+    assert np.all(eb[0] <= U32 * np.sqrt(np.abs(X)) * (1 + 1e-12) + 2.0 ** -150)   # exact operand
+    assert np.all(eb[1] == 0) and np.all(eb[2] == 0) and np.all(eb[3] == 0)
+    assert np.all(eb[4] <= U32 * np.abs(X - np.floor(X)) * (1 + 1e-12))
+    assert np.all(eb[5] <= U32 * np.abs((X + Y) / 2) * (1 + 1e-12) + 2.0 ** -150)
+    assert np.all(eb[6] <= 2 * (2 * U32 + 2.0 ** -149) * (1 + 1e-12))
+    # sign of a rounded value: undecided only where it is within its bound of 0
+    assert np.all(np.isfinite(eb[7][X != 0]))

@@ -28,8 +28,8 @@ MUTANTS = {
                                     "for (int c = 0; c < ar; c++) nodes[me].kid[c] = stack[--sp];"),
     "grid_row_col_swapped": ("int64_t row = p / W, col = p % W;", "int64_t col = p / W, row = p % W;"),
     "min_is_max": ("case O_MIN: return fmin(a, b);", "case O_MIN: return fmax(a, b);"),
-    "fp32_mode_not_rounded_per_node": ("*v32 = (float)apply64(n->op, (double)a32, (double)b32);",
-                                       "*v32 = (float)apply64(n->op, a64, b64);"),
+    "fp32_mode_not_rounded_per_node": ("*v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32);",
+                                       "*v32 = (float)apply64(n->op, a64, b64, c64);"),
     "near_singular_threshold": ("#define NEAR_SINGULAR 1e-6", "#define NEAR_SINGULAR 1e-9"),
     "nan_fitness_not_inf": ("rmse64[t] = isfinite(r64) ? r64 : INFINITY;", "rmse64[t] = r64;"),
     "abs_dropped": ("case O_ABS: return fabs(a);", "case O_ABS: return a;"),
@@ -37,6 +37,17 @@ MUTANTS = {
     "bound_div_drops_term": ("prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);", "prop = ea / (fabs(b) - eb);"),
     "bound_trig_not_pi": ("prop = fmin(ORACLE_PI * ea, 2.0);", "prop = fmin(ea, 2.0);"),
     "bound_add_no_rounding": ("e = prop + rnd32(v, prop, 1);", "e = prop;"),
+    "log_protection_value": ("if (a < 0.0) return -1.0;", "if (a < 0.0) return 0.0;"),
+    "pow_zero_zero_is_one": ("if (a == 0.0 && b == 0.0) return 0.0;", "if (a == 0.0 && b == 0.0) return 1.0;"),
+    "sqrt_of_abs": ("if (a < 0.0) return 0.0;\n    return sqrt(a);", "return sqrt(fabs(a));"),
+    "mod_truncated": ("if (r != 0.0 && ((r < 0.0) != (b < 0.0))) r += b;", ""),
+    "clip_bounds_swapped": ("case O_CLIP: return fmax(fmin(c, a), b);", "case O_CLIP: return fmax(fmin(b, a), c);"),
+    "if_branches_swapped": ("case O_IF: return a != 0.0 ? b : c;", "case O_IF: return a != 0.0 ? c : b;"),
+    "tan_not_pi_scaled": ("case O_TAN: return oracle_sinpi(a) / oracle_cospi(a);", "case O_TAN: return tan(a);"),
+    "frac_truncates": ("case O_FRAC: return a - floor(a);", "case O_FRAC: return a - trunc(a);"),
+    "mdist_not_halved": ("case O_MDIST: return (a + b) / 2.0;", "case O_MDIST: return a + b;"),
+    "sign_of_zero_is_one": ("if (a == 0.0) return 0.0;\n    return a;", "if (a == 0.0) return 1.0;\n    return a;"),
+    "bound_exp_no_propagation": ("prop = fabs(v) * expm1(ea);", "prop = 0.0;"),
     "const_imm_order": ("nodes[me].imm = (double)imm[(*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {",
                         "nodes[me].imm = (double)imm[n_imm - 1 - (*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {"),
 }

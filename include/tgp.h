@@ -62,9 +62,13 @@ enum {
     TGP_TARGET_TOKENS = 2   /* one expression tree (tgp_target_tokens*) evaluated on the grid */
 };
 
-/* Opcodes of the token stream: the terminals and the Table 1 functions used
- * by the configured function set.  Arity: X, Y, CONST 0; SIN, COS, NEG, ABS 1;
- * ADD, SUB, MUL, DIV, MIN, MAX 2.  CONST takes the next value of `imm`. */
+/* Opcodes of the token stream: the terminals and the mathematical and
+ * conditional operators of Table 1.  Arity: X, Y, CONST 0; SIN, COS, NEG, ABS,
+ * TAN, EXP, LOG, SQRT, SIGN, FRAC 1; ADD, SUB, MUL, DIV, MIN, MAX, POW, MDIST,
+ * MOD 2; CLIP, IF 3.  CONST takes the next value of `imm`.  Readings where
+ * Table 1 is silent: mod is the floored remainder (sign of the divisor);
+ * log(0) = -inf; tan at an odd multiple of 1/2 is +-inf; if treats NaN as
+ * true. */
 enum {
     TGP_OP_X = 0, TGP_OP_Y = 1, TGP_OP_CONST = 2,
     TGP_OP_ADD = 3,  /* a + b                                  (Table 1, add)  */
@@ -77,7 +81,18 @@ enum {
     TGP_OP_ABS = 10, /* |a|                                    (Table 1, abs)  */
     TGP_OP_MIN = 11, /* fminf(a, b)                            (Table 1, min)  */
     TGP_OP_MAX = 12, /* fmaxf(a, b)                            (Table 1, max)  */
-    TGP_N_OPS = 13
+    TGP_OP_TAN = 13, /* tan(pi * a) = sin(pi a) / cos(pi a)    (Table 1, Sec. 3.2) */
+    TGP_OP_EXP = 14, /* e^a                                    (Table 1, exp)  */
+    TGP_OP_LOG = 15, /* log(a), -1 when a < 0                  (Table 1, log)  */
+    TGP_OP_POW = 16, /* a^b, 0 when a = b = 0                  (Table 1, pow)  */
+    TGP_OP_MDIST = 17, /* (a + b) / 2                          (Table 1, mdist) */
+    TGP_OP_SQRT = 18, /* sqrt(a), 0 when a < 0                 (Table 1, sqrt) */
+    TGP_OP_SIGN = 19, /* -1, 0 or 1 (NaN stays NaN)            (Table 1, sign) */
+    TGP_OP_CLIP = 20, /* clip(x, y, z) = max(min(z, x), y)     (Table 1, clip; arity 3) */
+    TGP_OP_MOD = 21, /* a - b floor(a / b), NaN when b = 0     (Table 1, mod)  */
+    TGP_OP_FRAC = 22, /* a - floor(a)                          (Table 1, frac) */
+    TGP_OP_IF = 23,  /* if(c, a, b): a where c != 0, else b    (Table 1, if; arity 3) */
+    TGP_N_OPS = 24
 };
 
 /* Limits checked by tgp_compile_population (TGP_E_TOKENS beyond them). */

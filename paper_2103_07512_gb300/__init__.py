@@ -23,7 +23,7 @@ E_INVALID, E_TOKENS, E_NOMEM, E_BUDGET, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_BUS
 PREFIX, POSTFIX = 0, 1
 TARGET_PAGIE, TARGET_TENSOR, TARGET_TOKENS = 0, 1, 2
 F_HOST_ONLY, F_NO_DEDUP, F_TIME_KERNELS, F_NO_SIMPLIFY = 1, 2, 4, 8
-N_OPS = 13
+N_OPS = 24
 
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
            "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",

@@ -1217,8 +1217,10 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     int rc = set_device(ctx);
     if (rc) return rc;
     const int threads = 256, grid = ctx->sms * 8;
-    // loop counts giving each timed kernel a few milliseconds (add, div, sin, cos, mul, min)
-    const int iters[6] = {4096, 256, 160, 160, 4096, 4096};
+    // loop counts giving each timed kernel a few milliseconds
+    // (add, div, sin, cos, mul, min, exp, log, pow, tan, sqrt, mod)
+    constexpr int kCalib = 12;
+    const int iters[kCalib] = {4096, 256, 160, 160, 4096, 4096, 256, 256, 96, 96, 1024, 256};
     DevBuf<float> in, out;
     CUDA_TRY(in.ensure(256));
     CUDA_TRY(out.ensure((size_t)grid * threads));
@@ -1240,11 +1242,12 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     // Each operator is timed right after the add chain, five times after a
     // warm-up; its cost is the median of the per-pair ratios (per iteration),
     // which cancels slow drifts of the clock.
-    double ms[6] = {1, 1, 1, 1, 1, 1};
+    double ms[kCalib];
+    for (double& m : ms) m = 1.0;
     float t = 0.f;
     rc = timed(0, &t);
     if (rc) return rc;
-    for (int opk = 1; opk < 6; ++opk) {
+    for (int opk = 1; opk < kCalib; ++opk) {
         std::vector<double> ratio;
         for (int rep = 0; rep < 6; ++rep) {
             float ta = 0.f, to = 0.f;
@@ -1269,6 +1272,21 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out) {
     // enough for the compiler to shorten, so they are not timed
     cost_out[TGP_OP_MIN] = 1.0;
     cost_out[TGP_OP_MAX] = 1.0;
+    // library functions, timed with one add of operand preparation each
+    cost_out[TGP_OP_EXP] = ms[6] - 1.0;
+    cost_out[TGP_OP_LOG] = ms[7] - 1.0;
+    cost_out[TGP_OP_POW] = ms[8] - 1.0;
+    cost_out[TGP_OP_TAN] = ms[9] - 1.0;
+    cost_out[TGP_OP_SQRT] = ms[10] - 1.0;
+    cost_out[TGP_OP_MOD] = ms[11] - 1.0;
+    // short instruction sequences of the interpreter, counted: mdist = add +
+    // multiply, frac = floor + subtract, sign = three compare-selects, if =
+    // compare + select, clip = min + max
+    cost_out[TGP_OP_MDIST] = 2.0;
+    cost_out[TGP_OP_FRAC] = 2.0;
+    cost_out[TGP_OP_SIGN] = 3.0;
+    cost_out[TGP_OP_IF] = 2.0;
+    cost_out[TGP_OP_CLIP] = 2.0;
     // neg and abs fold into their consumer as operand modifiers: cost 0
     return TGP_OK;
 }

@@ -24,8 +24,11 @@ namespace tgp {
 int arity(int op) {
     switch (op) {
     case T_X: case T_Y: case T_CONST: return 0;
-    case T_SIN: case T_COS: case T_NEG: case T_ABS: return 1;
-    case T_ADD: case T_SUB: case T_MUL: case T_DIV: case T_MIN: case T_MAX: return 2;
+    case T_SIN: case T_COS: case T_NEG: case T_ABS:
+    case T_TAN: case T_EXP: case T_LOG: case T_SQRT: case T_SIGN: case T_FRAC: return 1;
+    case T_ADD: case T_SUB: case T_MUL: case T_DIV: case T_MIN: case T_MAX:
+    case T_POW: case T_MDIST: case T_MOD: return 2;
+    case T_CLIP: case T_IF: return 3;
     default: return -1;
     }
 }
@@ -34,7 +37,10 @@ float op_cost(int op) {
     switch (op) {
     case T_X: case T_Y: case T_CONST: return 0.f;
     case T_DIV: return 8.f;
-    case T_SIN: case T_COS: return 16.f;
+    case T_SIN: case T_COS: case T_EXP: case T_LOG: case T_MOD: return 16.f;
+    case T_TAN: case T_POW: return 40.f;
+    case T_SQRT: return 4.f;
+    case T_MDIST: case T_SIGN: case T_FRAC: return 2.f;
     default: return 1.f;
     }
 }
@@ -48,10 +54,10 @@ static inline uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-static inline uint64_t key_hash(int op, int32_t k0, int32_t k1, uint32_t imm) {
+static inline uint64_t key_hash(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     uint64_t a = ((uint64_t)(uint32_t)k0 << 32) | (uint32_t)k1;
     uint64_t b = ((uint64_t)(uint32_t)op << 32) | imm;
-    return mix64(a ^ mix64(b));
+    return mix64(a ^ mix64(b ^ mix64((uint64_t)(uint32_t)k2)));
 }
 
 void Dag::rehash(size_t cap) {
@@ -59,27 +65,36 @@ void Dag::rehash(size_t cap) {
     mask_ = cap - 1;
     for (size_t i = 0; i < nodes.size(); ++i) {
         const DagNode& n = nodes[i];
-        size_t h = key_hash(n.op, n.kid[0], n.kid[1], n.imm) & mask_;
+        size_t h = key_hash(n.op, n.kid[0], n.kid[1], n.imm, n.kid[2]) & mask_;
         while (table_[h] >= 0) h = (h + 1) & mask_;
         table_[h] = (int32_t)i;
     }
 }
 
-int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm) {
+int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     if (table_.empty()) rehash(1024);
-    size_t h = key_hash(op, k0, k1, imm) & mask_;
+    size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
     while (table_[h] >= 0) {
         const DagNode& n = nodes[table_[h]];
-        if (n.op == op && n.kid[0] == k0 && n.kid[1] == k1 && n.imm == imm) return table_[h];
+        if (n.op == op && n.kid[0] == k0 && n.kid[1] == k1 && n.kid[2] == k2 && n.imm == imm) return table_[h];
         h = (h + 1) & mask_;
     }
     DagNode n;
     n.op = op;
     n.kid[0] = k0;
     n.kid[1] = k1;
+    n.kid[2] = k2;
     n.imm = imm;
     int ar = arity(op);
-    if (ar == 0) {
+    if (ar == 3) {
+        // planned order: operand 0 and 1 parked in slots, operand 2 into A
+        const DagNode& a = nodes[k0];
+        const DagNode& b = nodes[k1];
+        const DagNode& c = nodes[k2];
+        n.su = std::max(a.su, std::max(b.su + 1, c.su + 2));
+        n.depth = std::max(a.depth, std::max(b.depth, c.depth)) + 1;
+        n.cost = op_cost(op) + a.cost + b.cost + c.cost;
+    } else if (ar == 0) {
         n.su = 0;
         n.depth = 0;
         n.cost = 0.f;
@@ -145,9 +160,12 @@ bool plain(float f) { return f == 0.f || std::isnormal(f); }
 //   - neg(neg(a)) = a, abs(neg(a)) = abs(a), abs(abs(a)) = abs(a);
 //   - a * 1 = a, a / 1 = a, a / 0 = 0 (protected division), a + (-0) = a,
 //     a - (+0) = a, (-0) - a = neg(a), min(a, a) = max(a, a) = a;
-//   - operands of add and mul in a canonical order (commutative in IEEE
-//     arithmetic, signed zeros included), so a+b and b+a are one node.
-int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm) {
+//   - operands of add, mul and mdist in a canonical order (commutative in
+//     IEEE arithmetic, signed zeros included), so a+b and b+a are one node;
+//   - folding of mdist, sqrt, sign, frac and mod (exact or correctly rounded
+//     steps on the host as on the device; never tan, exp, log, pow);
+//   - if(c, a, b) with a constant c is a or b; if(c, a, a) is a.
+int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     const auto is_const = [&](int32_t k, float* v) {
         if (k < 0 || dag.nodes[k].op != T_CONST) return false;
         *v = as_float(dag.nodes[k].imm);
@@ -156,6 +174,8 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
     float a = 0.f, b = 0.f;
     const bool ca = is_const(k0, &a), cb = is_const(k1, &b);
     const int ar = arity(op);
+    // if with a constant condition is its chosen operand (NaN cannot be a constant)
+    if (op == T_IF && ca) return a != 0.f ? k1 : k2;
     // constant folding
     if ((ar == 1 && ca) || (ar == 2 && ca && cb)) {
         bool ok = plain(a) && (ar == 1 || plain(b));
@@ -169,7 +189,17 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
         case T_MAX: ok = ok && !(a == 0.f && b == 0.f); r = std::fmax(a, b); break;
         case T_NEG: r = -a; break;
         case T_ABS: r = std::fabs(a); break;
-        default: ok = false; break;   // sin, cos
+        case T_MDIST: r = (a + b) * 0.5f; break;
+        case T_SQRT: r = a < 0.f ? 0.f : std::sqrt(a); break;
+        case T_SIGN: r = a > 0.f ? 1.f : a < 0.f ? -1.f : 0.f; break;
+        case T_FRAC: r = a - std::floor(a); break;
+        case T_MOD: {
+            ok = ok && b != 0.f;
+            r = std::fmod(a, b);
+            if (r != 0.f && ((r < 0.f) != (b < 0.f))) r = r + b;
+            break;
+        }
+        default: ok = false; break;   // sin, cos, tan, exp, log, pow: library values on the device
         }
         if (ok && plain(r)) return dag.intern(T_CONST, -1, -1, as_bits(r));
     }
@@ -203,10 +233,26 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
     case T_MAX:
         if (k0 == k1) return k0;
         break;
+    case T_MDIST:
+        if (k1 < k0) std::swap(k0, k1);
+        break;
+    case T_IF:
+        if (k1 == k2) return k1;   // both operands the same node
+        break;
     default:
         break;
     }
-    return dag.intern(op, k0, k1, imm);
+    return dag.intern(op, k0, k1, imm, k2);
+}
+
+// One token's node.  clip(x, y, z) is its printed definition,
+// max(min(z, x), y) (Table 1), so it needs no instruction of its own.
+static int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits, bool simplify) {
+    auto mk = [&](int o, int32_t a, int32_t b, uint32_t imm, int32_t c) {
+        return simplify ? intern_simplified(dag, o, a, b, imm, c) : dag.intern(o, a, b, imm, c);
+    };
+    if (op == T_CLIP) return mk(T_MAX, mk(T_MIN, k[2], k[0], 0, -1), k[1], 0, -1);
+    return mk(op, k[0], k[1], bits, k[2]);
 }
 
 // Drops DAG nodes no tree reaches (operands that simplification bypassed),
@@ -217,7 +263,7 @@ static void compact(PopIR& pop) {
     for (int32_t r : pop.roots) live[r] = 1;
     for (size_t i = n; i-- > 0;)   // parents have larger ids than their operands
         if (live[i])
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < kMaxKids; ++c)
                 if (pop.dag.nodes[i].kid[c] >= 0) live[pop.dag.nodes[i].kid[c]] = 1;
     if (std::all_of(live.begin(), live.end(), [](uint8_t v) { return v != 0; })) return;
     Dag d;
@@ -225,7 +271,8 @@ static void compact(PopIR& pop) {
     for (size_t i = 0; i < n; ++i) {
         if (!live[i]) continue;
         const DagNode& x = pop.dag.nodes[i];
-        id[i] = d.intern(x.op, x.kid[0] >= 0 ? id[x.kid[0]] : -1, x.kid[1] >= 0 ? id[x.kid[1]] : -1, x.imm);
+        id[i] = d.intern(x.op, x.kid[0] >= 0 ? id[x.kid[0]] : -1, x.kid[1] >= 0 ? id[x.kid[1]] : -1, x.imm,
+                         x.kid[2] >= 0 ? id[x.kid[2]] : -1);
     }
     for (auto& r : pop.roots) r = id[r];
     pop.dag = std::move(d);
@@ -235,7 +282,8 @@ void append_population(PopIR& dst, const PopIR& src) {
     std::vector<int32_t> id(src.dag.size());
     for (size_t n = 0; n < src.dag.size(); ++n) {   // children precede parents
         const DagNode& s = src.dag.nodes[n];
-        id[n] = dst.dag.intern(s.op, s.kid[0] >= 0 ? id[s.kid[0]] : -1, s.kid[1] >= 0 ? id[s.kid[1]] : -1, s.imm);
+        id[n] = dst.dag.intern(s.op, s.kid[0] >= 0 ? id[s.kid[0]] : -1, s.kid[1] >= 0 ? id[s.kid[1]] : -1, s.imm,
+                               s.kid[2] >= 0 ? id[s.kid[2]] : -1);
     }
     for (size_t t = 0; t < src.roots.size(); ++t) {
         dst.roots.push_back(id[src.roots[t]]);
@@ -292,15 +340,13 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                     fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
                     return -2;
                 }
-                int32_t k0 = -1, k1 = -1, d = 0;
+                int32_t k[kMaxKids] = {-1, -1, -1}, d = 0;
                 uint32_t bits = 0;
                 for (int a = 0; a < ar; ++a) { d = std::max(d, dstack.back() + 1); dstack.pop_back(); }
-                if (ar == 2) { k1 = stack.back(); stack.pop_back(); k0 = stack.back(); stack.pop_back(); }
-                else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
+                for (int a = ar - 1; a >= 0; --a) { k[a] = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[ip++]; std::memcpy(&bits, &v, 4); }
                 dstack.push_back(d);
-                stack.push_back(simplify ? intern_simplified(out.dag, op, k0, k1, bits)
-                                         : out.dag.intern(op, k0, k1, bits));
+                stack.push_back(make_node(out.dag, op, k, bits, simplify));
             }
         } else {            // prefix: scan backwards, first popped = first operand
             int64_t ip = imm_pos + nconst;
@@ -310,15 +356,13 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                     fmt(err, "tree %lld token %lld: operator lacks operands", t, i - b);
                     return -2;
                 }
-                int32_t k0 = -1, k1 = -1, d = 0;
+                int32_t k[kMaxKids] = {-1, -1, -1}, d = 0;
                 uint32_t bits = 0;
                 for (int a = 0; a < ar; ++a) { d = std::max(d, dstack.back() + 1); dstack.pop_back(); }
-                if (ar == 2) { k0 = stack.back(); stack.pop_back(); k1 = stack.back(); stack.pop_back(); }
-                else if (ar == 1) { k0 = stack.back(); stack.pop_back(); }
+                for (int a = 0; a < ar; ++a) { k[a] = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[--ip]; std::memcpy(&bits, &v, 4); }
                 dstack.push_back(d);
-                stack.push_back(simplify ? intern_simplified(out.dag, op, k0, k1, bits)
-                                         : out.dag.intern(op, k0, k1, bits));
+                stack.push_back(make_node(out.dag, op, k, bits, simplify));
             }
         }
         if (stack.size() != 1) {
@@ -437,7 +481,7 @@ private:
                 if (last_pos_[n] < 0) { first_pos_[n] = (int32_t)i; span_touched_.push_back(n); }
                 last_pos_[n] = (int32_t)i;
                 if (is_cached(n)) continue;
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < kMaxKids; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k >= 0 && !is_leaf(N(k).op)) dfs_.push_back(k);
                 }
@@ -453,7 +497,7 @@ private:
                 int32_t n = dfs_.back();
                 dfs_.pop_back();
                 if (is_cached(n)) continue;
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < kMaxKids; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k < 0 || is_leaf(N(k).op) || where_[k] == -2) continue;
                     where_[k] = -2;   // visited mark, reset below
@@ -473,7 +517,7 @@ private:
                        last_pos_[n] - first_pos_[n] <= kKeepSpan;
             if (is_cached(n)) continue;   // loaded, operands not evaluated
             int32_t f = keep_[n] ? 1 : e;
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < kMaxKids; ++c) {
                 int32_t k = N(n).kid[c];
                 if (k >= 0 && !is_leaf(N(k).op)) uses_[k] += f;
             }
@@ -570,7 +614,9 @@ private:
     // and a * b == b * a bitwise; fminf / fmaxf return the same value in
     // either order (a NaN operand yields the other operand; equal zeros
     // compare equal).
-    static bool commutative(int fn) { return fn == T_ADD || fn == T_MUL || fn == T_MIN || fn == T_MAX; }
+    static bool commutative(int fn) {
+        return fn == T_ADD || fn == T_MUL || fn == T_MIN || fn == T_MAX || fn == T_MDIST;
+    }
 
     // A = fn(o, A)
     void emit_rev(int fn, int o, int slot, uint32_t imm) {
@@ -578,11 +624,37 @@ private:
         else emit(F_OA, fn, o, 0, slot, imm);
     }
 
+    // Leaves n's value in a slot: the slot it is held in, or a temporary one
+    // (*temp = true) after computing it.
+    int hold(int32_t n, bool* temp) {
+        *temp = false;
+        if (!is_leaf(N(n).op) && where_[n] >= 0) return where_[n];
+        to_acc(n);
+        if (!is_leaf(N(n).op) && where_[n] >= 0) return where_[n];   // kept by to_acc
+        int j = alloc_slot(false);
+        emit(F_ST, 0, 0, 0, j, 0);
+        *temp = true;
+        return j;
+    }
+
     // Computes internal node n (not held anywhere) into A.
     void compute(int32_t n) {
         const DagNode& x = N(n);
         int fn = x.op;
         uint32_t imm = 0;
+        if (arity(fn) == 3) {   // if(c, a, b): c and a in slots, b in A, then one select
+            bool tc = false, ta = false;
+            int sc = hold(x.kid[0], &tc);
+            int sa = hold(x.kid[1], &ta);
+            to_acc(x.kid[2]);
+            emit(F_SEL, fn, kOpS, kOpS, sc, (uint32_t)sa);
+            if (tc) free_slot(sc);
+            if (ta) free_slot(sa);
+            use(x.kid[0]);
+            use(x.kid[1]);
+            use(x.kid[2]);
+            return;
+        }
         if (arity(fn) == 1) {
             int32_t c = x.kid[0];
             if (is_leaf(N(c).op)) {
@@ -674,6 +746,7 @@ Ins encode(const IrIns& in) {
     case F_ROOT: opc = OPC_ROOT; y = (uint32_t)in.aux; break;
     case F_CST: opc = OPC_CST; y = (uint32_t)in.aux; break;
     case F_CLD: opc = OPC_CLD; y = (uint32_t)in.aux; break;
+    case F_SEL: opc = OPC_SEL; y = (uint32_t)in.aux | (in.imm << 16); break;
     default: opc = OPC_END; break;
     }
     Ins e;
@@ -711,7 +784,7 @@ std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv) {
             seen[n] = 1;
             if (cv.active() && cv.cached[n] >= 0) continue;
             out.push_back(n);
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < kMaxKids; ++c)
                 if (d.kid[c] >= 0) stack.push_back(d.kid[c]);
         }
     }
@@ -740,7 +813,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
             seen[n] = (int32_t)t;
             tree_uses[n]++;
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < kMaxKids; ++c)
                 if (pop.dag.nodes[n].kid[c] >= 0) stack.push_back(pop.dag.nodes[n].kid[c]);
         }
     }
@@ -756,7 +829,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             if (seen[n] == (int32_t)t || is_leaf(d.op)) continue;
             seen[n] = (int32_t)t;
             if (tree_uses[n] >= 2 && d.cost > key_cost[t]) { key_cost[t] = d.cost; key[t] = n; }
-            for (int c = 0; c < 2; ++c)
+            for (int c = 0; c < kMaxKids; ++c)
                 if (d.kid[c] >= 0) stack.push_back(d.kid[c]);
         }
     }

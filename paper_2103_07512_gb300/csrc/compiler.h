@@ -14,7 +14,7 @@ namespace tgp {
 // to the same id (Handley's DAG, Sec. 2 of TensorGP).
 struct DagNode {
     int32_t op;
-    int32_t kid[2];     // -1 when absent
+    int32_t kid[kMaxKids];   // operands in order, -1 when absent
     uint32_t imm;       // binary32 bits of a CONST
     int32_t su;         // register slots needed to evaluate it (Sethi-Ullman)
     int32_t depth;      // root alone = 0
@@ -24,7 +24,7 @@ struct DagNode {
 class Dag {
 public:
     std::vector<DagNode> nodes;
-    int32_t intern(int op, int32_t k0, int32_t k1, uint32_t imm);
+    int32_t intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2 = -1);
     size_t size() const { return nodes.size(); }
 
 private:
@@ -55,7 +55,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
 // Hash-conses one node after exact algebraic simplification (constant
 // folding, identities, canonical operand order; see compiler.cpp).  The
 // operands must already be nodes of `dag`.
-int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm);
+int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2 = -1);
 
 // Appends the trees of `src` to `dst`, hash-consing src's nodes into dst's
 // DAG (subtrees common to both are shared).

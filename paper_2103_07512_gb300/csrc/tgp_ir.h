@@ -26,8 +26,11 @@ namespace tgp {
 // Token opcodes (same numbering as the public header).
 enum TokOp : int {
     T_X = 0, T_Y = 1, T_CONST = 2, T_ADD = 3, T_SUB = 4, T_MUL = 5, T_DIV = 6,
-    T_SIN = 7, T_COS = 8, T_NEG = 9, T_ABS = 10, T_MIN = 11, T_MAX = 12, T_NOPS = 13
+    T_SIN = 7, T_COS = 8, T_NEG = 9, T_ABS = 10, T_MIN = 11, T_MAX = 12,
+    T_TAN = 13, T_EXP = 14, T_LOG = 15, T_POW = 16, T_MDIST = 17, T_SQRT = 18,
+    T_SIGN = 19, T_CLIP = 20, T_MOD = 21, T_FRAC = 22, T_IF = 23, T_NOPS = 24
 };
+constexpr int kMaxKids = 3;   // clip and if take three operands
 
 // Operand kinds.
 constexpr int kOpX = 0, kOpY = 1, kOpC = 2, kOpS = 3;
@@ -47,20 +50,24 @@ enum Form : int {
     F_ROOT,   // tree aux is complete in A: fitness partial or phenotype store
     F_CST,    // cache entry aux = A (HBM)
     F_CLD,    // A = cache entry aux (HBM)
+    F_SEL,    // A = slot aux != 0 ? slot imm : A    (if; both operands in slots)
     F_NFORMS
 };
 
-// binary function index 0..5, reversed-operand index 0..1, unary 0..3
-constexpr int kNBin = 6, kNOrd = 2, kNUn = 4;
+// binary function index 0..8, reversed-operand index 0..3, unary 0..9
+constexpr int kNBin = 9, kNOrd = 4, kNUn = 10;
 __host__ __device__ constexpr int bin_index(int tok) {
     return tok == T_ADD ? 0 : tok == T_SUB ? 1 : tok == T_MUL ? 2 : tok == T_DIV ? 3
-         : tok == T_MIN ? 4 : tok == T_MAX ? 5 : -1;
+         : tok == T_MIN ? 4 : tok == T_MAX ? 5 : tok == T_POW ? 6 : tok == T_MDIST ? 7
+         : tok == T_MOD ? 8 : -1;
 }
-__host__ __device__ constexpr int ord_index(int tok) {   // F_OA functions
-    return tok == T_SUB ? 0 : tok == T_DIV ? 1 : -1;
+__host__ __device__ constexpr int ord_index(int tok) {   // F_OA functions (not commutative)
+    return tok == T_SUB ? 0 : tok == T_DIV ? 1 : tok == T_POW ? 2 : tok == T_MOD ? 3 : -1;
 }
 __host__ __device__ constexpr int un_index(int tok) {
-    return tok == T_SIN ? 0 : tok == T_COS ? 1 : tok == T_NEG ? 2 : tok == T_ABS ? 3 : -1;
+    return tok == T_SIN ? 0 : tok == T_COS ? 1 : tok == T_NEG ? 2 : tok == T_ABS ? 3
+         : tok == T_TAN ? 4 : tok == T_EXP ? 5 : tok == T_LOG ? 6 : tok == T_SQRT ? 7
+         : tok == T_SIGN ? 8 : tok == T_FRAC ? 9 : -1;
 }
 
 // Encoded opcode layout (dense, so the device switch becomes a jump table).
@@ -75,7 +82,8 @@ constexpr int OPC_ST = OPC_LD + kNOpnd;
 constexpr int OPC_ROOT = OPC_ST + 1;
 constexpr int OPC_CST = OPC_ROOT + 1;
 constexpr int OPC_CLD = OPC_CST + 1;
-constexpr int OPC_COUNT = OPC_CLD + 1;
+constexpr int OPC_SEL = OPC_CLD + 1;
+constexpr int OPC_COUNT = OPC_SEL + 1;
 
 // One encoded instruction: x = opcode, y = immediate bits, slot, or aux.
 struct Ins {

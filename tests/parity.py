@@ -3,14 +3,16 @@
 Element rule.  An element passes when |gpu - v64| <= 1e-4 * (1 + |v64|) (the
 stated tolerance), or when |gpu - v64| <= E, where E is the oracle's forward
 error bound for ANY binary32 evaluation of that tree at that point (correctly
-rounded + - * /, sin/cos(pi a) within 2 ulp; see oracle/tgp_oracle.c).  The
-second clause covers ill-conditioned elements (e.g. a division by a difference
-of nearly equal values) that no binary32 program can get within the fixed
-tolerance.  Excluded from the element check, and counted: elements where a
-division saw |denominator| < 1e-6 (the stated exclusion) and elements whose
-bound is unbounded (undecided zero test of a denominator, or binary32
-overflow).  Where v64 itself is not finite, the GPU value must not be finite
-either.
+rounded + - * / sqrt, sin/cos(pi a), exp, log within 2 ulp, tan within 4, pow
+within 8; see oracle/tgp_oracle.c).  The second clause covers ill-conditioned
+elements (e.g. a division by a difference of nearly equal values) that no
+binary32 program can get within the fixed tolerance.  Excluded from the element
+check, and counted: elements where a division saw |denominator| < 1e-6 (the
+stated exclusion), elements whose bound is unbounded (undecided zero test of a
+denominator or an if condition, a jump of sign/frac/mod within the bound, a
+pole, binary32 overflow), and, when the FP32-faithful values are passed,
+elements not finite in binary64 but finite in the FP32-faithful walk.
+Otherwise, where v64 is not finite, the GPU value must not be finite either.
 
 Fitness rule.  |gpu - r64| <= 1e-5 |r64| + R + 1e-6, where R = sqrt(mean E^2)
 bounds the RMSE change caused by the element errors (triangle inequality in
@@ -39,17 +41,26 @@ def close(a, b, tol=ELEM_TOL):
     return same | near
 
 
-def classify(gpu, v64, flags, bound):
-    """Masks and counts for arrays shaped [T, n]."""
+def classify(gpu, v64, flags, bound, v32=None):
+    """Masks and counts for arrays shaped [T, n].  With v32 (the oracle's
+    FP32-faithful values), an element that is not finite in binary64 but
+    finite in the FP32-faithful walk (a binary32 evaluation took another
+    branch of an undecided test: an if condition, a sign, a pole) is excluded
+    instead of requiring a non-finite device value."""
     g = np.asarray(gpu, np.float64)
     v64 = np.asarray(v64, np.float64)
     fin64 = np.isfinite(v64)
     unbounded = fin64 & ~np.isfinite(bound)
     excluded = np.asarray(flags, bool) | unbounded
+    must_be_nonfinite = ~fin64
+    if v32 is not None:
+        diverged = ~fin64 & np.isfinite(np.asarray(v32, np.float64))
+        excluded = excluded | diverged
+        must_be_nonfinite = must_be_nonfinite & ~diverged
     with np.errstate(all="ignore"):
         by_tol = close(g, v64)
         by_bound = np.abs(g - v64) <= bound
-    fail = (fin64 & ~excluded & ~(by_tol | by_bound)) | (~fin64 & np.isfinite(g))
+    fail = (fin64 & ~excluded & ~(by_tol | by_bound)) | (must_be_nonfinite & np.isfinite(g))
     ill = fin64 & ~excluded & ~by_tol & by_bound
     return {
         "excluded": excluded, "ill": ill, "fail": fail,
@@ -58,8 +69,8 @@ def classify(gpu, v64, flags, bound):
     }
 
 
-def assert_elements(gpu, v64, flags, bound, context=""):
-    c = classify(gpu, v64, flags, bound)
+def assert_elements(gpu, v64, flags, bound, context="", v32=None):
+    c = classify(gpu, v64, flags, bound, v32)
     if c["n_fail"]:
         idx = np.argwhere(c["fail"])[:5]
         sel = tuple(idx.T)

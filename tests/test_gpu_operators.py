@@ -1,0 +1,122 @@
+"""The rest of Table 1 on the device (tan, exp, log, pow, mdist, sqrt, sign,
+clip, mod, frac, if): every element and fitness against the oracle, the
+exactly rounded operators bitwise against the FP32-faithful oracle, special
+values, and simplification still exact with every operator."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_07512_gb300 as tgp
+from paper_2103_07512_gb300 import inputs as I
+from parity import assert_elements, assert_fitness
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+EXACT = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.ABS, I.MIN, I.MAX, I.MDIST, I.SQRT, I.SIGN, I.CLIP, I.FRAC, I.IF)
+
+
+def device(ctx, tok, g):
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    pop = ctx.compile_tokens(tok)
+    out = torch.empty((tok.n_trees, g.N), dtype=torch.float32, device="cuda")
+    ctx.evaluate(pop, dom, out)
+    fit = ctx.fitness(pop, dom, tok.n_trees)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), fit
+
+
+@pytest.mark.parametrize("K", [0, 1, 4, 8])
+def test_all_operators_against_oracle(K):
+    rng = np.random.default_rng(51)
+    trees = [I._full(rng, int(rng.integers(2, 6)), I.ALL_FUNCTIONS) for _ in range(200)]
+    trees += I.ramped_half_and_half(100, 2, 6, rng, I.ALL_FUNCTIONS)
+    tok = I.to_tokens(trees)
+    g = I.Grid(33, 17)
+    with tgp.Context(points_per_thread=K) as ctx:
+        ph, fit = device(ctx, tok, g)
+    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
+    c = assert_elements(ph, v64, fl, eb, context=f"all operators K={K}", v32=v32)
+    assert c["n"] - c["n_excluded"] > 0.6 * c["n"]
+    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
+    assert_fitness(fit, r64, re, g.N, "all operators")
+
+
+def test_exactly_rounded_operators_equal_fp32_faithful():
+    rng = np.random.default_rng(52)
+    trees = [I._full(rng, int(rng.integers(2, 7)), EXACT) for _ in range(200)]
+    tok = I.to_tokens(trees)
+    g = I.Grid(40, 30)
+    with tgp.Context() as ctx:
+        ph, _ = device(ctx, tok, g)
+    _, v32, _ = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    # equal as binary32 values: NaN = NaN, zeros of either sign equal (min/max/if of zeros)
+    assert np.array_equal(ph, v32, equal_nan=True)
+
+
+@pytest.mark.parametrize("expr,expect", [
+    ("tan(0.25)", 1.0), ("tan(0.0)", 0.0), ("exp(0.0)", 1.0), ("log(1.0)", 0.0), ("log(-3.0)", -1.0),
+    ("pow(0.0, 0.0)", 0.0), ("pow(2.0, 10.0)", 1024.0), ("pow(-2.0, 3.0)", -8.0), ("mdist(1.0, 2.0)", 1.5),
+    ("sqrt(-4.0)", 0.0), ("sqrt(9.0)", 3.0), ("sign(-2.5)", -1.0), ("sign(0.0)", 0.0), ("sign(7.0)", 1.0),
+    ("clip(5.0, 0.0, 1.0)", 1.0), ("mod(-5.0, 3.0)", 1.0), ("mod(5.0, -3.0)", -1.0), ("frac(-2.25)", 0.75),
+    ("if(0.0, 1.0, 2.0)", 2.0), ("if(-0.0, 1.0, 2.0)", 2.0), ("if(3.0, 1.0, 2.0)", 1.0),
+])
+def test_special_values_on_device(expr, expect):
+    # a copy whose constants c become add(x, c), so nothing is folded on the
+    # host (x = 0 on this grid), beside the expression as written
+    def unfold(t):
+        op, v, kids = t
+        if op == I.CONST:
+            return I.node(I.ADD, I.leaf(I.X), t)
+        return (op, v, tuple(unfold(k) for k in kids))
+    t = I.parse_string(expr)
+    tok = I.to_tokens([unfold(t), t])
+    e = I.to_string(unfold(t))
+    g = I.Grid(1, 1, 0.0, 0.0, 0.0, 0.0)
+    with tgp.Context() as ctx:
+        ph, _ = device(ctx, tok, g)
+    assert ph[0, 0] == np.float32(expect), (e, ph[0, 0])
+    assert ph[1, 0] == np.float32(expect), (expr, ph[1, 0])
+
+
+def test_nonfinite_results_on_device():
+    tok = I.to_tokens([I.parse_string(e) for e in
+                       ["tan(add(x, 0.5))", "log(mult(x, 0.0))", "pow(add(x, -8.0), 0.5)", "mod(1.0, mult(x, 0.0))",
+                        "exp(add(x, 100.0))", "sign(mod(1.0, mult(x, 0.0)))"]])
+    g = I.Grid(1, 1, 0.0, 0.0, 0.0, 0.0)
+    with tgp.Context() as ctx:
+        ph, fit = device(ctx, tok, g)
+    v = ph[:, 0]
+    assert np.isinf(v[0]) and v[1] == -np.inf and np.isnan(v[2]) and np.isnan(v[3])
+    assert v[4] == np.inf and np.isnan(v[5])
+    assert np.all(np.isinf(fit))
+
+
+def test_simplified_equals_as_given_with_every_operator():
+    rng = np.random.default_rng(53)
+
+    def tree(d):
+        if d == 0 or rng.random() < 0.2:
+            r = rng.random()
+            if r < 0.3:
+                return I.leaf(I.X if r < 0.2 else I.Y)
+            return I.leaf(I.CONST, (0.0, -0.0, 1.0, -1.0, 2.0, 0.5, 3.0)[int(rng.integers(7))])
+        f = I.ALL_FUNCTIONS[int(rng.integers(len(I.ALL_FUNCTIONS)))]
+        return I.node(f, *[tree(d - 1) for _ in range(I.ARITY[f])])
+
+    tok = I.to_tokens([tree(int(rng.integers(2, 7))) for _ in range(300)])
+    g = I.Grid(48, 40)
+    with tgp.Context() as a, tgp.Context(simplify=False) as b:
+        pa, fa = device(a, tok, g)
+        pb, fb = device(b, tok, g)
+        assert a.stats()["dag_internal"] < b.stats()["dag_internal"]
+
+    def bits(x):
+        y = x.view(np.int32).copy()
+        y[np.isnan(x)] = 0x7FC00000
+        return y
+    assert np.array_equal(bits(pa), bits(pb))
+    assert np.array_equal(fa.view(np.int64), fb.view(np.int64))

@@ -11,11 +11,12 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
+from parity import classify as parity_classify
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # decoded forms (order of the Form enum of the bytecode) and operand kinds
-(F_END, F_AO, F_OA, F_TT, F_UA, F_UT, F_LD, F_ST, F_ROOT, F_CST, F_CLD) = range(11)
+(F_END, F_AO, F_OA, F_TT, F_UA, F_UT, F_LD, F_ST, F_ROOT, F_CST, F_CLD, F_SEL) = range(12)
 O_X, O_Y, O_C, O_S = range(4)
 
 
@@ -38,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_layout():
     lay = tgp.debug_layout()
-    assert lay["n_opnd"] == 4 and lay["n_forms"] == 11
+    assert lay["n_opnd"] == 4 and lay["n_forms"] == 12
 
 
 def test_host_only_context_refuses_device_work(ctx):
@@ -124,14 +125,28 @@ def test_prefix_and_postfix_give_same_dag(ctx):
 
 # ---------------------------------------------------------------- bytecode
 
+def _trigpi(a, shift):
+    """sin(pi a) (shift 0) or cos(pi a) (shift 1) in binary64 with the
+    argument reduced exactly to [-1/4, 1/4] around a multiple of 1/2, so zeros
+    and +-1 at multiples of 1/2 are exact; rounded to binary32."""
+    with np.errstate(invalid="ignore"):
+        a64 = a.astype(np.float64)
+        r = np.remainder(a64, 2.0)
+        n = np.rint(2.0 * r)
+        f = r - 0.5 * n
+        q = (np.nan_to_num(n).astype(np.int64) + shift) % 4
+        s, c = np.sin(np.pi * f), np.cos(np.pi * f)
+        v = np.select([q == 0, q == 1, q == 2], [s, c, -s], -c)
+        v = np.where(np.isfinite(a64), v, np.nan)
+    return (v + 0.0).astype(np.float32)
+
+
 def _sinpi32(a):
-    a64 = a.astype(np.float64)
-    return np.sin(np.pi * np.remainder(a64, 2.0)).astype(np.float32)
+    return _trigpi(a, 0)
 
 
 def _cospi32(a):
-    a64 = a.astype(np.float64)
-    return np.cos(np.pi * np.remainder(a64, 2.0)).astype(np.float32)
+    return _trigpi(a, 1)
 
 
 def _bin(fn, a, b):
@@ -148,6 +163,14 @@ def _bin(fn, a, b):
             return np.fmin(a, b)
         if fn == I.MAX:
             return np.fmax(a, b)
+        if fn == I.MDIST:
+            return (a + b) * np.float32(0.5)
+        if fn == I.MOD:
+            r = np.fmod(a, b)
+            return np.where((r != 0) & ((r < 0) != (b < 0)), r + b, r).astype(np.float32)
+        if fn == I.POW:
+            r = np.power(a.astype(np.float64), b.astype(np.float64)).astype(np.float32)
+            return np.where((a == 0) & (b == 0), np.float32(0), r)
     raise AssertionError(fn)
 
 
@@ -160,6 +183,20 @@ def _un(fn, a):
         return -a
     if fn == I.ABS:
         return np.abs(a)
+    with np.errstate(all="ignore"):
+        if fn == I.SQRT:
+            return np.where(a < 0, np.float32(0), np.sqrt(a))
+        if fn == I.SIGN:
+            return np.where(a > 0, np.float32(1), np.where(a < 0, np.float32(-1),
+                                                            np.where(a == 0, np.float32(0), a)))
+        if fn == I.FRAC:
+            return a - np.floor(a)
+        if fn == I.TAN:
+            return (_sinpi32(a).astype(np.float64) / _cospi32(a).astype(np.float64)).astype(np.float32)
+        if fn == I.EXP:
+            return np.exp(a.astype(np.float64)).astype(np.float32)
+        if fn == I.LOG:
+            return np.where(a < 0, np.float32(-1), np.log(a.astype(np.float64)).astype(np.float32))
     raise AssertionError(fn)
 
 
@@ -190,7 +227,7 @@ def run_bytecode(ins, off, n_trees, X, Y):
             if form == F_AO:
                 A = _bin(fn, A, opnd(o1))
             elif form == F_OA:
-                assert fn in (I.SUB, I.DIV)
+                assert fn in (I.SUB, I.DIV, I.POW, I.MOD)
                 A = _bin(fn, opnd(o1), A)
             elif form == F_TT:
                 assert o1 <= 2 and o2 <= 2 and not (o1 == 2 and o2 == 2)
@@ -204,6 +241,10 @@ def run_bytecode(ins, off, n_trees, X, Y):
                 A = opnd(o1).copy()
             elif form == F_ST:
                 S[aux] = A.copy()
+            elif form == F_SEL:
+                assert aux in S and immb in S, "select reads a slot before it was written"
+                c = S[aux]
+                A = np.where((c != 0) | np.isnan(c), S[immb], A).astype(np.float32)
             elif form == F_ROOT:
                 assert not seen[aux], "tree emitted twice"
                 seen[aux] = True
@@ -379,3 +420,60 @@ def test_simplified_bytecode_equals_oracle_on_raw_trees(ctx):
     # equal as binary32 values (NaN = NaN; a zero of either sign = 0: fmin/fmax of
     # two zeros may return either, and operand order differs between the plans)
     assert np.array_equal(got, v32, equal_nan=True)
+
+
+# ---------------------------------------------------------------- the rest of Table 1
+
+EXACT_FUNCS = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.ABS, I.MIN, I.MAX, I.MDIST, I.SQRT, I.SIGN,
+               I.CLIP, I.FRAC, I.IF)
+
+
+def test_bytecode_new_exact_operators_equal_oracle(ctx):
+    """mdist, sqrt, sign, clip, frac and if are exactly rounded steps: the
+    plan, run by the numpy interpreter, gives the oracle's binary32 values."""
+    rng = np.random.default_rng(41)
+    trees = [I._full(rng, int(rng.integers(2, 6)), EXACT_FUNCS) for _ in range(120)]
+    tok = I.to_tokens(trees)
+    W, H = 6, 5
+    pop = ctx.compile_tokens(tok)
+    ins, off = ctx.debug_plan(pop, W * H)
+    assert (ins[:, 0] == F_SEL).any()
+    xs = np.array([oracle.grid_point(W, H, -5, 5, -5, 5, p) for p in range(W * H)], np.float32)
+    got = run_bytecode(ins, off, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
+    v64, v32, fl = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5)
+    assert np.array_equal(got, v32, equal_nan=True)
+
+
+def test_bytecode_all_operators_close_to_oracle(ctx):
+    rng = np.random.default_rng(42)
+    trees = [I._full(rng, int(rng.integers(2, 5)), I.ALL_FUNCTIONS) for _ in range(150)]
+    tok = I.to_tokens(trees)
+    for order in (I.PREFIX, I.POSTFIX):
+        t = I.convert_order(tok, order)
+        W, H = 5, 4
+        pop = ctx.compile_tokens(t)
+        ins, off = ctx.debug_plan(pop, W * H)
+        xs = np.array([oracle.grid_point(W, H, -5, 5, -5, 5, p) for p in range(W * H)], np.float32)
+        got = run_bytecode(ins, off, t.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
+        v64, v32, fl, eb = oracle.evaluate(t.ops, t.imm, t.tree_off, order, W, H, -5, 5, -5, 5,
+                                           with_bound=True)
+        c = parity_classify(got, v64, fl, eb, v32)
+        assert c["n_fail"] == 0, c["n_fail"]
+        assert c["n"] - c["n_excluded"] > 0.7 * c["n"]
+
+
+def test_clip_is_lowered_to_min_max(ctx):
+    a = I.to_tokens([I.parse_string("clip(x, -1.0, 1.0)")])
+    b = I.to_tokens([I.parse_string("max(min(1.0, x), -1.0)")])
+    pa, pb = ctx.compile_tokens(a), ctx.compile_tokens(b)
+    ia, _ = ctx.debug_plan(pa, 16)
+    ib, _ = ctx.debug_plan(pb, 16)
+    assert np.array_equal(ia, ib)
+
+
+def test_three_operand_tokens_validate(ctx):
+    bad = I.Tokens(np.array([I.IF, I.X, I.Y], np.int32), np.zeros(0, np.float32),
+                   np.array([0, 3], np.int64), I.PREFIX)
+    with pytest.raises(tgp.TgpError) as e:
+        ctx.compile_tokens(bad)
+    assert e.value.code == tgp.E_TOKENS

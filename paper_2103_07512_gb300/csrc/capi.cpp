@@ -182,7 +182,7 @@ struct tgp_ctx {
     std::map<int64_t, std::unique_ptr<Population>> pops;
     tgp_stats stats{};
     int sms = 0;
-    std::map<std::tuple<int, int, int, size_t>, int> occ;   // (K, pheno, threads, smem) -> blocks/SM
+    std::map<std::tuple<int, int, int, size_t>, int> occ;   // (K, pheno*2+ext, threads, smem) -> blocks/SM
     std::map<TuneKey, TuneChoice> tuned;                     // tgp_autotune results
     Dag gdag;                                                // context-wide DAG (cache on)
     int64_t epoch = 0;                                       // calls that used the cache
@@ -273,12 +273,12 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
     return s;
 }
 
-int occupancy(tgp_ctx* c, int K, bool pheno, int threads, size_t smem, int* out) {
-    auto key = std::make_tuple(K, (int)pheno, threads, smem);
+int occupancy(tgp_ctx* c, int K, bool pheno, bool ext, int threads, size_t smem, int* out) {
+    auto key = std::make_tuple(K, (int)pheno * 2 + (int)ext, threads, smem);
     auto it = c->occ.find(key);
     if (it != c->occ.end()) { *out = it->second; return TGP_OK; }
     int b = 0;
-    CUDA_TRY(eval_occupancy(K, pheno, threads, smem, &b));
+    CUDA_TRY(eval_occupancy(K, pheno, ext, threads, smem, &b));
     if (b <= 0) return fail(TGP_E_INVALID, "kernel cannot be resident with %d threads and %zu bytes of shared memory", threads, smem);
     c->occ[key] = b;
     *out = b;
@@ -364,7 +364,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         }
     }
     int bps = 0;
-    int rc = occupancy(c, shape.K, pheno, shape.threads, pl->smem, &bps);
+    int rc = occupancy(c, shape.K, pheno, pl->hp.ext, shape.threads, pl->smem, &bps);
     if (rc) return rc;
     int64_t slots = (int64_t)bps * std::max(c->sms, 1);
     pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl->hp.n_items, slots));
@@ -651,7 +651,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         }
         CUDA_TRY(cudaEventRecord(ev.first, s));
     }
-    CUDA_TRY(launch_eval(p, hp.shape.K, pheno, pl->grid, hp.shape.threads, pl->smem, s));
+    CUDA_TRY(launch_eval(p, hp.shape.K, pheno, hp.ext, pl->grid, hp.shape.threads, pl->smem, s));
     if (timed) {
         CUDA_TRY(cudaEventRecord(ev.second, s));
         c->ev_pending.push_back(ev);

@@ -887,7 +887,12 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
                      [&](int32_t a, int32_t b) { return plan.group_cost[a] > plan.group_cost[b]; });
     plan.n_items = (int64_t)G * plan.n_tiles;
     plan.code.reserve(plan.ir.size() + 1);
-    for (const IrIns& in : plan.ir) plan.code.push_back(encode(in));
+    for (const IrIns& in : plan.ir) {
+        plan.code.push_back(encode(in));
+        // the interpreter variant with the rest of Table 1 is needed
+        const bool form_fn = in.form == F_AO || in.form == F_OA || in.form == F_TT || in.form == F_UA || in.form == F_UT;
+        if (in.form == F_SEL || (form_fn && in.fn >= T_TAN)) plan.ext = true;
+    }
     plan.code.push_back(encode(IrIns{F_END, 0, 0, 0, 0, 0}));
 }
 

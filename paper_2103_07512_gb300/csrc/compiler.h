@@ -85,6 +85,7 @@ struct HostPlan {
     std::vector<int32_t> group_order;   // groups by descending estimated cost
     std::vector<double> group_cost;
     int n_slots = 0;                    // shared-memory value slots per thread
+    bool ext = false;                   // uses operators beyond the benchmark function set
     int n_tiles = 0;
     int64_t n_items = 0;
 };

@@ -6,11 +6,13 @@
 
 namespace tgp {
 
-// Fused interpreter: K in {1, 2, 4, 8}; pheno selects phenotype stores
-// instead of fitness partials at tree roots.  threads <= 128.
-cudaError_t launch_eval(const EvalParams& p, int K, bool pheno, int grid, int threads, size_t smem,
+// Fused interpreter: K in {1, 2, 4, 8, 16}; pheno selects phenotype stores
+// instead of fitness partials at tree roots; ext selects the variant that also
+// runs the rest of Table 1 (a plan without those operators uses the smaller
+// kernel).  threads <= 128.
+cudaError_t launch_eval(const EvalParams& p, int K, bool pheno, bool ext, int grid, int threads, size_t smem,
                         cudaStream_t s);
-cudaError_t eval_occupancy(int K, bool pheno, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t eval_occupancy(int K, bool pheno, bool ext, int threads, size_t smem, int* blocks_per_sm);
 
 // Dynamic shared memory of one interpreter CTA: target values and value
 // slots, K points per thread.

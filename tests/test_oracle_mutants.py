@@ -53,20 +53,39 @@ MUTANTS = {
 }
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
+def _run_mutant(name, workdir):
+    """Builds one mutant and runs the pins against it; returns (rc, output)."""
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site for {name} not found"
-    mutated = src.replace(old, new)
-    c = tmp_path / "mut.c"
-    so = tmp_path / "libmut.so"
-    c.write_text(mutated)
+    if src.count(old) < 1:
+        return None, f"mutation site for {name} not found"
+    c = os.path.join(workdir, f"{name}.c")
+    so = os.path.join(workdir, f"lib{name}.so")
+    with open(c, "w") as f:
+        f.write(src.replace(old, new))
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-                           "-o", str(so), str(c), "-lm"])
-    env = dict(os.environ, TGP_ORACLE_LIB_OVERRIDE=str(so))
+                           "-o", so, c, "-lm"])
+    env = dict(os.environ, TGP_ORACLE_LIB_OVERRIDE=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"mutant {name} survived the oracle pins:\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """Every mutant's pin run, several at a time (each is its own process)."""
+    from concurrent.futures import ThreadPoolExecutor
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        futs = {n: ex.submit(_run_mutant, n, workdir) for n in sorted(MUTANTS)}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, mutant_results):
+    rc, out = mutant_results[name]
+    assert rc is not None, out
+    assert rc != 0, f"mutant {name} survived the oracle pins:\n{out}"

@@ -120,3 +120,24 @@ def test_simplified_equals_as_given_with_every_operator():
         return y
     assert np.array_equal(bits(pa), bits(pb))
     assert np.array_equal(fa.view(np.int64), fb.view(np.int64))
+
+
+@pytest.mark.parametrize("lo,hi", [(-2.0, 2.0), (-1e-3, 1e-3), (999.0, 1003.0), (4194304.0, 4194368.0),
+                                   (-3e7, 3e7), (0.49, 0.51), (-1e30, 1e30)])
+def test_sin_cos_pi_within_one_ulp(lo, hi):
+    """The device's sin(pi a) / cos(pi a) against the exactly reduced binary64
+    values: within 1 ulp everywhere (the oracle's bound allows 2), 0 at the
+    zeros."""
+    W = 1 << 14
+    g = I.Grid(W, 1, lo, hi, 0.0, 0.0)
+    tok = I.to_tokens([I.parse_string("sin(x)"), I.parse_string("cos(x)")])
+    with tgp.Context(simplify=False) as ctx:
+        ph, _ = device(ctx, tok, g)
+    xs = np.array([oracle.grid_point(W, 1, lo, hi, 0.0, 0.0, p)[0] for p in range(W)], np.float32)
+    for row, f in ((0, oracle.sinpi), (1, oracle.cospi)):
+        exact = np.array([f(float(v)) for v in xs])
+        ulp = np.spacing(np.abs(exact).astype(np.float32)).astype(np.float64)
+        err = np.abs(ph[row].astype(np.float64) - exact) / ulp
+        assert err.max() <= 1.0, (row, float(err.max()), xs[int(err.argmax())])
+        zero = exact == 0
+        assert np.all(ph[row][zero] == 0)

@@ -400,6 +400,7 @@ public:
           cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0) {}
 
     int slot_high = 0;                    // slots used by the last run
+    void set_kept_cap(int c) { kept_cap_ = c; }
     std::vector<int32_t> refused;         // kept nodes that found no slot under the cap (last run)
 
     // Forgets the cache stores of the last attempt (the group is re-planned).
@@ -861,11 +862,16 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     // CTAs at this K.  Temporaries may exceed it (a tree needs as many as its
     // Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
-    const int cap = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
-    GroupGen gen(pop.dag, plan.ir, shape.dedup, cap, cv);
+    const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
+    GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv);
     plan.group_off.push_back(0);
     std::vector<int32_t> forbid;
     for (int g = 0; g < G; ++g) {
+        // kept nodes get what the group's temporaries leave of the budget (a
+        // tree's evaluation parks up to its Sethi-Ullman number of values)
+        int su = 0;
+        for (int32_t t : groups[g]) su = std::max(su, pop.dag.nodes[pop.roots[t]].su);
+        gen.set_kept_cap(std::max(2, budget - su));
         // A kept node that found no slot under the cap is demoted to
         // re-evaluation and the group is planned again.  Demotion only
         // shrinks the kept set, so this terminates.

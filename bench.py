@@ -51,6 +51,19 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def replica_throughput(local_seconds, units_per_rank, world, dist=None, device=None):
+    """Whole-job time and throughput of `world` independent replicas (one per
+    GPU, no collective on the data path): the slowest rank's time is the job's,
+    and the job processed world * units_per_rank units in it."""
+    t = float(local_seconds)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, world * units_per_rank / t
+
+
 def workload():
     tok, g = I.population_at_scale(seed=1)
     return tok, g
@@ -239,14 +252,11 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     s1 = ctx.stats()
-    step_ms = float(np.sum([a.elapsed_time(b) for a, b in evs])) / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_s, value = replica_throughput(float(np.sum([a.elapsed_time(b) for a, b in evs])) / args.steps * 1e-3,
+                                       units, world, dist, dev)
+    step_ms = step_s * 1e3
     kern_ms = (s1["eval_ms_sum"] - s0["eval_ms_sum"]) / max(1, s1["eval_timed"] - s0["eval_timed"])
     launches = int(s1["launches"] - s0["launches"])
-    value = world * units / (step_ms * 1e-3)
 
     # -------- end to end through the public API from host tokens
     e2e_steps = max(3, min(args.steps, 20))
@@ -265,8 +275,7 @@ def run_ours(args):
             e2e_times.append(t1 - t0)
         h2d = (s["code_instrs"] + 1) * 8 + (s["n_groups"] + 1) * 8 + s["n_groups"] * 4
         d2h = 8 * T
-    e2e_s = float(np.mean(e2e_times))
-    e2e_value = world * units / e2e_s
+    e2e_s, e2e_value = replica_throughput(float(np.mean(e2e_times)), units, world, dist, dev)
 
     # -------- per-operator materialising baseline on the same GPU
     per = PerOpEvaluator(g, device=dev)

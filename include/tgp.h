@@ -334,6 +334,69 @@ int tgp_debug_layout(int32_t* out, int32_t n);
 int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
 
 /* ------------------------------------------------------------------------
+ * Generational step on the host (TensorGP, Sec. 3 and Table 2).
+ *
+ * tgp_evolve builds the next generation of `pop` from its trees' RMSE values
+ * and registers it as a new population (`pop` stays valid; release it when
+ * done).  Variation works on the population DAG itself: crossover and
+ * mutation rebuild only the nodes on the path from the replaced subtree to
+ * the root, and every unchanged subtree keeps its structural identity, so the
+ * next generation needs no token re-parse and subtrees already in the
+ * context's cache stay cached.
+ *
+ *   selection: tournament of `tournament` trees drawn with replacement; the
+ *     lowest RMSE wins (NaN and +inf rank last; ties go to the lower index);
+ *   elitism: the `elitism` best trees (stable order of RMSE) are copied first;
+ *   then, per offspring, with probability p_crossover a subtree crossover (a
+ *     uniformly chosen node occurrence of the first parent, in preorder, is
+ *     replaced by a uniformly chosen subtree of a second tournament winner),
+ *     else with probability p_mutation a subtree mutation (the chosen node is
+ *     replaced by a grow tree of depth 0..mutation_depth over `functions`,
+ *     terminals x, y and constants uniform in [const_lo, const_hi)), else a
+ *     copy; an offspring deeper than max_depth (measured on the stored tree,
+ *     clip being stored as max(min(z, x), y)) is replaced by its first parent.
+ *
+ * Zero fields take the defaults: tournament 3, p_crossover 0.9, p_mutation
+ * 0.1, elitism 1, max_depth 12, mutation_depth 4 (a negative probability or
+ * elitism means none),
+ * functions {add, sub, mult, div, sin, cos, neg, abs, min, max}, constants in
+ * [-1, 1).  The random stream is splitmix64 from `seed`: the same population,
+ * RMSE values and configuration give the same next generation.  With the
+ * context's simplification on, rebuilt nodes are simplified exactly as
+ * tgp_compile_population would.  Works on host-only contexts.
+ *
+ * rmse: host array with one value per tree of `pop`.
+ */
+typedef struct tgp_evolve_config {
+    int32_t tournament;
+    float p_crossover;
+    float p_mutation;
+    int32_t elitism;
+    int32_t max_depth;
+    int32_t mutation_depth;
+    const int32_t* functions;   /* opcodes of arity >= 1, NULL for the default set */
+    int32_t n_functions;
+    float const_lo, const_hi;
+    uint64_t seed;
+    int64_t reserved[4];
+} tgp_evolve_config;
+
+int tgp_evolve(tgp_ctx* ctx, tgp_handle pop, const double* rmse, const tgp_evolve_config* cfg,
+               tgp_handle* next_pop);
+
+/*
+ * Writes the trees of a population as prefix-order tokens (the format of
+ * tgp_compile_population with order TGP_PREFIX): ops[cap_ops], imm[cap_imm]
+ * (one binary32 per CONST, in token order) and tree_off[cap_off] (n_trees + 1
+ * offsets).  Trees are written as stored, i.e. after the context's
+ * simplification and with clip(x, y, z) as its definition max(min(z, x), y).  *n_ops, *n_imm and *n_trees (each may be NULL) receive
+ * the sizes; pass NULL arrays to query them.  TGP_E_INVALID when an array is
+ * too small (nothing beyond its capacity is written).
+ */
+int tgp_population_tokens(tgp_ctx* ctx, tgp_handle pop, int32_t* ops, int64_t cap_ops, float* imm, int64_t cap_imm,
+                          int64_t* tree_off, int64_t cap_off, int64_t* n_ops, int64_t* n_imm, int32_t* n_trees);
+
+/* ------------------------------------------------------------------------
  * Serving: evaluation jobs that arrive over time.
  *
  * A server owns a worker thread on a context.  tgp_server_submit copies and

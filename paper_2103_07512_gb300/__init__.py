@@ -30,7 +30,7 @@ EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tg
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
            "tgp_calibrate_op_costs", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune",
            "tgp_server_create", "tgp_server_destroy", "tgp_server_submit", "tgp_server_wait",
-           "tgp_server_stats_get"]
+           "tgp_server_stats_get", "tgp_evolve", "tgp_population_tokens"]
 
 
 class TgpError(RuntimeError):
@@ -100,6 +100,14 @@ class ServerStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
+class EvolveConfig(ctypes.Structure):
+    _fields_ = [("tournament", ctypes.c_int32), ("p_crossover", ctypes.c_float), ("p_mutation", ctypes.c_float),
+                ("elitism", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("mutation_depth", ctypes.c_int32),
+                ("functions", ctypes.c_void_p), ("n_functions", ctypes.c_int32),
+                ("const_lo", ctypes.c_float), ("const_hi", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
 _lib = None
 
 
@@ -136,6 +144,8 @@ def lib():
             "tgp_server_submit": [P, P, P],
             "tgp_server_wait": [P, i64, i64, P, P],
             "tgp_server_stats_get": [P, P],
+            "tgp_evolve": [P, i64, P, P, P],
+            "tgp_population_tokens": [P, i64, P, i64, P, i64, P, i64, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -261,6 +271,34 @@ class Context:
 
     def release_population(self, pop):
         self._check(self._L.tgp_release_population(self._h, pop))
+
+    def evolve(self, pop, rmse, seed, tournament=0, p_crossover=0.0, p_mutation=0.0, elitism=0, max_depth=0,
+               mutation_depth=0, functions=None, const_range=(0.0, 0.0)):
+        """tgp_evolve: the next generation of `pop` from its RMSE values, as a
+        new population handle (zero arguments take the library's defaults)."""
+        rmse = np.ascontiguousarray(rmse, np.float64)
+        fn = None if functions is None else np.ascontiguousarray(functions, np.int32)
+        cfg = EvolveConfig(tournament=tournament, p_crossover=p_crossover, p_mutation=p_mutation,
+                           elitism=elitism, max_depth=max_depth, mutation_depth=mutation_depth,
+                           functions=None if fn is None else fn.ctypes.data,
+                           n_functions=0 if fn is None else fn.size,
+                           const_lo=const_range[0], const_hi=const_range[1], seed=seed)
+        out = ctypes.c_int64()
+        self._check(self._L.tgp_evolve(self._h, pop, _ptr(rmse), ctypes.byref(cfg), ctypes.byref(out)))
+        return out.value
+
+    def population_tokens(self, pop):
+        """tgp_population_tokens: the population's trees as prefix tokens (inputs.Tokens)."""
+        from .inputs import Tokens
+        no, ni, nt = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        sizes = (ctypes.byref(no), ctypes.byref(ni), ctypes.byref(nt))
+        self._check(self._L.tgp_population_tokens(self._h, pop, None, 0, None, 0, None, 0, *sizes))
+        ops = np.empty(no.value, np.int32)
+        imm = np.empty(ni.value, np.float32)
+        off = np.empty(nt.value + 1, np.int64)
+        self._check(self._L.tgp_population_tokens(self._h, pop, _ptr(ops), ops.size, _ptr(imm), imm.size,
+                                                  _ptr(off), off.size, *sizes))
+        return Tokens(ops, imm, off, PREFIX)
 
     def evaluate(self, pop, dom, out, stream=None):
         """tgp_evaluate into a device float32 buffer [n_trees, H*W] (torch tensor)."""

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libtgp.so")
 BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu", "server.cpp"]
+SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu", "server.cpp", "evolve.cpp"]
 HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h", "gen_fastloop.py"]
 
 

@@ -705,7 +705,8 @@ void adopt_ir(tgp_ctx* ctx, Population* pop) {
             const DagNode& dn = nodes[n];
             int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
             int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
-            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm);
+            int32_t k2 = dn.kid[2] >= 0 ? pop->gid[dn.kid[2]] : -1;
+            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm, k2);
         }
     }
     ctx->stats.tree_nodes = pop->ir.tree_nodes;
@@ -803,6 +804,15 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
 }
 
 bool context_simplifies(const tgp_ctx* ctx) { return simplify_on(ctx); }
+
+int population_copy(tgp_ctx* ctx, tgp_handle pop, PopIR* out) {
+    if (!ctx || !out) return fail(TGP_E_INVALID, "ctx / out is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    if (!p) return fail(TGP_E_INVALID, "unknown population handle %lld", (long long)pop);
+    *out = p->ir;
+    return TGP_OK;
+}
 
 int context_device(tgp_ctx* ctx, int* device) {
     if (!ctx || !device) return fail(TGP_E_INVALID, "ctx / device is NULL");

@@ -247,7 +247,7 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
 
 // One token's node.  clip(x, y, z) is its printed definition,
 // max(min(z, x), y) (Table 1), so it needs no instruction of its own.
-static int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits, bool simplify) {
+int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits, bool simplify) {
     auto mk = [&](int o, int32_t a, int32_t b, uint32_t imm, int32_t c) {
         return simplify ? intern_simplified(dag, o, a, b, imm, c) : dag.intern(o, a, b, imm, c);
     };
@@ -257,7 +257,7 @@ static int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_
 
 // Drops DAG nodes no tree reaches (operands that simplification bypassed),
 // keeping ids in topological order.
-static void compact(PopIR& pop) {
+void compact(PopIR& pop) {
     const size_t n = pop.dag.size();
     std::vector<uint8_t> live(n, 0);
     for (int32_t r : pop.roots) live[r] = 1;

@@ -116,4 +116,11 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
 
 Ins encode(const IrIns& in);
 
+// The node of one token with operands k (as the parser makes it: clip is
+// lowered to max(min(z, x), y); simplified when `simplify`).
+int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits, bool simplify);
+
+// Drops DAG nodes no tree reaches, keeping ids in topological order.
+void compact(PopIR& pop);
+
 }  // namespace tgp

@@ -30,6 +30,9 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
 int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi, int32_t target_kind,
                 const void* target, void* stream, bool sync, tgp_handle* domain_out);
 
+// A copy of a population's IR (its DAG and roots).
+int population_copy(tgp_ctx* ctx, tgp_handle pop, PopIR* out);
+
 // Whether the context simplifies populations while compiling them.
 bool context_simplifies(const tgp_ctx* ctx);
 

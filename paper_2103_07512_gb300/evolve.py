@@ -1,9 +1,16 @@
-"""Generational GP on the host around the GPU fitness path.
+"""Generational GP around the GPU fitness path.
 
-Each generation the whole population is written as tokens, compiled into one
-population DAG and scored in one fitness call; selection and variation run on
-the host (TensorGP, Sec. 3 and Table 2: tournament selection, subtree
-crossover and subtree mutation, elitism).  With a context created with a
+Two drivers of the same algorithm (TensorGP, Sec. 3 and Table 2: tournament
+selection, subtree crossover and subtree mutation, elitism):
+  * Evolution: the population lives as Python trees; each generation is
+    written as tokens, compiled into one population DAG and scored in one
+    fitness call.  Any fitness callable works (the oracle, the GPU path).
+  * DeviceEvolution: the population stays a library population; the
+    variation step runs in the library on the population DAG (tgp_evolve),
+    so unchanged subtrees are never re-parsed and no tokens cross the API
+    between generations.
+Their random streams differ (numpy here, splitmix64 in the library), so the
+two produce different runs of the same algorithm.  With a context created with a
 non-zero cache budget, subtrees that survive from one generation to the next
 are read back from the device-resident subtree cache instead of being
 evaluated again (Sec. 2, Handley's DAG caching across evaluations).
@@ -144,6 +151,64 @@ class Evolution:
         return self.history
 
 
+class DeviceEvolution:
+    """The generational loop with selection and variation in the library
+    (tgp_evolve); `ctx` is a library context and `domain` a loaded domain.
+    The initial population is the same ramped half-and-half draw as
+    Evolution's for the same seed."""
+
+    def __init__(self, ctx, domain, pop_size=50, generations=50, seed=0, tournament=3, p_crossover=0.9,
+                 p_mutation=0.1, elitism=1, max_depth=12, init_depth=(2, 6), mutation_depth=4,
+                 funcs=I.FUNCTIONS):
+        self.ctx = ctx
+        self.domain = domain
+        self.pop_size = pop_size
+        self.generations = generations
+        self.seed = seed
+        self.params = dict(tournament=tournament, p_crossover=p_crossover, p_mutation=p_mutation,
+                           elitism=elitism, max_depth=max_depth, mutation_depth=mutation_depth,
+                           functions=list(funcs))
+        rng = np.random.default_rng(seed)
+        self.pop = ctx.compile_tokens(I.to_tokens(I.ramped_half_and_half(pop_size, init_depth[0], init_depth[1],
+                                                                         rng, funcs)))
+        self.history: list[Generation] = []
+        self.variation_seconds = 0.0
+        self.best = None
+
+    def step(self, on_generation=None):
+        ctx = self.ctx
+        t0 = time.perf_counter()
+        rmse = ctx.fitness(self.pop, self.domain, self.pop_size)
+        dt = time.perf_counter() - t0
+        st = ctx.stats()
+        best = min(range(len(rmse)), key=lambda i: (_rank_key(rmse[i]), i))
+        if self.best is None or _rank_key(rmse[best]) < _rank_key(self.best[1]):
+            tok = ctx.population_tokens(self.pop)
+            self.best = (I.from_tokens(tok)[best], float(rmse[best]))
+        g = Generation(len(self.history), float(rmse[best]), st["tree_nodes"] / self.pop_size,
+                       int(st["tree_nodes"]), dt)
+        if on_generation:
+            on_generation(g, rmse)
+        self.history.append(g)
+        t1 = time.perf_counter()
+        gen_seed = (self.seed * 1000003 + len(self.history)) & 0xFFFFFFFFFFFFFFFF
+        nxt = ctx.evolve(self.pop, rmse, seed=gen_seed, **self.params)
+        ctx.release_population(self.pop)
+        self.pop = nxt
+        self.variation_seconds += time.perf_counter() - t1
+        return rmse
+
+    def run(self, on_generation=None):
+        for _ in range(self.generations):
+            self.step(on_generation)
+        return self.history
+
+    def close(self):
+        if self.pop is not None:
+            self.ctx.release_population(self.pop)
+            self.pop = None
+
+
 def gpu_fitness(ctx, domain):
     """Fitness callable for Evolution on a library context and loaded domain:
     compiles the generation's tokens, scores them, releases the population."""
@@ -169,10 +234,15 @@ def main(argv=None):
     ap.add_argument("--cache-gb", type=float, default=20.0, help="subtree cache budget (0: off)")
     ap.add_argument("--min-cost", type=int, default=0, help="store threshold of the cache (0: default)")
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--variation", choices=("host", "library"), default="host",
+                    help="selection and variation in Python (host) or in the library on the DAG (library)")
     a = ap.parse_args(argv)
     with Context(device=a.device, cache_budget_bytes=int(a.cache_gb * 1e9), cache_min_cost=a.min_cost) as ctx:
         dom = ctx.load_domain(a.grid, a.grid)
-        ev = Evolution(gpu_fitness(ctx, dom), pop_size=a.population, generations=a.generations, seed=a.seed)
+        if a.variation == "library":
+            ev = DeviceEvolution(ctx, dom, pop_size=a.population, generations=a.generations, seed=a.seed)
+        else:
+            ev = Evolution(gpu_fitness(ctx, dom), pop_size=a.population, generations=a.generations, seed=a.seed)
 
         def report(g, rmse):
             st = ctx.stats()

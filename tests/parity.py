@@ -104,6 +104,30 @@ def assert_fitness(gpu, r64, rmse_err, n_points, context=""):
     return skipped
 
 
+def assert_fitness_of_phenotype(gpu_fit, phenotype, target, trees, context="", rtol=1e-4):
+    """For trees whose oracle fitness is not comparable (an unbounded element):
+    the device RMSE against the binary64 RMSE of the device's own phenotype
+    (checks the fused residual-and-reduction step on exactly those trees).
+    rtol covers the binary32 target and the binary32 per-warp sums."""
+    ref = rmse_of(np.asarray(phenotype)[trees], target)
+    got = np.asarray(gpu_fit, np.float64)[trees]
+    n = np.asarray(phenotype).shape[1]
+    bad = []
+    for t, g, r in zip(trees, got, ref):
+        if np.isinf(r) or np.isinf(g):
+            if not (np.isinf(g) and (np.isinf(r) or n * r * r >= FLT_MAX / 2)):
+                bad.append((int(t), g, r))
+        elif abs(g - r) > rtol * abs(r) + FIT_ATOL:
+            bad.append((int(t), g, r))
+    assert not bad, f"{context}: device fitness off its own phenotype for {len(bad)} trees, first {bad[:5]}"
+
+
+def grid_target(g):
+    """Eq. 1 in binary64 at the grid's binary32 points, flat in point order."""
+    import oracle
+    return np.array([oracle.pagie(*oracle.grid_point(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, p)) for p in range(g.N)])
+
+
 def oracle_fitness_chunk(args):
     """Worker for a spawn process pool: oracle fitness of one chunk of trees."""
     import oracle

@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import assert_elements, assert_fitness
+from parity import assert_elements, assert_fitness, assert_fitness_of_phenotype, grid_target
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +43,8 @@ def test_all_operators_against_oracle(K):
     r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
                                    g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
     assert_fitness(fit, r64, re, g.N, "all operators")
+    skipped = np.flatnonzero(~np.isfinite(re))
+    assert_fitness_of_phenotype(fit, ph, grid_target(g), skipped, f"all operators K={K}")
 
 
 def test_exactly_rounded_operators_equal_fp32_faithful():

@@ -123,6 +123,10 @@ enum {
                                  for add and mul.  Each is exact in binary32, so
                                  results are bitwise those of the trees as given
                                  (a NaN may differ in sign or payload). */
+#define TGP_F_TRIG_RADIANS 16 /* sin, cos and tan take their argument in radians
+                                 (the footnote of Table 1) instead of multiplied
+                                 by pi (Sec. 3.2, the default): CUDA's binary32
+                                 sinf, cosf and tanf (within 2, 2 and 4 ulp) */
 
 /* Context configuration.  Zero-initialise, then set what you need. */
 typedef struct tgp_config {

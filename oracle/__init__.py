@@ -59,10 +59,10 @@ def _load():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         lib.oracle_eval.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
-                                    i64, P, P, P, P, P]
+                                    i64, P, P, P, P, P, i32]
         lib.oracle_eval.restype = ctypes.c_int
         lib.oracle_fitness.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
-                                       i32, P, i64, P, P, P, P, P]
+                                       i32, P, i64, P, P, P, P, P, i32]
         lib.oracle_fitness.restype = ctypes.c_int
         lib.oracle_pagie.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.oracle_pagie.restype = ctypes.c_double
@@ -96,8 +96,20 @@ def _pop_arrays(ops, imm, tree_off):
     return ops, imm, tree_off
 
 
-def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None, with_bound=False):
+TRIG_MODES = {"pi": 0, "rad": 1}
+
+
+def _trig(trig):
+    if trig not in TRIG_MODES:
+        raise ValueError(f"trig must be one of {sorted(TRIG_MODES)}")
+    return TRIG_MODES[trig]
+
+
+def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None, with_bound=False, trig="pi"):
     """Phenotypes of every tree.
+
+    trig: "pi" (sin(a) = sin(pi a), Sec. 3.2) or "rad" (radians, the footnote
+    of Table 1); it applies to sin, cos and tan.
 
     Returns (v64 [T, n], v32 [T, n], flags [T, n]) where n = H*W (all points in
     flat order) or len(pts).  v32 is the FP32-faithful evaluation, flags marks
@@ -119,7 +131,7 @@ def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None, with
     eb = np.empty((T, n), np.float64) if with_bound else None
     rc = lib.oracle_eval(_ptr(ops), _ptr(imm), imm.size, _ptr(tree_off), T, order,
                          W, H, xlo, xhi, ylo, yhi, n, _ptr(pts_arr), _ptr(v64), _ptr(v32), _ptr(fl),
-                         _ptr(eb))
+                         _ptr(eb), _trig(trig))
     if rc != 0:
         raise OracleError(f"oracle_eval failed: {rc}")
     if with_bound:
@@ -128,8 +140,9 @@ def evaluate(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, pts=None, with
 
 
 def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pts=None,
-            with_bound=False):
-    """RMSE of every tree against Pagie (target None) or a [H*W] value array.
+            with_bound=False, trig="pi"):
+    """RMSE of every tree against Pagie (target None) or a [H*W] value array
+    (trig as for evaluate).
 
     Returns (rmse64 [T], rmse32 [T], n_flagged [T]); with with_bound=True also
     rmse_err [T], the L2 bound of the per-element binary32 error bounds.
@@ -154,7 +167,7 @@ def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pt
     re = np.empty(T, np.float64) if with_bound else None
     rc = lib.oracle_fitness(_ptr(ops), _ptr(imm), imm.size, _ptr(tree_off), T, order,
                             W, H, xlo, xhi, ylo, yhi, kind, _ptr(tv), n, _ptr(pts_arr),
-                            _ptr(r64), _ptr(r32), _ptr(nf), _ptr(re))
+                            _ptr(r64), _ptr(r32), _ptr(nf), _ptr(re), _trig(trig))
     if rc != 0:
         raise OracleError(f"oracle_fitness failed: {rc}")
     if with_bound:

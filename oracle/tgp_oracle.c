@@ -17,7 +17,9 @@
  *     its mathematical and conditional operators: tan, exp, log with -1 for a
  *     negative argument, pow with 0 for 0^0, mdist, sqrt with 0 for a negative
  *     argument, sign, clip, mod, frac, if);
- *   - trigonometric operators take the argument multiplied by pi: Sec. 3.2;
+ *   - trigonometric operators take the argument multiplied by pi: Sec. 3.2
+ *     (the default); the footnote of Table 1 states radians instead, which
+ *     the `trig` argument selects (1: sin(a), cos(a), tan(a) of a itself);
  *   - Pagie polynomial target: Eq. 1;
  *   - RMSE fitness against the target: Sec. 4.1 and Table 2.
  *
@@ -70,7 +72,8 @@
  *   a / b:   P = (Ea + |a/b| Eb) / (|b| - Eb), unbounded if |b| <= Eb (the
  *            sign or zero test of the denominator is then undecided); 0 for
  *            an exact zero denominator (the protected result is exactly 0)
- *   sin/cos(pi a): P = min(pi Ea, 2), plus 2 ulp of the result
+ *   sin/cos(pi a): P = min(pi Ea, 2), plus 2 ulp of the result (radians:
+ *            P = min(Ea, 2); tan likewise with pi replaced by 1)
  *   -a, |a|: Ea;  min/max: max(Ea, Eb)
  *   tan(pi a): P = pi Ea / (|c| - pi Ea)^2 with c = cos(pi a), unbounded if
  *            |c| <= pi Ea; plus 4 ulp (a quotient of two trig values)
@@ -329,11 +332,12 @@ static double floor_mod(double a, double b)
     return r;
 }
 
-/* One operator of Table 1 applied in binary64 (c: third operand). */
-static double apply64(int op, double a, double b, double c)
+/* One operator of Table 1 applied in binary64 (c: third operand; rad:
+ * trigonometric arguments in radians instead of multiplied by pi). */
+static double apply64(int op, double a, double b, double c, int rad)
 {
     switch (op) {
-    case O_TAN: return oracle_sinpi(a) / oracle_cospi(a);
+    case O_TAN: return rad ? tan(a) : oracle_sinpi(a) / oracle_cospi(a);
     case O_EXP: return exp(a);
     case O_LOG: return plog(a);
     case O_POW: return ppow(a, b);
@@ -348,8 +352,8 @@ static double apply64(int op, double a, double b, double c)
     case O_SUB: return a - b;
     case O_MUL: return a * b;
     case O_DIV: return pdiv(a, b);
-    case O_SIN: return oracle_sinpi(a);
-    case O_COS: return oracle_cospi(a);
+    case O_SIN: return rad ? sin(a) : oracle_sinpi(a);
+    case O_COS: return rad ? cos(a) : oracle_cospi(a);
     case O_NEG: return -a;
     case O_ABS: return fabs(a);
     case O_MIN: return fmin(a, b);
@@ -394,8 +398,9 @@ static double ulps32(double k, double m)
 }
 
 /* Error bound of one node from its operands' bounds (see the header). */
-static double err_bound(int op, double a, double b, double c, double ea, double eb, double ec, double v)
+static double err_bound(int op, double a, double b, double c, double ea, double eb, double ec, double v, int rad)
 {
+    const double k = rad ? 1.0 : ORACLE_PI;   /* d(argument)/da of the trigonometric operators */
     double e, prop;
     if (op == O_IF) {   /* only the chosen operand matters, once the zero test is decided */
         if (!isfinite(v) || !isfinite(ea)) return INFINITY;
@@ -407,10 +412,10 @@ static double err_bound(int op, double a, double b, double c, double ea, double 
     if (!isfinite(v) || !isfinite(ea) || !isfinite(eb) || !isfinite(ec)) return INFINITY;
     switch (op) {
     case O_TAN: {
-        double cs = fabs(oracle_cospi(a));
-        if (cs <= ORACLE_PI * ea) return INFINITY;
-        double d = cs - ORACLE_PI * ea;
-        prop = ORACLE_PI * ea / (d * d);
+        double cs = fabs(rad ? cos(a) : oracle_cospi(a));
+        if (cs <= k * ea) return INFINITY;
+        double d = cs - k * ea;
+        prop = k * ea / (d * d);
         e = prop + ulps32(TAN_ULPS, fabs(v) + prop);
         break;
     }
@@ -495,7 +500,7 @@ static double err_bound(int op, double a, double b, double c, double ea, double 
         e = prop + rnd32(v, prop, 0);
         break;
     case O_SIN: case O_COS:
-        prop = fmin(ORACLE_PI * ea, 2.0);
+        prop = fmin(k * ea, 2.0);
         e = prop + TRIG_ULPS * (2.0 * U32 * (fabs(v) + prop) + TINY32);
         break;
     case O_NEG: case O_ABS:
@@ -514,6 +519,7 @@ static double err_bound(int op, double a, double b, double c, double ea, double 
 typedef struct {
     double x64, y64;   /* coordinates (binary32 values widened) */
     int flag;          /* near-singular division seen */
+    int rad;           /* trigonometric arguments in radians */
 } opoint;
 
 /* Recursive tree walk in both modes at once, with the error bound. */
@@ -534,9 +540,9 @@ static void eval_node(const onode* nodes, int i, opoint* pt, double* v64, float*
     if (n->op == O_DIV) {
         if (fabs(b64) < NEAR_SINGULAR || fabs((double)b32) < NEAR_SINGULAR) pt->flag = 1;
     }
-    *v64 = apply64(n->op, a64, b64, c64);
-    *v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32);
-    *eb = err_bound(n->op, a64, b64, c64, ea, eb_, ec, *v64);
+    *v64 = apply64(n->op, a64, b64, c64, pt->rad);
+    *v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32, pt->rad);
+    *eb = err_bound(n->op, a64, b64, c64, ea, eb_, ec, *v64, pt->rad);
 }
 
 /* ------------------------------------------------------------------ grid */
@@ -577,15 +583,16 @@ double oracle_pagie(double x, double y)
  *   out32 [n_trees][n_pts]  FP32-faithful values (may be NULL)
  *   flags [n_trees][n_pts]  1 where a division saw |denominator| < 1e-6 (may be NULL)
  *   errb  [n_trees][n_pts]  bound on |any binary32 evaluation - exact| (may be NULL)
+ * trig: 0 = trigonometric arguments multiplied by pi (Sec. 3.2), 1 = radians.
  * Returns 0 or a negative error code (malformed tokens, bad opcode, imm count).
  */
 int oracle_eval(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                 int32_t n_trees, int32_t order,
                 int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                 int64_t n_pts, const int64_t* pts,
-                double* out64, float* out32, uint8_t* flags, double* errb)
+                double* out64, float* out32, uint8_t* flags, double* errb, int32_t trig)
 {
-    if (n_trees < 0 || W <= 0 || H <= 0 || n_pts < 0) return OR_ARG;
+    if (n_trees < 0 || W <= 0 || H <= 0 || n_pts < 0 || (trig != 0 && trig != 1)) return OR_ARG;
     otree* trees = (otree*)calloc((size_t)(n_trees > 0 ? n_trees : 1), sizeof(otree));
     if (!trees) return OR_NOMEM;
     int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, trees);
@@ -595,7 +602,7 @@ int oracle_eval(const int32_t* ops, const float* imm, int64_t n_imm, const int64
             int64_t p = pts ? pts[i] : i;
             float xf, yf;
             oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
-            opoint pt = { (double)xf, (double)yf, 0 };
+            opoint pt = { (double)xf, (double)yf, 0, trig };
             double v64, e;
             float v32;
             eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32, &e);
@@ -625,16 +632,16 @@ enum { TG_PAGIE = 0, TG_VALUES = 1 };
  *     bound on how far the RMSE of any binary32 evaluation of the phenotype
  *     can be from rmse64 (triangle inequality in the L2 norm); +inf when
  *     some element is unbounded (may be NULL).
- * A non-finite sum gives +inf.
+ * trig as for oracle_eval.  A non-finite sum gives +inf.
  */
 int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                    int32_t n_trees, int32_t order,
                    int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                    int32_t target_kind, const double* target_vals,
                    int64_t n_pts, const int64_t* pts,
-                   double* rmse64, double* rmse32, int64_t* n_flagged, double* rmse_err)
+                   double* rmse64, double* rmse32, int64_t* n_flagged, double* rmse_err, int32_t trig)
 {
-    if (n_trees < 0 || W <= 0 || H <= 0) return OR_ARG;
+    if (n_trees < 0 || W <= 0 || H <= 0 || (trig != 0 && trig != 1)) return OR_ARG;
     if (target_kind == TG_VALUES && !target_vals) return OR_ARG;
     if (target_kind != TG_PAGIE && target_kind != TG_VALUES) return OR_ARG;
     int64_t N = pts ? n_pts : (int64_t)W * (int64_t)H;
@@ -650,7 +657,7 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
             float xf, yf;
             oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
             double tv = target_kind == TG_PAGIE ? oracle_pagie((double)xf, (double)yf) : target_vals[p];
-            opoint pt = { (double)xf, (double)yf, 0 };
+            opoint pt = { (double)xf, (double)yf, 0, trig };
             double v64, e;
             float v32;
             eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32, &e);

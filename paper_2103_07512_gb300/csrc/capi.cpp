@@ -273,6 +273,10 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
     return s;
 }
 
+bool trig_radians(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_TRIG_RADIANS) != 0; }
+// Radian trigonometry runs in the interpreter variant with the rest of Table 1.
+bool use_ext(const tgp_ctx* c, const HostPlan& hp) { return hp.ext || trig_radians(c); }
+
 int occupancy(tgp_ctx* c, int K, bool pheno, bool ext, int threads, size_t smem, int* out) {
     auto key = std::make_tuple(K, (int)pheno * 2 + (int)ext, threads, smem);
     auto it = c->occ.find(key);
@@ -364,7 +368,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         }
     }
     int bps = 0;
-    int rc = occupancy(c, shape.K, pheno, pl->hp.ext, shape.threads, pl->smem, &bps);
+    int rc = occupancy(c, shape.K, pheno, use_ext(c, pl->hp), shape.threads, pl->smem, &bps);
     if (rc) return rc;
     int64_t slots = (int64_t)bps * std::max(c->sms, 1);
     pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl->hp.n_items, slots));
@@ -633,6 +637,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.counter = pl->counter.p;
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
+    p.trig_rad = trig_radians(c) ? 1 : 0;
     if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
     CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
@@ -651,7 +656,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         }
         CUDA_TRY(cudaEventRecord(ev.first, s));
     }
-    CUDA_TRY(launch_eval(p, hp.shape.K, pheno, hp.ext, pl->grid, hp.shape.threads, pl->smem, s));
+    CUDA_TRY(launch_eval(p, hp.shape.K, pheno, use_ext(c, hp), pl->grid, hp.shape.threads, pl->smem, s));
     if (timed) {
         CUDA_TRY(cudaEventRecord(ev.second, s));
         c->ev_pending.push_back(ev);
@@ -742,6 +747,7 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->shape = choose_shape(ctx, p->ir, d->N());
     v->sms = ctx->sms;
     v->device = ctx->device;
+    v->trig_radians = trig_radians(ctx);
     return TGP_OK;
 }
 
@@ -893,6 +899,9 @@ int tgp_create(tgp_ctx** out, const tgp_config* cfg) {
     std::unique_ptr<tgp_ctx> c(new (std::nothrow) tgp_ctx());
     if (!c) return fail(TGP_E_NOMEM, "out of host memory");
     if (cfg) c->cfg = *cfg;
+    constexpr int32_t kKnownFlags =
+        TGP_F_HOST_ONLY | TGP_F_NO_DEDUP | TGP_F_TIME_KERNELS | TGP_F_NO_SIMPLIFY | TGP_F_TRIG_RADIANS;
+    if (c->cfg.flags & ~kKnownFlags) return fail(TGP_E_INVALID, "unknown flag bits 0x%x", c->cfg.flags & ~kKnownFlags);
     c->device = c->cfg.device;
     if (c->cfg.flags & TGP_F_HOST_ONLY) {
         c->host_only = true;

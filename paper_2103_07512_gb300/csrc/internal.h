@@ -19,6 +19,7 @@ struct View {
     PlanShape shape;                 // the shape tgp_fitness would use
     int sms = 0;
     int device = 0;
+    bool trig_radians = false;       // TGP_F_TRIG_RADIANS
 };
 
 // Locks the context into `lk`, makes its device current and fills `v`.

@@ -117,7 +117,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
 
     const size_t smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.n_slots);
     int bps = 0;
-    NA_TRY(eval_occupancy(hp.shape.K, false, hp.ext, hp.shape.threads, smem, &bps));
+    NA_TRY(eval_occupancy(hp.shape.K, false, hp.ext || v.trig_radians, hp.shape.threads, smem, &bps));
     if (bps <= 0) return internal::set_error(TGP_E_INVALID, "interpreter cannot be resident with this plan");
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(hp.n_items, (int64_t)bps * std::max(v.sms, 1)));
 
@@ -142,7 +142,8 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.counter = counter;
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
-    NA_TRY(launch_eval(p, hp.shape.K, false, hp.ext, grid, hp.shape.threads, smem, s));
+    p.trig_rad = v.trig_radians ? 1 : 0;
+    NA_TRY(launch_eval(p, hp.shape.K, false, hp.ext || v.trig_radians, grid, hp.shape.threads, smem, s));
 
     FinalizeParams f{};
     f.partial = partial;

@@ -141,6 +141,7 @@ struct EvalParams {
     int32_t* counter;           // work-queue head, zero before the launch
     int32_t n_slots;            // shared-memory value slots per thread
     int32_t max_items_per_cta;  // bound on the work-queue loop
+    int32_t trig_rad;           // sin/cos/tan in radians (interpreter variant with the rest of Table 1 only)
 };
 
 struct FinalizeParams {

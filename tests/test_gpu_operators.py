@@ -143,3 +143,50 @@ def test_sin_cos_pi_within_one_ulp(lo, hi):
         assert err.max() <= 1.0, (row, float(err.max()), xs[int(err.argmax())])
         zero = exact == 0
         assert np.all(ph[row][zero] == 0)
+
+
+@pytest.mark.parametrize("K", [1, 8])
+def test_radian_trigonometry_against_oracle(K):
+    """TGP_F_TRIG_RADIANS (the footnote of Table 1): sin, cos and tan of the
+    argument itself, every element and fitness against the oracle's radian
+    mode, and not the default pi-scaled values."""
+    rng = np.random.default_rng(54)
+    funcs = (I.ADD, I.SUB, I.MUL, I.DIV, I.SIN, I.COS, I.TAN, I.NEG, I.MIN)
+    trees = [I._full(rng, int(rng.integers(2, 6)), funcs) for _ in range(150)]
+    trees += [I.parse_string(e) for e in ("sin(x)", "cos(y)", "tan(x)", "sin(mult(x, 40.0))")]
+    tok = I.to_tokens(trees)
+    g = I.Grid(37, 21)
+    with tgp.Context(points_per_thread=K, trig="rad") as ctx:
+        ph, fit = device(ctx, tok, g)
+    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
+    c = assert_elements(ph, v64, fl, eb, context=f"radians K={K}", v32=v32)
+    assert c["n"] - c["n_excluded"] > 0.8 * c["n"]
+    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
+    assert_fitness(fit, r64, re, g.N, "radians")
+    xs = np.array([oracle.grid_point(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, p)[0] for p in range(g.N)])
+    assert np.allclose(ph[-4], np.sin(xs), rtol=0, atol=2e-7)
+    with tgp.Context(points_per_thread=K) as ctx:
+        pi_ph, _ = device(ctx, tok, g)
+    assert not np.allclose(pi_ph[-4], ph[-4], atol=1e-3)
+
+
+def test_radian_mode_with_cache_and_noalloc_paths():
+    rng = np.random.default_rng(55)
+    tok = I.to_tokens([I._full(rng, 4, I.FUNCTIONS) for _ in range(40)])
+    g = I.Grid(64, 48)
+    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
+                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
+    with tgp.Context(trig="rad", cache_budget_bytes=64 * g.N * 4, cache_min_cost=1) as ctx:
+        dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+        pop = ctx.compile_tokens(tok)
+        runs = [ctx.fitness(pop, dom, tok.n_trees) for _ in range(3)]
+        out = torch.empty(tok.n_trees, dtype=torch.float64, device="cuda")
+        ctx.fitness_noalloc(pop, dom, out)
+        torch.cuda.synchronize()
+        assert ctx.stats()["cache_hits"] > 0
+    for r in runs[1:]:
+        assert np.array_equal(r.view(np.int64), runs[0].view(np.int64))
+    assert np.array_equal(out.cpu().numpy().view(np.int64), runs[0].view(np.int64))
+    assert_fitness(runs[0], r64, re, g.N, "radians, cached")

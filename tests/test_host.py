@@ -477,3 +477,15 @@ def test_three_operand_tokens_validate(ctx):
     with pytest.raises(tgp.TgpError) as e:
         ctx.compile_tokens(bad)
     assert e.value.code == tgp.E_TOKENS
+
+
+def test_unknown_context_flags_and_trig_mode_are_refused():
+    import ctypes
+    cfg = tgp.Config()
+    cfg.flags = tgp.F_HOST_ONLY | 1024
+    h = ctypes.c_void_p()
+    assert tgp.lib().tgp_create(ctypes.byref(h), ctypes.byref(cfg)) == tgp.E_INVALID
+    with pytest.raises(ValueError):
+        tgp.Context(host_only=True, trig="degrees")
+    with tgp.Context(host_only=True, trig="rad") as c:
+        c.compile_tokens(I.to_tokens([I.parse_string("sin(x)")]))

@@ -586,3 +586,65 @@ def test_error_bound_new_operators_closed_forms():
     assert np.all(eb[6] <= 2 * (2 * U32 + 2.0 ** -149) * (1 + 1e-12))
     # sign of a rounded value: undecided only where it is within its bound of 0
     assert np.all(np.isfinite(eb[7][X != 0]))
+
+
+# ------------------------------------------------ radians (Table 1 footnote)
+
+def ev_rad(exprs, W, H, lo=-5.0, hi=5.0, with_bound=False):
+    t = toks(*exprs)
+    return oracle.evaluate(t.ops, t.imm, t.tree_off, 0, W, H, lo, hi, lo, hi, with_bound=with_bound, trig="rad")
+
+
+def test_radian_trig_is_the_library_function_of_the_argument():
+    W, H = 9, 4
+    X, Y = np_grid(W, H)
+    v64, v32, _ = ev_rad(["sin(x)", "cos(y)", "tan(x)", "sin(0.5)", "cos(3.0)"], W, H)
+    assert np.array_equal(v64[0], np.sin(X)) and np.array_equal(v64[1], np.cos(Y))
+    assert np.allclose(v64[2], np.tan(X), rtol=1e-15, atol=0)
+    assert np.all(v64[3] == math.sin(0.5)) and np.all(v64[4] == math.cos(3.0))
+    assert np.array_equal(v32[0], np.sin(X).astype(np.float32))
+    # not pi-scaled, and the default is still pi-scaled
+    p64, _, _ = ev(["sin(x)"], W, H)
+    assert not np.allclose(p64[0], v64[0], atol=1e-3)
+
+
+def test_radian_trig_identities():
+    W, H = 13, 7
+    v64, _, _ = ev_rad(["add(mult(sin(x), sin(x)), mult(cos(x), cos(x)))", "sub(tan(y), div(sin(y), cos(y)))",
+                        "add(sin(neg(x)), sin(x))"], W, H, lo=-40.0, hi=40.0)
+    assert np.allclose(v64[0], 1.0, rtol=0, atol=1e-15)
+    assert np.allclose(v64[1], 0.0, rtol=0, atol=1e-12)
+    assert np.all(v64[2] == 0.0)
+
+
+def test_radian_fitness_by_hand():
+    W, H = 4, 3
+    X, Y = np_grid(W, H)
+    t = toks("cos(x)")
+    r64, _, _ = oracle.fitness(t.ops, t.imm, t.tree_off, 0, W, H, -5, 5, -5, 5, trig="rad")
+    P = X ** 4 / (1 + X ** 4) + Y ** 4 / (1 + Y ** 4)
+    assert r64[0] == pytest.approx(math.sqrt(np.mean((np.cos(X) - P) ** 2)), rel=1e-14)
+
+
+def test_radian_error_bound_contains_fp32_faithful_and_propagates():
+    rng = np.random.default_rng(11)
+    trees = [I._full(rng, int(rng.integers(2, 6)), (I.ADD, I.MUL, I.SIN, I.COS, I.TAN, I.SUB)) for _ in range(60)]
+    t = I.to_tokens(trees)
+    v64, v32, _, eb = oracle.evaluate(t.ops, t.imm, t.tree_off, 0, 23, 19, 10.0, 20.0, -5, 5, with_bound=True,
+                                      trig="rad")
+    m = np.isfinite(v64) & np.isfinite(eb)
+    assert m.mean() > 0.8
+    assert np.all(np.abs(v32.astype(np.float64) - v64)[m] <= eb[m])
+    W, H = 5, 3
+    X, Y = np_grid(W, H)
+    _, _, _, e = ev_rad(["sin(add(x, y))", "sin(x)"], W, H, with_bound=True)
+    # rounded argument: |cos| <= 1, so E(arg) itself is propagated (not pi E(arg))
+    assert np.all(e[0] >= U32 * np.abs(X + Y) * (1 - 1e-12))
+    assert np.all(e[0] < np.pi * U32 * np.abs(X + Y) + 4 * (2 * U32 + 2.0 ** -149))
+    assert np.all(e[1] <= 2 * (2 * U32 * np.abs(np.sin(X)) + 2.0 ** -149) * (1 + 1e-12))
+
+
+def test_unknown_trig_mode_is_refused():
+    t = toks("sin(x)")
+    with pytest.raises(ValueError):
+        oracle.evaluate(t.ops, t.imm, t.tree_off, 0, 2, 2, -5, 5, -5, 5, trig="degrees")

@@ -18,8 +18,12 @@ MUTANTS = {
     "sub_operands_swapped": ("case O_SUB: return a - b;", "case O_SUB: return b - a;"),
     "div_protection_value": ("if (b == 0.0) return 0.0;", "if (b == 0.0) return 1.0;"),
     "trig_not_pi_scaled": ("double pf = ORACLE_PI * f, v;", "double pf = f, v;"),
-    "sin_cos_swapped": ("case O_SIN: return oracle_sinpi(a);\n    case O_COS: return oracle_cospi(a);",
-                        "case O_SIN: return oracle_cospi(a);\n    case O_COS: return oracle_sinpi(a);"),
+    "sin_cos_swapped": ("case O_SIN: return rad ? sin(a) : oracle_sinpi(a);\n    case O_COS: return rad ? cos(a) : oracle_cospi(a);",
+                        "case O_SIN: return rad ? sin(a) : oracle_cospi(a);\n    case O_COS: return rad ? cos(a) : oracle_sinpi(a);"),
+    "radian_sin_pi_scaled": ("case O_SIN: return rad ? sin(a)", "case O_SIN: return rad ? sin(ORACLE_PI * a)"),
+    "radian_cos_is_sin": ("case O_COS: return rad ? cos(a)", "case O_COS: return rad ? sin(a)"),
+    "radian_tan_pi_scaled": ("case O_TAN: return rad ? tan(a)", "case O_TAN: return rad ? tan(ORACLE_PI * a)"),
+    "bound_radian_no_propagation": ("const double k = rad ? 1.0 : ORACLE_PI;", "const double k = rad ? 0.0 : ORACLE_PI;"),
     "pagie_wrong_index": ("y4 / (1.0 + y4)", "x4 / (1.0 + y4)"),
     "pagie_dropped_term": ("return x4 / (1.0 + x4) + y4 / (1.0 + y4);", "return x4 / (1.0 + x4);"),
     "linspace_off_by_one": ("float step = (hi - lo) / (float)(n - 1);", "float step = (hi - lo) / (float)n;"),
@@ -28,14 +32,14 @@ MUTANTS = {
                                     "for (int c = 0; c < ar; c++) nodes[me].kid[c] = stack[--sp];"),
     "grid_row_col_swapped": ("int64_t row = p / W, col = p % W;", "int64_t col = p / W, row = p % W;"),
     "min_is_max": ("case O_MIN: return fmin(a, b);", "case O_MIN: return fmax(a, b);"),
-    "fp32_mode_not_rounded_per_node": ("*v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32);",
-                                       "*v32 = (float)apply64(n->op, a64, b64, c64);"),
+    "fp32_mode_not_rounded_per_node": ("*v32 = (float)apply64(n->op, (double)a32, (double)b32, (double)c32, pt->rad);",
+                                       "*v32 = (float)apply64(n->op, a64, b64, c64, pt->rad);"),
     "near_singular_threshold": ("#define NEAR_SINGULAR 1e-6", "#define NEAR_SINGULAR 1e-9"),
     "nan_fitness_not_inf": ("rmse64[t] = isfinite(r64) ? r64 : INFINITY;", "rmse64[t] = r64;"),
     "abs_dropped": ("case O_ABS: return fabs(a);", "case O_ABS: return a;"),
     "bound_mul_drops_term": ("prop = fabs(b) * ea + fabs(a) * eb + ea * eb;", "prop = fabs(b) * ea + ea * eb;"),
     "bound_div_drops_term": ("prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);", "prop = ea / (fabs(b) - eb);"),
-    "bound_trig_not_pi": ("prop = fmin(ORACLE_PI * ea, 2.0);", "prop = fmin(ea, 2.0);"),
+    "bound_trig_not_pi": ("const double k = rad ? 1.0 : ORACLE_PI;", "const double k = 1.0;"),
     "bound_add_no_rounding": ("e = prop + rnd32(v, prop, 1);", "e = prop;"),
     "log_protection_value": ("if (a < 0.0) return -1.0;", "if (a < 0.0) return 0.0;"),
     "pow_zero_zero_is_one": ("if (a == 0.0 && b == 0.0) return 0.0;", "if (a == 0.0 && b == 0.0) return 1.0;"),
@@ -43,7 +47,8 @@ MUTANTS = {
     "mod_truncated": ("if (r != 0.0 && ((r < 0.0) != (b < 0.0))) r += b;", ""),
     "clip_bounds_swapped": ("case O_CLIP: return fmax(fmin(c, a), b);", "case O_CLIP: return fmax(fmin(b, a), c);"),
     "if_branches_swapped": ("case O_IF: return a != 0.0 ? b : c;", "case O_IF: return a != 0.0 ? c : b;"),
-    "tan_not_pi_scaled": ("case O_TAN: return oracle_sinpi(a) / oracle_cospi(a);", "case O_TAN: return tan(a);"),
+    "tan_not_pi_scaled": ("case O_TAN: return rad ? tan(a) : oracle_sinpi(a) / oracle_cospi(a);",
+                          "case O_TAN: return tan(a);"),
     "frac_truncates": ("case O_FRAC: return a - floor(a);", "case O_FRAC: return a - trunc(a);"),
     "mdist_not_halved": ("case O_MDIST: return (a + b) / 2.0;", "case O_MDIST: return a + b;"),
     "sign_of_zero_is_one": ("if (a == 0.0) return 0.0;\n    return a;", "if (a == 0.0) return 1.0;\n    return a;"),

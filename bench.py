@@ -423,10 +423,10 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
     out = {}
     rows = {}
     for arm, b, mc in (("cache", budget, 0), ("cache_min_cost_8", budget, 8), ("no_cache", 0, 0),
-                       ("library_variation", budget, 0)):
+                       ("library_variation", budget, 0), ("library_variation_no_cache", 0, 0)):
         ctx = ctx_cls(device=dev.index, cache_budget_bytes=b, cache_min_cost=mc)
         dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
-        if arm == "library_variation":
+        if arm.startswith("library_variation"):
             ev = DeviceEvolution(ctx, dom, pop_size=50, generations=generations, seed=3)
         else:
             ev = Evolution(gpu_fitness(ctx, dom), pop_size=50, generations=generations, seed=3)
@@ -446,11 +446,13 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
         if b:
             out[arm].update({k: int(st[k]) for k in ("cache_hits", "cache_inserts", "cache_evictions",
                                                        "cache_entries", "cache_bytes", "cache_reserved")})
-        if arm == "library_variation":
+        if arm.startswith("library_variation"):
             ev.close()
         ctx.close()
     same = all(np.array_equal(a.view(np.int64), c.view(np.int64))
-               for arm in ("cache", "cache_min_cost_8") for a, c in zip(rows[arm], rows["no_cache"]))
+               for arm, ref in (("cache", "no_cache"), ("cache_min_cost_8", "no_cache"),
+                                ("library_variation", "library_variation_no_cache"))
+               for a, c in zip(rows[arm], rows[ref]))
     out.update({"workload": "evolution: population 50, 50 generations, 4096x4096 grid, 20 GB cache budget, seed 3",
                 "unit": UNIT, "cached_equals_uncached_bitwise": bool(same),
                 "cache_speedup": out["no_cache"]["fitness_seconds"] / out["cache"]["fitness_seconds"],

@@ -236,9 +236,10 @@ TuneKey tune_key(const PopIR& ir, int64_t N) {
     return TuneKey{N, log2_bucket((int64_t)ir.roots.size()), log2_bucket(ir.tree_nodes)};
 }
 
-PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int K, int items_per_sm) {
+PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W, int K, int items_per_sm) {
     PlanShape s;
     s.N = N;
+    s.W = W;
     s.K = K;
     s.threads = 128;
     s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
@@ -250,13 +251,15 @@ PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int K, int items_per
     return s;
 }
 
-PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N) {
+// W: the grid's row length (0: one row of N points).
+PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W) {
     PlanShape s = default_shape(ir, N, c->sms);
+    s.W = W;
     s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
     bool forced = c->cfg.points_per_thread > 0 || c->cfg.threads_per_block > 0 || c->cfg.n_groups > 0;
     if (!forced) {
         auto it = c->tuned.find(tune_key(ir, N));
-        if (it != c->tuned.end()) return shape_for(c, ir, N, it->second.K, it->second.items_per_sm);
+        if (it != c->tuned.end()) return shape_for(c, ir, N, W, it->second.K, it->second.items_per_sm);
     }
     if (c->cfg.points_per_thread > 0) s.K = c->cfg.points_per_thread;
     if (c->cfg.threads_per_block > 0) s.threads = c->cfg.threads_per_block;
@@ -579,8 +582,8 @@ int fence_call(std::vector<CacheEntry*>& read, std::vector<CacheEntry*>& written
 }
 
 // The plan of `pop` for a grid of N points (configured, tuned or default shape).
-int get_plan(tgp_ctx* c, Population* pop, int64_t N, bool pheno, cudaStream_t s, Plan** out) {
-    return get_plan_shape(c, pop, choose_shape(c, pop->ir, N), pheno, s, out);
+int get_plan(tgp_ctx* c, Population* pop, const Domain* d, bool pheno, cudaStream_t s, Plan** out) {
+    return get_plan_shape(c, pop, choose_shape(c, pop->ir, d->N(), d->W), pheno, s, out);
 }
 
 // Entries a cached-mode call reads and writes (fenced after its launches).
@@ -593,13 +596,13 @@ struct CallCache {
 int get_call_plan(tgp_ctx* c, Population* pop, Domain* d, bool pheno, cudaStream_t s, Plan** out, CallCache& cc) {
     cc.read.clear();
     cc.written.clear();
-    if (!cache_on(c) || pop->gid.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
+    if (!cache_on(c) || pop->gid.empty()) return get_plan(c, pop, d, pheno, s, out);
     CacheView cv;
     std::vector<float*> table;
     int rc = prepare_cache(c, pop, d, s, cv, table, cc.read, cc.written);
     if (rc) return rc;
-    if (table.empty()) return get_plan(c, pop, d->N(), pheno, s, out);
-    return get_plan_shape(c, pop, choose_shape(c, pop->ir, d->N()), pheno, s, out, &cv, &table);
+    if (table.empty()) return get_plan(c, pop, d, pheno, s, out);
+    return get_plan_shape(c, pop, choose_shape(c, pop->ir, d->N(), d->W), pheno, s, out, &cv, &table);
 }
 
 // After the launches of a call in cached mode: fences its cache entries, and
@@ -616,6 +619,10 @@ int finish_call(Plan* pl, CallCache& cc, cudaStream_t s) {
 
 int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, cudaStream_t s) {
     const HostPlan& hp = pl->hp;
+    // the plan's work units cover the grid only for the row length it was built for
+    if (hp.shape.N != d->N() || hp.shape.W != d->W)
+        return fail(TGP_E_INVALID, "plan for %lld points in rows of %lld used on a %d x %d grid",
+                    (long long)hp.shape.N, (long long)hp.shape.W, d->W, d->H);
     EvalParams p{};
     p.code = pl->code.p;
     p.group_off = pl->group_off.p;
@@ -744,7 +751,7 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->W = d->W; v->H = d->H;
     v->xlo = d->xlo; v->xhi = d->xhi; v->ylo = d->ylo; v->yhi = d->yhi;
     v->target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
-    v->shape = choose_shape(ctx, p->ir, d->N());
+    v->shape = choose_shape(ctx, p->ir, d->N(), d->W);
     v->sms = ctx->sms;
     v->device = ctx->device;
     v->trig_radians = trig_radians(ctx);
@@ -787,7 +794,7 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
         if (prc) return fail(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "target tree: %s", err.c_str());
         CUDA_TRY(d->target.ensure((size_t)N));
         Plan* pl = nullptr;
-        rc = get_plan(ctx, tp.get(), N, true, s, &pl);
+        rc = get_plan(ctx, tp.get(), d.get(), true, s, &pl);
         if (rc) return rc;
         rc = launch_plan(ctx, pl, d.get(), true, d->target.p, s);
         if (rc) return rc;
@@ -827,11 +834,11 @@ int context_device(tgp_ctx* ctx, int* device) {
     return TGP_OK;
 }
 
-int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, std::shared_ptr<PrePlan>* out) {
+int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W, std::shared_ptr<PrePlan>* out) {
     auto pp = std::make_shared<PrePlan>();
     {
         std::lock_guard<std::mutex> g(ctx->mu);
-        pp->shape = choose_shape(ctx, ir, N);
+        pp->shape = choose_shape(ctx, ir, N, W);
     }
     build_plan(ir, pp->shape, pp->plan);
     *out = std::move(pp);
@@ -867,11 +874,10 @@ int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr
     return TGP_OK;
 }
 
-int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N) {
+int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W) {
     std::lock_guard<std::mutex> g(ctx->mu);
-    const PlanShape sh = choose_shape(ctx, ir, N);
-    const int64_t tile = (int64_t)sh.K * sh.threads;
-    const int64_t tiles = (N + tile - 1) / tile;
+    const PlanShape sh = choose_shape(ctx, ir, N, W);
+    const int64_t tiles = (plan_chunks(sh) + sh.threads - 1) / sh.threads;
     const int64_t T = (int64_t)ir.roots.size();
     const int64_t code = (ir.tree_nodes + 2 * (int64_t)sh.n_groups + 1) * (int64_t)sizeof(Ins);
     return T * tiles * (sh.threads / 32) * (int64_t)sizeof(float) + code + T * (int64_t)sizeof(double) +
@@ -1082,7 +1088,7 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
     if (it == p->graphs.end()) {
         // plan, allocation and upload happen before the capture
         Plan* pl = nullptr;
-        rc = get_plan(ctx, p, d->N(), false, s, &pl);
+        rc = get_plan(ctx, p, d, false, s, &pl);
         if (rc) return rc;
         CUDA_TRY(cudaStreamSynchronize(s));
         if (d->ready) {   // a capture cannot wait on work outside it
@@ -1138,7 +1144,7 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     for (int K : Ks) {
         if ((int64_t)K * 128 * 16 > N && K > 2) continue;   // tiles far larger than the grid
         for (int ips : items) {
-            PlanShape sh = shape_for(ctx, p->ir, N, K, ips);
+            PlanShape sh = shape_for(ctx, p->ir, N, d->W, K, ips);
             bool dup = false;
             for (const PlanShape& t : tried) dup |= !(t < sh) && !(sh < t);
             if (dup) continue;
@@ -1205,7 +1211,7 @@ int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points, int32_t* ins_
     Population* p = find(ctx->pops, pop);
     if (!p) return fail(TGP_E_INVALID, "unknown population handle");
     HostPlan hp;
-    build_plan(p->ir, choose_shape(ctx, p->ir, n_points), hp);
+    build_plan(p->ir, choose_shape(ctx, p->ir, n_points, 0), hp);
     if (n_ins) *n_ins = (int64_t)hp.ir.size();
     if (n_groups) *n_groups = hp.shape.n_groups;
     if (ins_out) {

@@ -798,8 +798,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     const int64_t T = (int64_t)pop.roots.size();
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>(shape.n_groups, std::max<int64_t>(T, 1)));
     plan.shape.n_groups = G;
-    int64_t tile = (int64_t)shape.K * shape.threads;
-    plan.n_tiles = (int)((shape.N + tile - 1) / tile);
+    plan.n_tiles = (int)((plan_chunks(shape) + shape.threads - 1) / shape.threads);
 
     // Tree order: trees that share a subtree are placed next to each other
     // (sorted by their most expensive subtree that another tree also uses),

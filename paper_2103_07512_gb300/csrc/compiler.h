@@ -64,6 +64,7 @@ void append_population(PopIR& dst, const PopIR& src);
 // Shape of one launch plan.
 struct PlanShape {
     int64_t N = 0;       // grid points
+    int64_t W = 0;       // grid width (row length); 0: the N points form one row
     int K = 8;           // points per thread
     int threads = 128;   // threads per CTA
     int n_groups = 1;    // tree groups
@@ -71,11 +72,20 @@ struct PlanShape {
     bool operator<(const PlanShape& o) const {
         if (dedup != o.dedup) return dedup < o.dedup;
         if (N != o.N) return N < o.N;
+        if (W != o.W) return W < o.W;
         if (K != o.K) return K < o.K;
         if (threads != o.threads) return threads < o.threads;
         return n_groups < o.n_groups;
     }
 };
+
+// Work units of a launch: every row of the grid is cut into ceil(W / K)
+// chunks of K consecutive points (the last one ragged); one thread per chunk.
+inline int64_t plan_chunks(const PlanShape& s) {
+    const int64_t w = s.W > 0 ? s.W : s.N;
+    const int64_t rows = w > 0 ? s.N / w : 0;
+    return rows * ((w + s.K - 1) / s.K);
+}
 
 struct HostPlan {
     PlanShape shape;

@@ -47,9 +47,10 @@ struct PrePlan {
     HostPlan plan;
 };
 
-// Builds the plan of `ir` on N points without holding the context lock (only
-// the shape choice takes it), so that callers may plan in their own threads.
-int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, std::shared_ptr<PrePlan>* out);
+// Builds the plan of `ir` on a grid of N points in rows of W without holding
+// the context lock (only the shape choice takes it), so that callers may plan
+// in their own threads.
+int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W, std::shared_ptr<PrePlan>* out);
 
 // Registers a population built on the host (e.g. several jobs' trees merged
 // with append_population) as if it had been compiled from tokens.  `pre`, if
@@ -61,9 +62,9 @@ int adopt_population(tgp_ctx* ctx, PopIR&& ir, tgp_handle* out, std::shared_ptr<
 // population's previous launches must have completed.
 int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr<PrePlan> pre = nullptr);
 
-// Device bytes one fitness launch of `ir` on N points needs beyond its
-// domain (partial sums, bytecode, results).
-int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N);
+// Device bytes one fitness launch of `ir` on N points in rows of W needs
+// beyond its domain (partial sums, bytecode, results).
+int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W);
 
 // Records the calling thread's error message; returns `code`.
 int set_error(int code, const char* fmt, ...);

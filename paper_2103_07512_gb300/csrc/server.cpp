@@ -482,10 +482,10 @@ int tgp_server_submit(tgp_server* srv, const tgp_job* job, int64_t* job_id) {
                                internal::context_simplifies(srv->ctx));
     if (prc) return internal::set_error(prc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     j->n_trees = job->n_trees;
-    j->est = internal::estimate_bytes(srv->ctx, j->ir, key.N());
+    j->est = internal::estimate_bytes(srv->ctx, j->ir, key.N(), key.W);
     // the bytecode is planned here, in the caller's thread, for a launch of
     // this job alone (a fused launch is planned again by the worker)
-    internal::preplan(srv->ctx, j->ir, key.N(), &j->plan);
+    internal::preplan(srv->ctx, j->ir, key.N(), key.W, &j->plan);
     j->dom_bytes = key.kind == TGP_TARGET_TOKENS ? key.N() * (int64_t)sizeof(float) : 0;
     if (j->est + j->dom_bytes > srv->cfg.hbm_budget_bytes)
         return internal::set_error(TGP_E_BUDGET, "job needs %lld bytes of device memory; the budget is %lld",

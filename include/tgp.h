@@ -146,7 +146,10 @@ typedef struct tgp_config {
     int32_t n_groups;            /* 0 = automatic; else trees are split into this many groups */
     int32_t cache_min_cost;      /* subtrees cheaper than this (per point, a binary32 add = 1) are
                                     never stored in the cache; 0 = 48 */
-    int32_t reserved[4];
+    int32_t plan_threads;        /* host threads that plan a population's tree groups
+                                    concurrently (the calling thread included); 0 = up to 8,
+                                    1 = serial.  The bytecode does not depend on it. */
+    int32_t reserved[3];
 } tgp_config;
 
 /* A target given as one expression tree (TGP_TARGET_TOKENS). */

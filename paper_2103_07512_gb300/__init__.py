@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
                 ("cache_budget_bytes", ctypes.c_int64),
                 ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("n_groups", ctypes.c_int32), ("cache_min_cost", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("plan_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TargetTokens(ctypes.Structure):
@@ -182,7 +182,7 @@ class Context:
 
     def __init__(self, device=0, host_only=False, cache_budget_bytes=0, points_per_thread=0,
                  threads_per_block=0, n_groups=0, dedup=True, time_kernels=False, cache_min_cost=0,
-                 simplify=True, trig="pi"):
+                 simplify=True, trig="pi", plan_threads=0):
         """trig: "pi" (sin(a) = sin(pi a), Sec. 3.2) or "rad" (radians, the
         footnote of Table 1), for sin, cos and tan."""
         if trig not in ("pi", "rad"):
@@ -198,6 +198,7 @@ class Context:
         cfg.threads_per_block = threads_per_block
         cfg.n_groups = n_groups
         cfg.cache_min_cost = cache_min_cost
+        cfg.plan_threads = plan_threads
         h = ctypes.c_void_p()
         self._h = None
         self._check(self._L.tgp_create(ctypes.byref(h), ctypes.byref(cfg)))

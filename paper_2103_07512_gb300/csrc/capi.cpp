@@ -21,6 +21,7 @@
 #include "compiler.h"
 #include "internal.h"
 #include "kernels.h"
+#include "pool.h"
 
 using namespace tgp;
 
@@ -196,6 +197,9 @@ struct tgp_ctx {
     bool capturing = false;                                  // inside tgp_fitness_graph capture
     // TGP_F_TIME_KERNELS: event pairs around interpreter launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+    // host threads that plan a population's tree groups concurrently
+    std::unique_ptr<tgp::WorkerPool> pool;
+    tgp::ParallelFor par;
     ~tgp_ctx() {
         for (auto& e : ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         for (auto& e : ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -347,7 +351,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         const bool pre = !cached && pop->preplanned && !(pop->preplanned->shape < shape) &&
                          !(shape < pop->preplanned->shape);
         if (pre) pl->hp = std::move(pop->preplanned->plan);
-        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr);
+        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr, &c->par);
         pop->preplanned.reset();
         if (cached) {
             pl->view = *cv;
@@ -360,7 +364,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         if (cached) {
             // the bytecode depends only on the view; entry pointers may differ
             if (pl->view.cached != cv->cached || pl->view.insert != cv->insert) {
-                build_plan(pop->ir, shape, pl->hp, cv);
+                build_plan(pop->ir, shape, pl->hp, cv, &c->par);
                 pl->view = *cv;
             }
             pl->h_table = *table;
@@ -755,6 +759,7 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->sms = ctx->sms;
     v->device = ctx->device;
     v->trig_radians = trig_radians(ctx);
+    v->par = &ctx->par;
     return TGP_OK;
 }
 
@@ -840,7 +845,7 @@ int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W, std::shared_ptr
         std::lock_guard<std::mutex> g(ctx->mu);
         pp->shape = choose_shape(ctx, ir, N, W);
     }
-    build_plan(ir, pp->shape, pp->plan);
+    build_plan(ir, pp->shape, pp->plan, nullptr, &ctx->par);
     *out = std::move(pp);
     return TGP_OK;
 }
@@ -905,6 +910,15 @@ int tgp_create(tgp_ctx** out, const tgp_config* cfg) {
     std::unique_ptr<tgp_ctx> c(new (std::nothrow) tgp_ctx());
     if (!c) return fail(TGP_E_NOMEM, "out of host memory");
     if (cfg) c->cfg = *cfg;
+    {
+        // planning workers besides the calling thread
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int want = c->cfg.plan_threads > 0 ? c->cfg.plan_threads : 8;
+        const int workers = (int)std::min<unsigned>((unsigned)(want - 1), hw > 1 ? hw - 1 : 0);
+        c->pool = std::make_unique<WorkerPool>(workers);
+        WorkerPool* pool = c->pool.get();
+        c->par = [pool](int n, const std::function<void(int)>& body) { pool->run(n, body); };
+    }
     constexpr int32_t kKnownFlags =
         TGP_F_HOST_ONLY | TGP_F_NO_DEDUP | TGP_F_TIME_KERNELS | TGP_F_NO_SIMPLIFY | TGP_F_TRIG_RADIANS;
     if (c->cfg.flags & ~kKnownFlags) return fail(TGP_E_INVALID, "unknown flag bits 0x%x", c->cfg.flags & ~kKnownFlags);
@@ -1211,7 +1225,7 @@ int tgp_debug_plan(tgp_ctx* ctx, tgp_handle pop, int64_t n_points, int32_t* ins_
     Population* p = find(ctx->pops, pop);
     if (!p) return fail(TGP_E_INVALID, "unknown population handle");
     HostPlan hp;
-    build_plan(p->ir, choose_shape(ctx, p->ir, n_points, 0), hp);
+    build_plan(p->ir, choose_shape(ctx, p->ir, n_points, 0), hp, nullptr, &ctx->par);
     if (n_ins) *n_ins = (int64_t)hp.ir.size();
     if (n_groups) *n_groups = hp.shape.n_groups;
     if (ins_out) {

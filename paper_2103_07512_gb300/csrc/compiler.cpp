@@ -71,6 +71,21 @@ void Dag::rehash(size_t cap) {
     }
 }
 
+void Dag::reserve(size_t n) {
+    nodes.reserve(n);
+    size_t cap = 1024;
+    while (cap < 2 * n + 2) cap *= 2;
+    if (cap > table_.size()) rehash(cap);
+}
+
+void Dag::assign_nodes(std::vector<DagNode>&& v) {
+    nodes = std::move(v);
+    used_ = nodes.size();
+    size_t cap = 1024;
+    while (cap < 2 * used_ + 2) cap *= 2;
+    rehash(cap);
+}
+
 int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     if (table_.empty()) rehash(1024);
     size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
@@ -265,17 +280,23 @@ void compact(PopIR& pop) {
         if (live[i])
             for (int c = 0; c < kMaxKids; ++c)
                 if (pop.dag.nodes[i].kid[c] >= 0) live[pop.dag.nodes[i].kid[c]] = 1;
-    if (std::all_of(live.begin(), live.end(), [](uint8_t v) { return v != 0; })) return;
-    Dag d;
+    const size_t n_live = (size_t)std::count(live.begin(), live.end(), (uint8_t)1);
+    if (n_live == n) return;
+    // the live nodes keep their keys (operands renumbered) and their derived
+    // fields, which depend on the operands' only
+    std::vector<DagNode> kept;
+    kept.reserve(n_live);
     std::vector<int32_t> id(n, -1);
     for (size_t i = 0; i < n; ++i) {
         if (!live[i]) continue;
-        const DagNode& x = pop.dag.nodes[i];
-        id[i] = d.intern(x.op, x.kid[0] >= 0 ? id[x.kid[0]] : -1, x.kid[1] >= 0 ? id[x.kid[1]] : -1, x.imm,
-                         x.kid[2] >= 0 ? id[x.kid[2]] : -1);
+        DagNode x = pop.dag.nodes[i];
+        for (int c = 0; c < kMaxKids; ++c)
+            if (x.kid[c] >= 0) x.kid[c] = id[x.kid[c]];
+        id[i] = (int32_t)kept.size();
+        kept.push_back(x);
     }
     for (auto& r : pop.roots) r = id[r];
-    pop.dag = std::move(d);
+    pop.dag.assign_nodes(std::move(kept));
 }
 
 void append_population(PopIR& dst, const PopIR& src) {
@@ -308,6 +329,8 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
     std::vector<int32_t> stack;
     std::vector<int32_t> dstack;   // depth of each stacked subtree as given (before simplification)
     int64_t imm_pos = 0;
+    if (n_trees > 0 && tree_off[n_trees] > 0 && tree_off[n_trees] < (int64_t)1 << 26)
+        out.dag.reserve((size_t)tree_off[n_trees]);   // at most one node per token (two for clip)
     for (int32_t t = 0; t < n_trees; ++t) {
         int64_t b = tree_off[t], e = tree_off[t + 1];
         int64_t n = e - b;
@@ -792,7 +815,32 @@ std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv) {
     return out;
 }
 
-void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv) {
+// One group's bytecode (appended to gen's output), with the kept-slot cap
+// that the group's temporaries leave of `budget`.  Returns the slots used.
+static int plan_group(GroupGen& gen, std::vector<IrIns>& ir, const PopIR& pop, const std::vector<int32_t>& trees,
+                      int budget) {
+    // kept nodes get what the group's temporaries leave of the budget (a
+    // tree's evaluation parks up to its Sethi-Ullman number of values)
+    int su = 0;
+    for (int32_t t : trees) su = std::max(su, pop.dag.nodes[pop.roots[t]].su);
+    gen.set_kept_cap(std::max(2, budget - su));
+    // A kept node that found no slot under the cap is demoted to
+    // re-evaluation and the group is planned again.  Demotion only
+    // shrinks the kept set, so this terminates.
+    std::vector<int32_t> forbid;
+    const size_t mark = ir.size();
+    for (int iter = 0;; ++iter) {
+        gen.run(trees, pop.roots, forbid);
+        if (gen.refused.empty() || iter >= 32) break;
+        forbid.insert(forbid.end(), gen.refused.begin(), gen.refused.end());
+        gen.rollback();
+        ir.resize(mark);
+    }
+    return gen.slot_high;
+}
+
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
+                const ParallelFor* par) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -862,29 +910,28 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     // Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
     const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
-    GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv);
     plan.group_off.push_back(0);
-    std::vector<int32_t> forbid;
-    for (int g = 0; g < G; ++g) {
-        // kept nodes get what the group's temporaries leave of the budget (a
-        // tree's evaluation parks up to its Sethi-Ullman number of values)
-        int su = 0;
-        for (int32_t t : groups[g]) su = std::max(su, pop.dag.nodes[pop.roots[t]].su);
-        gen.set_kept_cap(std::max(2, budget - su));
-        // A kept node that found no slot under the cap is demoted to
-        // re-evaluation and the group is planned again.  Demotion only
-        // shrinks the kept set, so this terminates.
-        forbid.clear();
-        const size_t mark = plan.ir.size();
-        for (int iter = 0;; ++iter) {
-            gen.run(groups[g], pop.roots, forbid);
-            if (gen.refused.empty() || iter >= 32) break;
-            forbid.insert(forbid.end(), gen.refused.begin(), gen.refused.end());
-            gen.rollback();
-            plan.ir.resize(mark);
+    if (par && *par && G > 1 && !(cv && cv->active())) {
+        std::vector<std::vector<IrIns>> part(G);
+        std::vector<int> slots(G, 0);
+        (*par)(G, [&](int g) {
+            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr);
+            slots[g] = plan_group(gen, part[g], pop, groups[g], budget);
+        });
+        size_t total_ins = 0;
+        for (const auto& v : part) total_ins += v.size();
+        plan.ir.reserve(total_ins);
+        for (int g = 0; g < G; ++g) {
+            plan.ir.insert(plan.ir.end(), part[g].begin(), part[g].end());
+            plan.n_slots = std::max(plan.n_slots, slots[g]);
+            plan.group_off.push_back((int64_t)plan.ir.size());
         }
-        plan.n_slots = std::max(plan.n_slots, gen.slot_high);
-        plan.group_off.push_back((int64_t)plan.ir.size());
+    } else {
+        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv);
+        for (int g = 0; g < G; ++g) {
+            plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
+            plan.group_off.push_back((int64_t)plan.ir.size());
+        }
     }
     plan.group_order.resize(G);
     std::iota(plan.group_order.begin(), plan.group_order.end(), 0);

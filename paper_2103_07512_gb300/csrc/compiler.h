@@ -2,6 +2,7 @@
 // hash-consing into the population DAG, and bytecode generation.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,11 @@ public:
     std::vector<DagNode> nodes;
     int32_t intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2 = -1);
     size_t size() const { return nodes.size(); }
+    // Room for n nodes without growing the node array or the hash table.
+    void reserve(size_t n);
+    // Takes `v` as the node array (distinct keys, operands before their
+    // users) and rebuilds the hash index over it.
+    void assign_nodes(std::vector<DagNode>&& v);
 
 private:
     std::vector<int32_t> table_;   // open addressing, -1 = empty
@@ -122,7 +128,16 @@ struct CacheView {
 std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv);
 
 // Partitions the trees into shape.n_groups groups and emits their bytecode.
-void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr);
+// Runs body(i) for every i in [0, n), possibly concurrently, and returns
+// when all calls have returned.
+using ParallelFor = std::function<void(int n, const std::function<void(int)>& body)>;
+
+// With `par`, the tree groups are planned concurrently (each group's plan
+// depends on its own trees only, so the result is the same); a cache view
+// keeps the planning serial (a node is stored by the first group that
+// evaluates it).
+void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr,
+                const ParallelFor* par = nullptr);
 
 Ins encode(const IrIns& in);
 

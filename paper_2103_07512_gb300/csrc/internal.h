@@ -20,6 +20,7 @@ struct View {
     int sms = 0;
     int device = 0;
     bool trig_radians = false;       // TGP_F_TRIG_RADIANS
+    const ParallelFor* par = nullptr;   // the context's planning workers
 };
 
 // Locks the context into `lk`, makes its device current and fills `v`.

@@ -72,7 +72,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
 
     // host-side plan (host memory only)
     HostPlan hp;
-    build_plan(*v.ir, v.shape, hp);
+    build_plan(*v.ir, v.shape, hp, nullptr, v.par);
     const int warps = hp.shape.threads / 32;
     const size_t n_partial = (size_t)T * hp.n_tiles * warps;
     const size_t off_counter = 0;

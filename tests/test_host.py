@@ -489,3 +489,21 @@ def test_unknown_context_flags_and_trig_mode_are_refused():
         tgp.Context(host_only=True, trig="degrees")
     with tgp.Context(host_only=True, trig="rad") as c:
         c.compile_tokens(I.to_tokens([I.parse_string("sin(x)")]))
+
+
+@pytest.mark.parametrize("name", ["small", "at_scale", "batched"])
+def test_concurrent_group_planning_gives_the_serial_bytecode(name):
+    """Tree groups planned on the context's worker threads (the default) give
+    the bytecode of serial planning (plan_threads = 1), group by group."""
+    if name == "small":
+        tok, g = I.small_population()
+    elif name == "at_scale":
+        tok, g = I.population_at_scale()
+    else:
+        tok, g = I.batched_uneven()[:2]
+    with tgp.Context(host_only=True, plan_threads=1) as a, tgp.Context(host_only=True) as b:
+        for n_points in (g.N, 4096, 1):
+            ia, oa = a.debug_plan(a.compile_tokens(tok), n_points)
+            ib, ob = b.debug_plan(b.compile_tokens(tok), n_points)
+            assert np.array_equal(oa, ob) and np.array_equal(ia, ib)
+            assert len(oa) > 2 or n_points == 1

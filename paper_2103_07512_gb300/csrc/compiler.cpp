@@ -420,7 +420,7 @@ public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
           first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
-          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0) {}
+          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0) {}
 
     int slot_high = 0;                    // slots used by the last run
     void set_kept_cap(int c) { kept_cap_ = c; }
@@ -475,6 +475,7 @@ private:
     std::vector<int32_t> stored_log_;   // stores of the current group attempt
     std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
+    std::vector<uint8_t> mark_;    // scratch of sort_touched_descending, all zero between calls
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
     bool is_cached(int32_t n) const { return cv_ && cv_->cached[n] >= 0; }
@@ -530,8 +531,7 @@ private:
                 }
             }
         }
-        std::sort(touched_.begin(), touched_.end(), [](int32_t a, int32_t b) { return a > b; });
-        touched_.erase(std::unique(touched_.begin(), touched_.end()), touched_.end());
+        sort_touched_descending();
         for (int32_t n : touched_) where_[n] = -1;
         for (int32_t n : forbid) where_[n] = -3;   // mark: never keep (reset below)
         // uses_ holds the root counts so far; push evaluations down
@@ -549,6 +549,23 @@ private:
         for (int32_t n : forbid) where_[n] = -1;
         for (int32_t n : span_touched_) { first_pos_[n] = -1; last_pos_[n] = -1; }
         span_touched_.clear();
+    }
+
+    // touched_ in descending id order without repeats (parents before their
+    // operands): a scan of the id range when it is short, else a sort
+    void sort_touched_descending() {
+        if (touched_.empty()) return;
+        int32_t lo = touched_[0], hi = touched_[0];
+        for (int32_t n : touched_) { lo = std::min(lo, n); hi = std::max(hi, n); }
+        if ((int64_t)(hi - lo) <= 16 * (int64_t)touched_.size() + 64) {
+            for (int32_t n : touched_) mark_[n] = 1;
+            touched_.clear();
+            for (int32_t n = hi; n >= lo; --n)
+                if (mark_[n]) { mark_[n] = 0; touched_.push_back(n); }
+        } else {
+            std::sort(touched_.begin(), touched_.end(), [](int32_t a, int32_t b) { return a > b; });
+            touched_.erase(std::unique(touched_.begin(), touched_.end()), touched_.end());
+        }
     }
 
     // operand kind of a leaf (and its immediate)
@@ -851,9 +868,12 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     // Tree order: trees that share a subtree are placed next to each other
     // (sorted by their most expensive subtree that another tree also uses),
     // then the order is cut into G contiguous groups of balanced cost.
+    // distinct internal nodes of each tree (flat, tree t at [tree_at[t], tree_at[t+1]))
     std::vector<int32_t> tree_uses(pop.dag.size(), 0), seen(pop.dag.size(), -1);
-    std::vector<int32_t> stack;
+    std::vector<int32_t> stack, tree_nodes, tree_at(T + 1, 0);
+    tree_nodes.reserve((size_t)std::min<int64_t>(pop.tree_nodes, (int64_t)1 << 26));
     for (int64_t t = 0; t < T; ++t) {
+        tree_at[t] = (int32_t)tree_nodes.size();
         stack.assign(1, pop.roots[t]);
         while (!stack.empty()) {
             int32_t n = stack.back();
@@ -861,24 +881,19 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
             seen[n] = (int32_t)t;
             tree_uses[n]++;
+            tree_nodes.push_back(n);
             for (int c = 0; c < kMaxKids; ++c)
                 if (pop.dag.nodes[n].kid[c] >= 0) stack.push_back(pop.dag.nodes[n].kid[c]);
         }
     }
+    tree_at[T] = (int32_t)tree_nodes.size();
     std::vector<int32_t> key(T, -1);
     std::vector<float> key_cost(T, 0.f);
-    std::fill(seen.begin(), seen.end(), -1);
     for (int64_t t = 0; t < T; ++t) {
-        stack.assign(1, pop.roots[t]);
-        while (!stack.empty()) {
-            int32_t n = stack.back();
-            stack.pop_back();
-            const DagNode& d = pop.dag.nodes[n];
-            if (seen[n] == (int32_t)t || is_leaf(d.op)) continue;
-            seen[n] = (int32_t)t;
-            if (tree_uses[n] >= 2 && d.cost > key_cost[t]) { key_cost[t] = d.cost; key[t] = n; }
-            for (int c = 0; c < kMaxKids; ++c)
-                if (d.kid[c] >= 0) stack.push_back(d.kid[c]);
+        for (int32_t i = tree_at[t]; i < tree_at[t + 1]; ++i) {
+            const int32_t n = tree_nodes[i];
+            const float c = pop.dag.nodes[n].cost;
+            if (tree_uses[n] >= 2 && c > key_cost[t]) { key_cost[t] = c; key[t] = n; }
         }
     }
     std::vector<int32_t> order(T);

@@ -262,17 +262,20 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 20))
     h2d = d2h = 0
     e2e_times = []
+    compile_times = []
     for i in range(e2e_steps + 1):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = ctx.compile_population(tok.ops, tok.imm, tok.tree_off, tok.order)
+        tc = time.perf_counter()
         fit = ctx.fitness(p2, dom, T, blocking=True)
         t1 = time.perf_counter()
         s = ctx.stats()
         ctx.release_population(p2)
         if i > 0:                                          # first one warms the allocator
             e2e_times.append(t1 - t0)
+            compile_times.append(tc - t0)
         h2d = (s["code_instrs"] + 1) * 8 + (s["n_groups"] + 1) * 8 + s["n_groups"] * 4
         d2h = 8 * T
     e2e_s, e2e_value = replica_throughput(float(np.mean(e2e_times)), units, world, dist, dev)
@@ -327,7 +330,8 @@ def run_ours(args):
                          "sample": f"{cpu_info['rows']} of {g.H} rows ({cpu_info['points']} points), all trees, "
                                    f"{cpu_info['seconds']:.1f} s"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": e2e_s * 1e3},
+                "ms_per_step": e2e_s * 1e3, "compile_ms": 1e3 * float(np.mean(compile_times)),
+                "fitness_call_ms": 1e3 * (float(np.mean(e2e_times)) - float(np.mean(compile_times)))},
         "perop_baseline": {"value": perop_value, "unit": UNIT, "ms_per_step": perop_ms,
                            "speedup": value / perop_value, "fitness_agreement": perop_agree,
                            "launches_per_step": per.launches // 5},

@@ -54,10 +54,12 @@ static inline uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// Node ids do not depend on the hash (they are creation order); the key
+// comparison on a hit is exact, so only the probe length depends on it.
 static inline uint64_t key_hash(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
-    uint64_t a = ((uint64_t)(uint32_t)k0 << 32) | (uint32_t)k1;
-    uint64_t b = ((uint64_t)(uint32_t)op << 32) | imm;
-    return mix64(a ^ mix64(b ^ mix64((uint64_t)(uint32_t)k2)));
+    const uint64_t a = ((uint64_t)(uint32_t)k0 << 32) | (uint32_t)k1;
+    const uint64_t b = ((uint64_t)(uint32_t)op << 32) | imm;
+    return mix64(a * 0x9e3779b97f4a7c15ull ^ b ^ (uint64_t)(uint32_t)k2 * 0xc2b2ae3d27d4eb4full);
 }
 
 void Dag::rehash(size_t cap) {

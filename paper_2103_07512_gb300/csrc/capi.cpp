@@ -302,13 +302,13 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     const HostPlan& hp = pl->hp;
     const int warps = hp.shape.threads / 32;
     CUDA_TRY(pl->code.ensure(hp.code.size()));
-    CUDA_TRY(pl->group_off.ensure(hp.group_off.size()));
+    CUDA_TRY(pl->group_off.ensure(hp.code_off.size()));
     CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
     CUDA_TRY(pl->counter.ensure(1));
     CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
+    CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s));

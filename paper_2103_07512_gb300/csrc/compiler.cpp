@@ -957,10 +957,33 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     plan.n_items = (int64_t)G * plan.n_tiles;
     plan.code.reserve(plan.ir.size() + 1);
     for (const IrIns& in : plan.ir) {
-        plan.code.push_back(encode(in));
         // the interpreter variant with the rest of Table 1 is needed
         const bool form_fn = in.form == F_AO || in.form == F_OA || in.form == F_TT || in.form == F_UA || in.form == F_UT;
         if (in.form == F_SEL || (form_fn && in.fn >= T_TAN)) plan.ext = true;
+    }
+    // a store followed by the start of a new subexpression is one word
+    plan.code_off.assign(1, 0);
+    for (int g = 0; g < G; ++g) {
+        for (int64_t i = plan.group_off[g]; i < plan.group_off[g + 1]; ++i) {
+            const IrIns& in = plan.ir[i];
+            if (in.form == F_ST && i + 1 < plan.group_off[g + 1] && in.aux >= 0 && in.aux < (1 << 15)) {
+                const IrIns& nx = plan.ir[i + 1];
+                int fused = -1;
+                if (nx.form == F_TT && bin_index(nx.fn) >= 0 && bin_index(nx.fn) < kNHotBin)
+                    fused = OPC_STT + bin_index(nx.fn) * 9 + nx.o1 * 3 + nx.o2;
+                else if (nx.form == F_UT && un_index(nx.fn) >= 0 && un_index(nx.fn) < kNHotUn)
+                    fused = OPC_SUT + un_index(nx.fn) * 3 + nx.o1;
+                if (fused >= 0) {
+                    Ins e = encode(nx);
+                    e.x = (uint32_t)fused | ((uint32_t)in.aux << kStoreSlotShift);
+                    plan.code.push_back(e);
+                    ++i;
+                    continue;
+                }
+            }
+            plan.code.push_back(encode(in));
+        }
+        plan.code_off.push_back((int64_t)plan.code.size());
     }
     plan.code.push_back(encode(IrIns{F_END, 0, 0, 0, 0, 0}));
 }

@@ -97,7 +97,8 @@ struct HostPlan {
     PlanShape shape;
     std::vector<IrIns> ir;              // decoded, all groups back to back
     std::vector<Ins> code;              // encoded, plus one trailing END
-    std::vector<int64_t> group_off;     // [n_groups + 1]
+    std::vector<int64_t> group_off;     // [n_groups + 1] offsets into ir
+    std::vector<int64_t> code_off;      // [n_groups + 1] offsets into code (fused pairs are one word)
     std::vector<int32_t> group_order;   // groups by descending estimated cost
     std::vector<double> group_cost;
     int n_slots = 0;                    // shared-memory value slots per thread

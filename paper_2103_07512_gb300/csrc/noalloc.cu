@@ -78,7 +78,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     const size_t off_counter = 0;
     const size_t off_code = align256(sizeof(int32_t));
     const size_t off_goff = off_code + align256(hp.code.size() * sizeof(Ins));
-    const size_t off_gord = off_goff + align256(hp.group_off.size() * sizeof(int64_t));
+    const size_t off_gord = off_goff + align256(hp.code_off.size() * sizeof(int64_t));
     const size_t off_part = off_gord + align256(hp.group_order.size() * sizeof(int32_t));
     const size_t need = off_part + n_partial * sizeof(float);
     if (need > (size_t)TGP_NOALLOC_SCRATCH_BYTES)
@@ -110,7 +110,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     // return once staged, so the host plan may go out of scope afterwards.
     NA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), s));
     NA_TRY(cudaMemcpyAsync(code, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
-    NA_TRY(cudaMemcpyAsync(goff, hp.group_off.data(), hp.group_off.size() * sizeof(int64_t),
+    NA_TRY(cudaMemcpyAsync(goff, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
                            cudaMemcpyHostToDevice, s));
     NA_TRY(cudaMemcpyAsync(gord, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s));

@@ -84,8 +84,23 @@ constexpr int OPC_CST = OPC_ROOT + 1;
 constexpr int OPC_CLD = OPC_CST + 1;
 constexpr int OPC_SEL = OPC_CLD + 1;
 constexpr int OPC_COUNT = OPC_SEL + 1;
+// Fused "store, then start a new subexpression": slot x >> 16 = A, then the
+// F_TT of one of the first kNHotBin binary functions (+ bin * 9 + o1 * 3 + o2)
+// or the F_UT of one of the first kNHotUn unary ones (+ un * 3 + o1).  A
+// subexpression that follows a store almost always starts from terminals.
+constexpr int kNHotBin = 6;    // add sub mul div min max
+constexpr int kNHotUn = 4;     // sin cos neg abs
+constexpr int OPC_STT = OPC_COUNT;
+constexpr int OPC_SUT = OPC_STT + kNHotBin * 9;
+constexpr int OPC_FUSED_END = OPC_SUT + kNHotUn * 3;
+// The dispatch takes the low byte of x; every one of its 256 entries is a
+// valid target (codes without a form leave the loop).
+constexpr int kDispatchMask = 255;
+constexpr int kStoreSlotShift = 16;
+static_assert(OPC_FUSED_END <= kDispatchMask + 1, "opcodes must fit the dispatch byte");
 
-// One encoded instruction: x = opcode, y = immediate bits, slot, or aux.
+// One encoded instruction: x = opcode (low byte; a fused store's slot in the
+// high half), y = immediate bits, slot, or aux.
 struct Ins {
     uint32_t x;
     uint32_t y;

@@ -177,6 +177,12 @@ bool plain(float f) { return f == 0.f || std::isnormal(f); }
 //   - neg(neg(a)) = a, abs(neg(a)) = abs(a), abs(abs(a)) = abs(a);
 //   - a * 1 = a, a / 1 = a, a / 0 = 0 (protected division), a + (-0) = a,
 //     a - (+0) = a, (-0) - a = neg(a), min(a, a) = max(a, a) = a;
+//   - negations absorbed by their consumer: a + neg(b) = a - b, neg(a) + b =
+//     b - a, a - neg(b) = a + b (IEEE subtraction is addition of the negated
+//     operand), neg(a) * neg(b) = a * b, neg(a) / neg(b) = a / b (zero
+//     denominator: 0 either way), neg(a) * c = a * (-c), neg(a) / c = a / (-c),
+//     c / neg(b) = (-c) / b for a constant c (the sign of a product or
+//     quotient is the exclusive or of the operands' signs);
 //   - operands of add, mul and mdist in a canonical order (commutative in
 //     IEEE arithmetic, signed zeros included), so a+b and b+a are one node;
 //   - folding of mdist, sqrt, sign, frac and mod (exact or correctly rounded
@@ -190,6 +196,9 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
     };
     float a = 0.f, b = 0.f;
     const bool ca = is_const(k0, &a), cb = is_const(k1, &b);
+    const auto is_neg = [&](int32_t k) { return k >= 0 && dag.nodes[k].op == T_NEG; };
+    const auto kid0 = [&](int32_t k) { return dag.nodes[k].kid[0]; };
+    const auto negated = [&](float v) { return dag.intern(T_CONST, -1, -1, as_bits(v) ^ 0x80000000u); };
     const int ar = arity(op);
     // if with a constant condition is its chosen operand (NaN cannot be a constant)
     if (op == T_IF && ca) return a != 0.f ? k1 : k2;
@@ -231,20 +240,29 @@ int32_t intern_simplified(Dag& dag, int op, int32_t k0, int32_t k1, uint32_t imm
     case T_MUL:
         if (cb && as_bits(b) == as_bits(1.f)) return k0;
         if (ca && as_bits(a) == as_bits(1.f)) return k1;
+        if (is_neg(k0) && is_neg(k1)) return intern_simplified(dag, T_MUL, kid0(k0), kid0(k1), 0);
+        if (cb && is_neg(k0)) return intern_simplified(dag, T_MUL, kid0(k0), negated(b), 0);
+        if (ca && is_neg(k1)) return intern_simplified(dag, T_MUL, negated(a), kid0(k1), 0);
         if (k1 < k0) std::swap(k0, k1);
         break;
     case T_DIV:
         if (cb && as_bits(b) == as_bits(1.f)) return k0;
         if (cb && b == 0.f) return dag.intern(T_CONST, -1, -1, as_bits(0.f));
+        if (is_neg(k0) && is_neg(k1)) return intern_simplified(dag, T_DIV, kid0(k0), kid0(k1), 0);
+        if (cb && is_neg(k0)) return intern_simplified(dag, T_DIV, kid0(k0), negated(b), 0);
+        if (ca && is_neg(k1)) return intern_simplified(dag, T_DIV, negated(a), kid0(k1), 0);
         break;
     case T_ADD:
         if (cb && as_bits(b) == as_bits(-0.f)) return k0;
         if (ca && as_bits(a) == as_bits(-0.f)) return k1;
+        if (is_neg(k1)) return intern_simplified(dag, T_SUB, k0, kid0(k1), 0);
+        if (is_neg(k0)) return intern_simplified(dag, T_SUB, k1, kid0(k0), 0);
         if (k1 < k0) std::swap(k0, k1);
         break;
     case T_SUB:
         if (cb && as_bits(b) == as_bits(0.f)) return k0;
         if (ca && as_bits(a) == as_bits(-0.f)) return intern_simplified(dag, T_NEG, k1, -1, 0);
+        if (is_neg(k1)) return intern_simplified(dag, T_ADD, k0, kid0(k1), 0);
         break;
     case T_MIN:
     case T_MAX:

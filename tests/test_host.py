@@ -369,6 +369,10 @@ def _nan_canonical_bits(a):
     ("add(x, -0.0)", "x"), ("sub(y, 0.0)", "y"), ("sub(-0.0, x)", "neg(x)"), ("min(x, x)", "x"),
     ("max(sin(y), sin(y))", "sin(y)"), ("add(0.5, 0.25)", "0.75"), ("mult(3.0, neg(0.5))", "-1.5"),
     ("div(1.0, 0.0)", "0.0"), ("abs(-2.0)", "2.0"), ("sub(1.0, 1.0)", "0.0"),
+    ("add(x, neg(y))", "sub(x, y)"), ("add(neg(x), y)", "sub(y, x)"), ("sub(x, neg(y))", "add(x, y)"),
+    ("mult(neg(x), neg(y))", "mult(x, y)"), ("div(neg(x), neg(y))", "div(x, y)"),
+    ("mult(neg(x), 2.0)", "mult(x, -2.0)"), ("div(neg(y), 4.0)", "div(y, -4.0)"),
+    ("div(3.0, neg(x))", "div(-3.0, x)"),
 ])
 def test_simplification_rewrites(ctx, expr, simplified):
     a = I.to_tokens([I.parse_string(expr)])
@@ -420,6 +424,28 @@ def test_simplified_bytecode_equals_oracle_on_raw_trees(ctx):
     # equal as binary32 values (NaN = NaN; a zero of either sign = 0: fmin/fmax of
     # two zeros may return either, and operand order differs between the plans)
     assert np.array_equal(got, v32, equal_nan=True)
+
+
+def test_absorbed_negations_keep_every_bit(ctx):
+    """Negation-heavy trees over add, sub, mult, div, neg and abs with signed
+    zeros among the constants: the simplified plan and the plan of the trees
+    as given, both run by the numpy interpreter, agree bit for bit (signed
+    zeros included; NaN canonical)."""
+    rng = np.random.default_rng(22)
+    funcs = (I.ADD, I.SUB, I.MUL, I.DIV, I.NEG, I.NEG, I.ABS)
+    trees = [_const_heavy_tree(rng, int(rng.integers(2, 7)), funcs) for _ in range(300)]
+    tok = I.to_tokens(trees)
+    W, H = 7, 3
+    xs = np.array([oracle.grid_point(W, H, -1, 1, -1, 1, p) for p in range(W * H)], np.float32)
+    with tgp.Context(host_only=True, simplify=False) as raw:
+        ins_r, off_r = raw.debug_plan(raw.compile_tokens(tok), W * H)
+        n_raw = raw.stats()["dag_internal"]
+    ins_s, off_s = ctx.debug_plan(ctx.compile_tokens(tok), W * H)
+    assert ctx.stats()["dag_internal"] < n_raw
+    with np.errstate(all="ignore"):
+        a = run_bytecode(ins_s, off_s, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
+        b = run_bytecode(ins_r, off_r, tok.n_trees, xs[:, 0].copy(), xs[:, 1].copy())
+    assert np.array_equal(_nan_canonical_bits(a), _nan_canonical_bits(b))
 
 
 # ---------------------------------------------------------------- the rest of Table 1

@@ -361,7 +361,9 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
  *     replaced by a grow tree of depth 0..mutation_depth over `functions`,
  *     terminals x, y and constants uniform in [const_lo, const_hi)), else a
  *     copy; an offspring deeper than max_depth (measured on the stored tree,
- *     clip being stored as max(min(z, x), y)) is replaced by its first parent.
+ *     clip being stored as max(min(z, x), y)), or larger than 2^24 tokens
+ *     once its shared subtrees are written out, is replaced by its first
+ *     parent.
  *
  * Zero fields take the defaults: tournament 3, p_crossover 0.9, p_mutation
  * 0.1, elitism 1, max_depth 12, mutation_depth 4 (a negative probability or

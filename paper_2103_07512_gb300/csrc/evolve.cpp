@@ -93,12 +93,18 @@ Site site_at(const Dag& dag, int32_t r, int64_t target) {
     return s;
 }
 
-// Number of nodes of the tree rooted at n (counting every occurrence).
+// Largest tree (in tokens, every occurrence of a shared subtree counted) an
+// offspring may have: the token limit of one tree in tgp_compile_population.
+constexpr int64_t kMaxTreeTokens = (int64_t)1 << 24;
+
+// Number of nodes of the tree rooted at n (counting every occurrence),
+// saturating above kMaxTreeTokens (shared subtrees can make it exponential
+// in the depth).
 int64_t tree_size(const Dag& dag, int32_t n, std::vector<int64_t>& memo) {
     if (memo[n] >= 0) return memo[n];
     int64_t t = 1;
     for (int c = 0; c < kMaxKids; ++c)
-        if (dag.nodes[n].kid[c] >= 0) t += tree_size(dag, dag.nodes[n].kid[c], memo);
+        if (dag.nodes[n].kid[c] >= 0) t = std::min(t + tree_size(dag, dag.nodes[n].kid[c], memo), kMaxTreeTokens + 1);
     memo[n] = t;
     return t;
 }
@@ -219,11 +225,13 @@ int tgp_evolve(tgp_ctx* ctx, tgp_handle pop, const double* rmse, const tgp_evolv
             const Site sa = site_at(dag, a, rng.below(size_of(a)));
             const Site sb = site_at(dag, b, rng.below(size_of(b)));
             if (sa.depth + dag.nodes[sb.node].depth <= max_depth) child = replace_at(dag, sa, sb.node, gs.simplify);
+            if (size_of(child) > kMaxTreeTokens) child = a;
         } else if (u < pc + pm) {
             const Site sa = site_at(dag, a, rng.below(size_of(a)));
             const int d = (int)rng.below(mdepth + 1);
             const int32_t sub = grow(dag, rng, gs, d, true);
             if (sa.depth + dag.nodes[sub].depth <= max_depth) child = replace_at(dag, sa, sub, gs.simplify);
+            if (size_of(child) > kMaxTreeTokens) child = a;
         }
         next.push_back(child);
     }

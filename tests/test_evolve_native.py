@@ -252,3 +252,24 @@ def test_all_non_finite_rmse_still_gives_a_generation():
         pop = c.compile_tokens(I.to_tokens(I.ramped_half_and_half(12, 2, 4, rng)))
         nxt = c.evolve(pop, np.full(12, math.inf), seed=3)
         assert c.population_tokens(nxt).n_trees == 12
+
+
+def test_offspring_stay_within_the_token_limit(raw):
+    """A tree whose written-out size doubles with every level (add(t, t),
+    23 levels: 2^24 - 1 tokens, 23 DAG nodes): crossover that would graft a
+    larger subtree deeper gives the parent instead, so every offspring stays
+    within the 2^24-token limit of one tree."""
+    seq = np.array([I.X], np.int32)
+    for _ in range(23):
+        seq = np.concatenate([np.array([I.ADD], np.int32), seq, seq])
+    ops = np.concatenate([seq, np.array([I.Y], np.int32)])
+    pop = raw.compile_population(ops, np.zeros(0, np.float32), np.array([0, seq.size, seq.size + 1], np.int64))
+    assert raw.stats()["dag_internal"] == 23
+    grew = 0
+    for seed in range(4):
+        tok = raw.population_tokens(raw.evolve(pop, np.array([0.0, 1.0]), seed=seed, p_crossover=1.0,
+                                               p_mutation=-1, elitism=-1, max_depth=64))
+        sizes = np.diff(tok.tree_off)
+        assert sizes.max() <= (1 << 24)
+        grew += int((sizes > 1).sum())
+    assert grew > 0

@@ -366,8 +366,8 @@ int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
  *     parent.
  *
  * Zero fields take the defaults: tournament 3, p_crossover 0.9, p_mutation
- * 0.1, elitism 1, max_depth 12, mutation_depth 4 (a negative probability or
- * elitism means none),
+ * 0.1, elitism 1, max_depth 12 (at most 1024), mutation_depth 4 (a negative
+ * probability or elitism means none),
  * functions {add, sub, mult, div, sin, cos, neg, abs, min, max}, constants in
  * [-1, 1).  The random stream is splitmix64 from `seed`: the same population,
  * RMSE values and configuration give the same next generation.  With the

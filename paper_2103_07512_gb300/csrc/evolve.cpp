@@ -168,6 +168,8 @@ int tgp_evolve(tgp_ctx* ctx, tgp_handle pop, const double* rmse, const tgp_evolv
     const double pm = cfg.p_mutation > 0 ? cfg.p_mutation : cfg.p_mutation < 0 ? 0.0 : 0.1;
     const int elit = cfg.elitism > 0 ? cfg.elitism : cfg.elitism < 0 ? 0 : 1;
     const int max_depth = cfg.max_depth > 0 ? cfg.max_depth : 12;
+    if (max_depth > 1024)   // the depth limit of tgp_compile_population
+        return internal::set_error(TGP_E_INVALID, "max_depth %d exceeds 1024", max_depth);
     const int mdepth = cfg.mutation_depth > 0 ? cfg.mutation_depth : 4;
     GrowSpec gs;
     if (cfg.functions && cfg.n_functions > 0) {

@@ -243,6 +243,8 @@ def test_invalid_arguments():
         with pytest.raises(tgp.TgpError):
             c.evolve(pop + 999, [1.0], seed=0)
         with pytest.raises(tgp.TgpError):
+            c.evolve(pop, [1.0], seed=0, max_depth=1025)
+        with pytest.raises(tgp.TgpError):
             c.population_tokens(pop + 999)
 
 

@@ -300,7 +300,7 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
 
 /*
  * Autotuner: times candidate launch shapes (points per thread K in {2,4,8,16},
- * tree groups for ~16/64/256 work items per SM) on this population and
+ * tree groups for ~16/64/256/512 work items per SM) on this population and
  * domain, with CUDA events on `stream` (synchronous), and records the fastest
  * for the (grid size, tree-count bucket, node-count bucket) of the
  * population.  Later plans of any population in the same bucket use it

@@ -1152,7 +1152,7 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     PlanShape best_shape{};
     std::vector<PlanShape> tried;
     const int Ks[] = {2, 4, 8, 16};
-    const int items[] = {16, 64, 256};
+    const int items[] = {16, 64, 256, 512};
     const bool was_capturing = ctx->capturing;
     ctx->capturing = true;   // no per-launch timing events while tuning
     for (int K : Ks) {

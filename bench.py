@@ -389,7 +389,8 @@ def bench_batched(ctx_cls, dev, flush, steps=20):
             "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "tree_nodes": int(tok.ops.size), "dag_internal_nodes": int(st1["dag_internal"]),
             "dup_fraction": round(float(st["dup_fraction"]), 4),
-            "autotuned": {"points_per_thread": K, "groups": G, "kernel_ms": tune_ms},
+            "autotuned": {"points_per_thread": K, "groups": G, "threads_per_block": int(st1["threads_per_block"]),
+                          "kernel_ms": tune_ms},
             "gpu_launches_per_step": (s1["launches"] - s0["launches"]) / steps,
             "graph": True, "l2": "flushed between steps"}
 

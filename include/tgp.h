@@ -300,12 +300,14 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
 
 /*
  * Autotuner: times candidate launch shapes (points per thread K in {2,4,8,16},
- * tree groups for ~16/64/256/512 work items per SM) on this population and
+ * 128 threads per block, and 64 for K in {4,8}; tree groups for ~16/64/256/512
+ * work items per SM) on this population and
  * domain, with CUDA events on `stream` (synchronous), and records the fastest
  * for the (grid size, tree-count bucket, node-count bucket) of the
  * population.  Later plans of any population in the same bucket use it
  * unless the context's configuration forces a shape.  Outputs (may be NULL):
- * the chosen K, group count and its kernel time in milliseconds.
+ * the chosen K, group count and its kernel time in milliseconds (the chosen
+ * threads per block is in tgp_stats after the next launch).
  */
 int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, int32_t* K_out,
                  int32_t* groups_out, double* ms_out);

@@ -163,6 +163,7 @@ struct TuneKey {
 struct TuneChoice {
     int K;
     int items_per_sm;
+    int threads;
 };
 
 int log2_bucket(int64_t v) {
@@ -240,12 +241,12 @@ TuneKey tune_key(const PopIR& ir, int64_t N) {
     return TuneKey{N, log2_bucket((int64_t)ir.roots.size()), log2_bucket(ir.tree_nodes)};
 }
 
-PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W, int K, int items_per_sm) {
+PlanShape shape_for(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W, int K, int items_per_sm, int threads) {
     PlanShape s;
     s.N = N;
     s.W = W;
     s.K = K;
-    s.threads = 128;
+    s.threads = threads;
     s.dedup = !(c->cfg.flags & TGP_F_NO_DEDUP);
     int64_t tile = (int64_t)K * s.threads;
     int64_t n_tiles = (N + tile - 1) / tile;
@@ -263,7 +264,8 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W) {
     bool forced = c->cfg.points_per_thread > 0 || c->cfg.threads_per_block > 0 || c->cfg.n_groups > 0;
     if (!forced) {
         auto it = c->tuned.find(tune_key(ir, N));
-        if (it != c->tuned.end()) return shape_for(c, ir, N, W, it->second.K, it->second.items_per_sm);
+        if (it != c->tuned.end())
+            return shape_for(c, ir, N, W, it->second.K, it->second.items_per_sm, it->second.threads);
     }
     if (c->cfg.points_per_thread > 0) s.K = c->cfg.points_per_thread;
     if (c->cfg.threads_per_block > 0) s.threads = c->cfg.threads_per_block;
@@ -1148,17 +1150,19 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    TuneChoice choice{8, 64};
+    TuneChoice choice{8, 64, 128};
     PlanShape best_shape{};
     std::vector<PlanShape> tried;
     const int Ks[] = {2, 4, 8, 16};
     const int items[] = {16, 64, 256, 512};
     const bool was_capturing = ctx->capturing;
     ctx->capturing = true;   // no per-launch timing events while tuning
-    for (int K : Ks) {
-        if ((int64_t)K * 128 * 16 > N && K > 2) continue;   // tiles far larger than the grid
+    for (int K : Ks)
+    for (int threads : {128, 64}) {
+        if ((int64_t)K * threads * 16 > N && K > 2) continue;   // tiles far larger than the grid
+        if (threads == 64 && (K < 4 || K > 8)) continue;         // small tiles only where registers allow many CTAs
         for (int ips : items) {
-            PlanShape sh = shape_for(ctx, p->ir, N, d->W, K, ips);
+            PlanShape sh = shape_for(ctx, p->ir, N, d->W, K, ips, threads);
             bool dup = false;
             for (const PlanShape& t : tried) dup |= !(t < sh) && !(sh < t);
             if (dup) continue;
@@ -1182,7 +1186,7 @@ int tgp_autotune(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
             }
             if (ms_best < best) {
                 best = ms_best;
-                choice = TuneChoice{K, ips};
+                choice = TuneChoice{K, ips, threads};
                 best_shape = sh;
             }
         }

@@ -98,6 +98,11 @@ constexpr int OPC_FUSED_END = OPC_SUT + kNHotUn * 3;
 constexpr int kDispatchMask = 255;
 constexpr int kStoreSlotShift = 16;
 static_assert(OPC_FUSED_END <= kDispatchMask + 1, "opcodes must fit the dispatch byte");
+// Codes with which the dispatch loop leaves for sin / cos of a value that all
+// of a thread's points share (y, an immediate), held in A[0]; never in bytecode.
+constexpr int kExitSinUniform = 250;
+constexpr int kExitCosUniform = 251;
+static_assert(OPC_FUSED_END <= kExitSinUniform, "exit codes must not be opcodes");
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
 // high half), y = immediate bits, slot, or aux.

@@ -437,10 +437,11 @@ namespace {
 
 class GroupGen {
 public:
-    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv)
+    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
+             const std::vector<uint8_t>* xfree)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
           first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
-          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0) {}
+          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0), xfree_(xfree) {}
 
     int slot_high = 0;                    // slots used by the last run
     void set_kept_cap(int c) { kept_cap_ = c; }
@@ -496,6 +497,7 @@ private:
     std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
     std::vector<uint8_t> mark_;    // scratch of sort_touched_descending, all zero between calls
+    const std::vector<uint8_t>* xfree_;   // node has no x below it (or nullptr)
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
     bool is_cached(int32_t n) const { return cv_ && cv_->cached[n] >= 0; }
@@ -647,6 +649,7 @@ private:
             emit(F_CLD, 0, 0, 0, cv_->cached[n], 0);
         } else {
             compute(n);
+            if (xfree_ && (*xfree_)[n]) out_.back().uni = 1;   // the instruction that computed n
             if (cv_ && cv_->insert[n] >= 0 && !stored_[n]) {
                 emit(F_CST, 0, 0, 0, cv_->insert[n], 0);
                 stored_[n] = 1;
@@ -811,7 +814,7 @@ Ins encode(const IrIns& in) {
     default: opc = OPC_END; break;
     }
     Ins e;
-    e.x = opc;
+    e.x = opc | (in.uni ? kUniformBit : 0u);
     e.y = y;
     return e;
 }
@@ -943,6 +946,16 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
     // values + slots) within the SM's share for the interpreter's resident
     // CTAs at this K.  Temporaries may exceed it (a tree needs as many as its
     // Sethi-Ullman number).
+    // nodes with no x below them: their value is the same at all K points of
+    // a thread (the points share a row), operands are interned before users
+    std::vector<uint8_t> xfree(pop.dag.size(), 0);
+    for (size_t n = 0; n < pop.dag.size(); ++n) {
+        const DagNode& d = pop.dag.nodes[n];
+        bool f = d.op != T_X;
+        for (int c = 0; c < kMaxKids; ++c)
+            if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
+        xfree[n] = f;
+    }
     const int slot_bytes = shape.K * shape.threads * 4;
     const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
     plan.group_off.push_back(0);
@@ -950,7 +963,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
         std::vector<std::vector<IrIns>> part(G);
         std::vector<int> slots(G, 0);
         (*par)(G, [&](int g) {
-            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr);
+            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree);
             slots[g] = plan_group(gen, part[g], pop, groups[g], budget);
         });
         size_t total_ins = 0;
@@ -962,7 +975,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             plan.group_off.push_back((int64_t)plan.ir.size());
         }
     } else {
-        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv);
+        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree);
         for (int g = 0; g < G; ++g) {
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
             plan.group_off.push_back((int64_t)plan.ir.size());
@@ -993,7 +1006,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
                     fused = OPC_SUT + un_index(nx.fn) * 3 + nx.o1;
                 if (fused >= 0) {
                     Ins e = encode(nx);
-                    e.x = (uint32_t)fused | ((uint32_t)in.aux << kStoreSlotShift);
+                    e.x = (uint32_t)fused | (e.x & kUniformBit) | ((uint32_t)in.aux << kStoreSlotShift);
                     plan.code.push_back(e);
                     ++i;
                     continue;

@@ -102,6 +102,11 @@ static_assert(OPC_FUSED_END <= kDispatchMask + 1, "opcodes must fit the dispatch
 // of a thread's points share (y, an immediate), held in A[0]; never in bytecode.
 constexpr int kExitSinUniform = 250;
 constexpr int kExitCosUniform = 251;
+// Set in an opcode word (above the dispatch byte) when the instruction
+// computes a value with no x below it, which is the same at all of a
+// thread's points (they share a row): a division or a library call is then
+// evaluated once for the K points.
+constexpr uint32_t kUniformBit = 0x100;
 static_assert(OPC_FUSED_END <= kExitSinUniform, "exit codes must not be opcodes");
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
@@ -116,6 +121,7 @@ struct IrIns {
     int32_t form, fn, o1, o2;
     int32_t aux;
     uint32_t imm;   // binary32 bits of the immediate operand
+    int32_t uni = 0;   // computes a value with no x below it: the same at all of a thread's points
 };
 
 // Resident CTAs per SM the interpreter is built for, by points per thread K

@@ -123,6 +123,15 @@ enum {
                                  for add and mul.  Each is exact in binary32, so
                                  results are bitwise those of the trees as given
                                  (a NaN may differ in sign or payload). */
+#define TGP_F_NO_COLUMNS 32   /* evaluate every subtree at every point.  By default a
+                                 costly subtree with x but no y below it (its value
+                                 depends on the grid column only) is evaluated once
+                                 per column, in a phenotype launch on one row of W
+                                 points before the launch that loads it; results
+                                 are bitwise the same (the same arithmetic on the
+                                 same binary32 coordinates).  Column tables are not
+                                 used with the cross-call cache nor by
+                                 tgp_fitness_noalloc. */
 #define TGP_F_TRIG_RADIANS 16 /* sin, cos and tan take their argument in radians
                                  (the footnote of Table 1) instead of multiplied
                                  by pi (Sec. 3.2, the default): CUDA's binary32
@@ -318,7 +327,8 @@ int tgp_stats_get(tgp_ctx* ctx, tgp_stats* out);
 
 /*
  * Host-only inspection of the bytecode plan the library would run for a grid
- * of n_points points (used by CPU tests of the compiler; no device needed).
+ * of n_points points in one row (used by CPU tests of the compiler; no device
+ * needed; a one-row grid has no column tables).
  * Fills up to `cap` decoded instructions into ins_out[i*6 .. i*6+5] as
  * (form, fn, operand1, operand2, aux, imm_bits) and the group boundaries
  * into group_off_out[0..n_groups] (cap_groups entries at most).

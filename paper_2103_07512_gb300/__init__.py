@@ -22,7 +22,7 @@ OK = 0
 E_INVALID, E_TOKENS, E_NOMEM, E_BUDGET, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_BUSY = range(-1, -9, -1)
 PREFIX, POSTFIX = 0, 1
 TARGET_PAGIE, TARGET_TENSOR, TARGET_TOKENS = 0, 1, 2
-F_HOST_ONLY, F_NO_DEDUP, F_TIME_KERNELS, F_NO_SIMPLIFY, F_TRIG_RADIANS = 1, 2, 4, 8, 16
+F_HOST_ONLY, F_NO_DEDUP, F_TIME_KERNELS, F_NO_SIMPLIFY, F_TRIG_RADIANS, F_NO_COLUMNS = 1, 2, 4, 8, 16, 32
 N_OPS = 24
 
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
@@ -182,7 +182,7 @@ class Context:
 
     def __init__(self, device=0, host_only=False, cache_budget_bytes=0, points_per_thread=0,
                  threads_per_block=0, n_groups=0, dedup=True, time_kernels=False, cache_min_cost=0,
-                 simplify=True, trig="pi", plan_threads=0):
+                 simplify=True, trig="pi", plan_threads=0, columns=True):
         """trig: "pi" (sin(a) = sin(pi a), Sec. 3.2) or "rad" (radians, the
         footnote of Table 1), for sin, cos and tan."""
         if trig not in ("pi", "rad"):
@@ -192,7 +192,7 @@ class Context:
         cfg.device = device
         cfg.flags = ((F_HOST_ONLY if host_only else 0) | (0 if dedup else F_NO_DEDUP)
                      | (F_TIME_KERNELS if time_kernels else 0) | (0 if simplify else F_NO_SIMPLIFY)
-                     | (F_TRIG_RADIANS if trig == "rad" else 0))
+                     | (F_TRIG_RADIANS if trig == "rad" else 0) | (0 if columns else F_NO_COLUMNS))
         cfg.cache_budget_bytes = cache_budget_bytes
         cfg.points_per_thread = points_per_thread
         cfg.threads_per_block = threads_per_block

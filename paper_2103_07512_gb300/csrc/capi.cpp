@@ -123,6 +123,13 @@ struct Plan {
     size_t smem = 0;
     DevBuf<float*> table;          // cache entry pointers of the current launch
     std::vector<float*> h_table;
+    // column tables: their plan's buffers and the tables
+    DevBuf<Ins> ccode;
+    DevBuf<int64_t> cgroup_off;
+    DevBuf<int32_t> cgroup_order;
+    DevBuf<float> ctab;
+    int cgrid = 0;
+    size_t csmem = 0;
     CacheView view;                // view the cached-mode plan was built for
     cudaEvent_t done = nullptr;    // cached mode: the plan's last launch has finished
     ~Plan() {
@@ -283,6 +290,7 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W) {
 }
 
 bool trig_radians(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_TRIG_RADIANS) != 0; }
+bool columns_on(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_NO_COLUMNS) == 0; }
 // Radian trigonometry runs in the interpreter variant with the rest of Table 1.
 bool use_ext(const tgp_ctx* c, const HostPlan& hp) { return hp.ext || trig_radians(c); }
 
@@ -308,7 +316,7 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
-    CUDA_TRY(pl->counter.ensure(1));
+    CUDA_TRY(pl->counter.ensure(2));   // work queues of the launch and of its column tables
     CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s));
@@ -320,6 +328,19 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
                                  cudaMemcpyHostToDevice, s));
     }
     pl->smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.n_slots);
+    if (hp.col_plan) {
+        const HostPlan& ch = *hp.col_plan;
+        CUDA_TRY(pl->ccode.ensure(ch.code.size()));
+        CUDA_TRY(pl->cgroup_off.ensure(ch.code_off.size()));
+        CUDA_TRY(pl->cgroup_order.ensure(ch.group_order.size()));
+        CUDA_TRY(pl->ctab.ensure(hp.col_roots.size() * (size_t)hp.col_stride));
+        CUDA_TRY(cudaMemcpyAsync(pl->ccode.p, ch.code.data(), ch.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->cgroup_off.p, ch.code_off.data(), ch.code_off.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->cgroup_order.p, ch.group_order.data(), ch.group_order.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+        pl->csmem = eval_smem_bytes(ch.shape.K, ch.shape.threads, ch.n_slots);
+    }
     return TGP_OK;
 }
 
@@ -353,7 +374,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         const bool pre = !cached && pop->preplanned && !(pop->preplanned->shape < shape) &&
                          !(shape < pop->preplanned->shape);
         if (pre) pl->hp = std::move(pop->preplanned->plan);
-        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr, &c->par);
+        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr, &c->par, columns_on(c) && !cached);
         pop->preplanned.reset();
         if (cached) {
             pl->view = *cv;
@@ -381,6 +402,13 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
     if (rc) return rc;
     int64_t slots = (int64_t)bps * std::max(c->sms, 1);
     pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(pl->hp.n_items, slots));
+    if (pl->hp.col_plan) {   // the tables are phenotypes
+        const HostPlan& ch = *pl->hp.col_plan;
+        int cbps = 0;
+        rc = occupancy(c, ch.shape.K, true, use_ext(c, ch), ch.shape.threads, pl->csmem, &cbps);
+        if (rc) return rc;
+        pl->cgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ch.n_items, (int64_t)cbps * std::max(c->sms, 1)));
+    }
     *out = pl;
     return TGP_OK;
 }
@@ -651,8 +679,11 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     p.trig_rad = trig_radians(c) ? 1 : 0;
+    p.out_stride = p.N;
+    p.coltab = hp.col_plan ? pl->ctab.p : nullptr;
+    p.col_stride = hp.col_stride;
     if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
-    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 2 * sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (timed) {
@@ -668,6 +699,33 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
             c->ev_free.pop_back();
         }
         CUDA_TRY(cudaEventRecord(ev.first, s));
+    }
+    if (hp.col_plan) {
+        // the column tables first: phenotypes of their subtrees on one row of
+        // W points (same x coordinates; no y below them)
+        const HostPlan& ch = *hp.col_plan;
+        EvalParams q{};
+        q.code = pl->ccode.p;
+        q.group_off = pl->cgroup_off.p;
+        q.item_group = pl->cgroup_order.p;
+        q.n_items = ch.n_items;
+        q.n_tiles = ch.n_tiles;
+        q.warps_per_tile = ch.shape.threads / 32;
+        q.N = d->W;
+        q.W = d->W;
+        q.H = 1;
+        q.xlo = d->xlo;
+        q.xhi = d->xhi;
+        q.ylo = d->ylo;
+        q.yhi = d->ylo;
+        q.out = pl->ctab.p;
+        q.out_stride = hp.col_stride;
+        q.counter = pl->counter.p + 1;
+        q.n_slots = ch.n_slots;
+        q.max_items_per_cta = (int32_t)std::min<int64_t>(ch.n_items, INT32_MAX);
+        q.trig_rad = p.trig_rad;
+        CUDA_TRY(launch_eval(q, ch.shape.K, true, use_ext(c, ch), pl->cgrid, ch.shape.threads, pl->csmem, s));
+        c->stats.launches++;
     }
     CUDA_TRY(launch_eval(p, hp.shape.K, pheno, use_ext(c, hp), pl->grid, hp.shape.threads, pl->smem, s));
     if (timed) {
@@ -847,7 +905,7 @@ int preplan(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W, std::shared_ptr
         std::lock_guard<std::mutex> g(ctx->mu);
         pp->shape = choose_shape(ctx, ir, N, W);
     }
-    build_plan(ir, pp->shape, pp->plan, nullptr, &ctx->par);
+    build_plan(ir, pp->shape, pp->plan, nullptr, &ctx->par, columns_on(ctx));
     *out = std::move(pp);
     return TGP_OK;
 }
@@ -922,7 +980,7 @@ int tgp_create(tgp_ctx** out, const tgp_config* cfg) {
         c->par = [pool](int n, const std::function<void(int)>& body) { pool->run(n, body); };
     }
     constexpr int32_t kKnownFlags =
-        TGP_F_HOST_ONLY | TGP_F_NO_DEDUP | TGP_F_TIME_KERNELS | TGP_F_NO_SIMPLIFY | TGP_F_TRIG_RADIANS;
+        TGP_F_HOST_ONLY | TGP_F_NO_DEDUP | TGP_F_TIME_KERNELS | TGP_F_NO_SIMPLIFY | TGP_F_TRIG_RADIANS | TGP_F_NO_COLUMNS;
     if (c->cfg.flags & ~kKnownFlags) return fail(TGP_E_INVALID, "unknown flag bits 0x%x", c->cfg.flags & ~kKnownFlags);
     c->device = c->cfg.device;
     if (c->cfg.flags & TGP_F_HOST_ONLY) {

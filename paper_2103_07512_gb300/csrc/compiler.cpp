@@ -438,10 +438,11 @@ namespace {
 class GroupGen {
 public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
-             const std::vector<uint8_t>* xfree)
+             const std::vector<uint8_t>* xfree, const std::vector<int32_t>* col)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
           first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
-          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0), xfree_(xfree) {}
+          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0), xfree_(xfree),
+          col_(col) {}
 
     int slot_high = 0;                    // slots used by the last run
     void set_kept_cap(int c) { kept_cap_ = c; }
@@ -498,9 +499,13 @@ private:
     std::vector<int32_t> dfs_;
     std::vector<uint8_t> mark_;    // scratch of sort_touched_descending, all zero between calls
     const std::vector<uint8_t>* xfree_;   // node has no x below it (or nullptr)
+    const std::vector<int32_t>* col_;     // column-table entry of a node, -1 (or nullptr: none)
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
     bool is_cached(int32_t n) const { return cv_ && cv_->cached[n] >= 0; }
+    bool is_col(int32_t n) const { return col_ && (*col_)[n] >= 0; }
+    // loaded (cache or column table): its operands are not evaluated
+    bool is_loaded(int32_t n) const { return is_cached(n) || is_col(n); }
 
     void emit(int form, int fn, int o1, int o2, int aux, uint32_t imm) {
         IrIns in;
@@ -527,7 +532,7 @@ private:
                 if (last_pos_[n] == (int32_t)i) continue;    // already seen in this tree
                 if (last_pos_[n] < 0) { first_pos_[n] = (int32_t)i; span_touched_.push_back(n); }
                 last_pos_[n] = (int32_t)i;
-                if (is_cached(n)) continue;
+                if (is_loaded(n)) continue;
                 for (int c = 0; c < kMaxKids; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k >= 0 && !is_leaf(N(k).op)) dfs_.push_back(k);
@@ -543,7 +548,7 @@ private:
             while (!dfs_.empty()) {
                 int32_t n = dfs_.back();
                 dfs_.pop_back();
-                if (is_cached(n)) continue;
+                if (is_loaded(n)) continue;
                 for (int c = 0; c < kMaxKids; ++c) {
                     int32_t k = N(n).kid[c];
                     if (k < 0 || is_leaf(N(k).op) || where_[k] == -2) continue;
@@ -561,7 +566,7 @@ private:
             int32_t e = uses_[n];
             keep_[n] = dedup_ && e >= 2 && N(n).cost >= kKeepMinCost && where_[n] != -3 &&
                        last_pos_[n] - first_pos_[n] <= kKeepSpan;
-            if (is_cached(n)) continue;   // loaded, operands not evaluated
+            if (is_loaded(n)) continue;   // loaded, operands not evaluated
             int32_t f = keep_[n] ? 1 : e;
             for (int c = 0; c < kMaxKids; ++c) {
                 int32_t k = N(n).kid[c];
@@ -647,6 +652,8 @@ private:
         }
         if (is_cached(n)) {
             emit(F_CLD, 0, 0, 0, cv_->cached[n], 0);
+        } else if (is_col(n)) {
+            emit(F_COL, 0, 0, 0, (*col_)[n], 0);
         } else {
             compute(n);
             if (xfree_ && (*xfree_)[n]) out_.back().uni = 1;   // the instruction that computed n
@@ -811,6 +818,7 @@ Ins encode(const IrIns& in) {
     case F_CST: opc = OPC_CST; y = (uint32_t)in.aux; break;
     case F_CLD: opc = OPC_CLD; y = (uint32_t)in.aux; break;
     case F_SEL: opc = OPC_SEL; y = (uint32_t)in.aux | (in.imm << 16); break;
+    case F_COL: opc = OPC_COL; y = (uint32_t)in.aux; break;
     default: opc = OPC_END; break;
     }
     Ins e;
@@ -855,9 +863,20 @@ std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv) {
     return out;
 }
 
+namespace {
+// What planning reads of a population: its DAG, the roots of its trees and
+// their costs (a population, or the subtrees that become column tables).
+struct PlanPop {
+    const Dag& dag;
+    const std::vector<int32_t>& roots;
+    const std::vector<float>& tree_cost;
+    int64_t tree_nodes;
+};
+}  // namespace
+
 // One group's bytecode (appended to gen's output), with the kept-slot cap
 // that the group's temporaries leave of `budget`.  Returns the slots used.
-static int plan_group(GroupGen& gen, std::vector<IrIns>& ir, const PopIR& pop, const std::vector<int32_t>& trees,
+static int plan_group(GroupGen& gen, std::vector<IrIns>& ir, const PlanPop& pop, const std::vector<int32_t>& trees,
                       int budget) {
     // kept nodes get what the group's temporaries leave of the budget (a
     // tree's evaluation parks up to its Sethi-Ullman number of values)
@@ -879,8 +898,21 @@ static int plan_group(GroupGen& gen, std::vector<IrIns>& ir, const PopIR& pop, c
     return gen.slot_high;
 }
 
+// Subtrees with cost >= this (a binary32 add = 1) and x but no y below them
+// become column tables: a table load costs about one add per point.
+constexpr float kColMinCost = 4.f;
+constexpr size_t kColMaxEntries = 16384;
+
+static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
+                            const ParallelFor* par, bool columns);
+
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                const ParallelFor* par) {
+                const ParallelFor* par, bool columns) {
+    build_plan_impl(PlanPop{pop.dag, pop.roots, pop.tree_cost, pop.tree_nodes}, shape, plan, cv, par, columns);
+}
+
+static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
+                            const ParallelFor* par, bool columns) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -956,6 +988,57 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
         xfree[n] = f;
     }
+    // Column tables (grids of at least two rows and two columns, no cache
+    // view): the largest costly subtrees with x and no y below them, i.e.
+    // those used by a node that is not one itself, or that are tree roots.
+    std::vector<int32_t> col;
+    const int64_t W = shape.W > 0 ? shape.W : shape.N;
+    if (columns && !(cv && cv->active()) && W > 1 && shape.N / W > 1) {
+        const size_t nn = pop.dag.size();
+        std::vector<uint8_t> yfree(nn, 0), elig(nn, 0), need(nn, 0);
+        for (size_t n = 0; n < nn; ++n) {
+            const DagNode& d = pop.dag.nodes[n];
+            bool f = d.op != T_Y;
+            for (int c = 0; c < kMaxKids; ++c)
+                if (d.kid[c] >= 0) f = f && yfree[d.kid[c]];
+            yfree[n] = f;
+            elig[n] = f && !xfree[n] && !is_leaf(d.op) && d.cost >= kColMinCost;
+        }
+        for (int32_t r : pop.roots) need[r] = elig[r];
+        for (size_t n = 0; n < nn; ++n) {
+            if (elig[n]) continue;
+            for (int c = 0; c < kMaxKids; ++c) {
+                const int32_t k = pop.dag.nodes[n].kid[c];
+                if (k >= 0 && elig[k]) need[k] = 1;
+            }
+        }
+        for (size_t n = 0; n < nn; ++n)
+            if (need[n]) plan.col_roots.push_back((int32_t)n);
+        if (!plan.col_roots.empty() && plan.col_roots.size() <= kColMaxEntries) {
+            col.assign(nn, -1);
+            for (size_t e = 0; e < plan.col_roots.size(); ++e) col[plan.col_roots[e]] = (int32_t)e;
+            plan.col_stride = (W + 15) / 16 * 16;
+            // the tables' own plan: phenotypes of the subtrees on one row of W points
+            std::vector<float> costs;
+            for (int32_t r : plan.col_roots) costs.push_back(pop.dag.nodes[r].cost);
+            PlanShape cs;
+            cs.N = W;
+            cs.W = W;
+            cs.threads = 128;
+            cs.K = W >= (1 << 14) ? 4 : W >= (1 << 12) ? 2 : 1;
+            cs.dedup = shape.dedup;
+            const int64_t tiles = (W + cs.K * cs.threads - 1) / (cs.K * cs.threads);
+            const int64_t want = 152 * 64;
+            cs.n_groups = (int)std::max<int64_t>(
+                1, std::min<int64_t>((want + tiles - 1) / tiles, (int64_t)plan.col_roots.size()));
+            plan.col_plan = std::make_shared<HostPlan>();
+            build_plan_impl(PlanPop{pop.dag, plan.col_roots, costs, 0}, cs, *plan.col_plan, nullptr, par, false);
+        } else {
+            plan.col_roots.clear();
+        }
+    }
+    const std::vector<int32_t>* colp = col.empty() ? nullptr : &col;
+
     const int slot_bytes = shape.K * shape.threads * 4;
     const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
     plan.group_off.push_back(0);
@@ -963,7 +1046,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
         std::vector<std::vector<IrIns>> part(G);
         std::vector<int> slots(G, 0);
         (*par)(G, [&](int g) {
-            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree);
+            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree, colp);
             slots[g] = plan_group(gen, part[g], pop, groups[g], budget);
         });
         size_t total_ins = 0;
@@ -975,7 +1058,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
             plan.group_off.push_back((int64_t)plan.ir.size());
         }
     } else {
-        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree);
+        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree, colp);
         for (int g = 0; g < G; ++g) {
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
             plan.group_off.push_back((int64_t)plan.ir.size());

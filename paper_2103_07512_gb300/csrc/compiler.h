@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <functional>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -105,6 +106,13 @@ struct HostPlan {
     bool ext = false;                   // uses operators beyond the benchmark function set
     int n_tiles = 0;
     int64_t n_items = 0;
+    // Column tables: subtrees with x but no y below them have one value per
+    // grid column.  They are evaluated once on a one-row grid by col_plan (a
+    // phenotype launch into a table of col_roots.size() entries of
+    // col_stride floats each) before the launch, which loads them (F_COL).
+    std::vector<int32_t> col_roots;
+    std::shared_ptr<HostPlan> col_plan;
+    int64_t col_stride = 0;
 };
 
 // Default shape for a grid of N points on a device with `sms` SMs.
@@ -137,8 +145,10 @@ using ParallelFor = std::function<void(int n, const std::function<void(int)>& bo
 // depends on its own trees only, so the result is the same); a cache view
 // keeps the planning serial (a node is stored by the first group that
 // evaluates it).
+// With `columns` (and no cache view, on a grid of at least two rows), the
+// costliest subtrees that have x but no y below them become column tables.
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr,
-                const ParallelFor* par = nullptr);
+                const ParallelFor* par = nullptr, bool columns = false);
 
 Ins encode(const IrIns& in);
 

@@ -143,6 +143,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     p.trig_rad = v.trig_radians ? 1 : 0;
+    p.out_stride = p.N;
     NA_TRY(launch_eval(p, hp.shape.K, false, hp.ext || v.trig_radians, grid, hp.shape.threads, smem, s));
 
     FinalizeParams f{};

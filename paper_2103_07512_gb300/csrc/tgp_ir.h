@@ -51,6 +51,7 @@ enum Form : int {
     F_CST,    // cache entry aux = A (HBM)
     F_CLD,    // A = cache entry aux (HBM)
     F_SEL,    // A = slot aux != 0 ? slot imm : A    (if; both operands in slots)
+    F_COL,    // A = column-table entry aux at the thread's columns (a subtree with no y below)
     F_NFORMS
 };
 
@@ -97,7 +98,8 @@ constexpr int OPC_FUSED_END = OPC_SUT + kNHotUn * 3;
 // valid target (codes without a form leave the loop).
 constexpr int kDispatchMask = 255;
 constexpr int kStoreSlotShift = 16;
-static_assert(OPC_FUSED_END <= kDispatchMask + 1, "opcodes must fit the dispatch byte");
+constexpr int OPC_COL = OPC_FUSED_END;   // F_COL, left to the C++ caller
+static_assert(OPC_COL < kDispatchMask + 1, "opcodes must fit the dispatch byte");
 // Codes with which the dispatch loop leaves for sin / cos of a value that all
 // of a thread's points share (y, an immediate), held in A[0]; never in bytecode.
 constexpr int kExitSinUniform = 250;
@@ -107,7 +109,7 @@ constexpr int kExitCosUniform = 251;
 // thread's points (they share a row): a division or a library call is then
 // evaluated once for the K points.
 constexpr uint32_t kUniformBit = 0x100;
-static_assert(OPC_FUSED_END <= kExitSinUniform, "exit codes must not be opcodes");
+static_assert(OPC_COL < kExitSinUniform, "exit codes must not be opcodes");
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
 // high half), y = immediate bits, slot, or aux.
@@ -168,6 +170,9 @@ struct EvalParams {
     int32_t n_slots;            // shared-memory value slots per thread
     int32_t max_items_per_cta;  // bound on the work-queue loop
     int32_t trig_rad;           // sin/cos/tan in radians (interpreter variant with the rest of Table 1 only)
+    const float* coltab;        // column tables (F_COL): entry e at coltab + e * col_stride, or nullptr
+    int64_t col_stride;         // floats per column-table entry
+    int64_t out_stride;         // floats between the phenotype rows of two trees (N, or a table's stride)
 };
 
 struct FinalizeParams {

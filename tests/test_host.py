@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_layout():
     lay = tgp.debug_layout()
-    assert lay["n_opnd"] == 4 and lay["n_forms"] == 12
+    assert lay["n_opnd"] == 4 and lay["n_forms"] == 13   # ... F_SEL, F_COL
 
 
 def test_host_only_context_refuses_device_work(ctx):
@@ -533,3 +533,12 @@ def test_concurrent_group_planning_gives_the_serial_bytecode(name):
             ib, ob = b.debug_plan(b.compile_tokens(tok), n_points)
             assert np.array_equal(oa, ob) and np.array_equal(ia, ib)
             assert len(oa) > 2 or n_points == 1
+
+
+def test_column_flag_is_accepted_and_debug_plans_have_no_column_loads():
+    tok = I.to_tokens([I.parse_string("add(sin(x), mult(y, cos(x)))")])
+    for cols in (True, False):
+        with tgp.Context(host_only=True, columns=cols) as c:
+            ins, off = c.debug_plan(c.compile_tokens(tok), 64 * 64)
+            assert not (ins[:, 0] == 12).any()   # F_COL: column tables need a grid of several rows
+    assert tgp.F_NO_COLUMNS == 32

@@ -127,11 +127,12 @@ enum {
                                  costly subtree with x but no y below it (its value
                                  depends on the grid column only) is evaluated once
                                  per column, in a phenotype launch on one row of W
-                                 points before the launch that loads it; results
-                                 are bitwise the same (the same arithmetic on the
-                                 same binary32 coordinates).  Column tables are not
-                                 used with the cross-call cache nor by
-                                 tgp_fitness_noalloc. */
+                                 points before the launch that loads it, and one
+                                 with no x below it once per row (one column of H
+                                 points); results are bitwise the same (the same
+                                 arithmetic on the same binary32 coordinates).
+                                 These tables are not used with the cross-call
+                                 cache nor by tgp_fitness_noalloc. */
 #define TGP_F_TRIG_RADIANS 16 /* sin, cos and tan take their argument in radians
                                  (the footnote of Table 1) instead of multiplied
                                  by pi (Sec. 3.2, the default): CUDA's binary32

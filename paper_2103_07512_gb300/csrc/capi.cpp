@@ -130,6 +130,13 @@ struct Plan {
     DevBuf<float> ctab;
     int cgrid = 0;
     size_t csmem = 0;
+    // row tables, likewise
+    DevBuf<Ins> rcode;
+    DevBuf<int64_t> rgroup_off;
+    DevBuf<int32_t> rgroup_order;
+    DevBuf<float> rtab;
+    int rgrid = 0;
+    size_t rsmem = 0;
     CacheView view;                // view the cached-mode plan was built for
     cudaEvent_t done = nullptr;    // cached mode: the plan's last launch has finished
     ~Plan() {
@@ -316,7 +323,7 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
-    CUDA_TRY(pl->counter.ensure(2));   // work queues of the launch and of its column tables
+    CUDA_TRY(pl->counter.ensure(3));   // work queues of the launch and of its column and row tables
     CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s));
@@ -340,6 +347,19 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
         CUDA_TRY(cudaMemcpyAsync(pl->cgroup_order.p, ch.group_order.data(), ch.group_order.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, s));
         pl->csmem = eval_smem_bytes(ch.shape.K, ch.shape.threads, ch.n_slots);
+    }
+    if (hp.row_plan) {
+        const HostPlan& rh = *hp.row_plan;
+        CUDA_TRY(pl->rcode.ensure(rh.code.size()));
+        CUDA_TRY(pl->rgroup_off.ensure(rh.code_off.size()));
+        CUDA_TRY(pl->rgroup_order.ensure(rh.group_order.size()));
+        CUDA_TRY(pl->rtab.ensure(hp.row_roots.size() * (size_t)hp.row_stride));
+        CUDA_TRY(cudaMemcpyAsync(pl->rcode.p, rh.code.data(), rh.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->rgroup_off.p, rh.code_off.data(), rh.code_off.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl->rgroup_order.p, rh.group_order.data(), rh.group_order.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+        pl->rsmem = eval_smem_bytes(rh.shape.K, rh.shape.threads, rh.n_slots);
     }
     return TGP_OK;
 }
@@ -408,6 +428,13 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         rc = occupancy(c, ch.shape.K, true, use_ext(c, ch), ch.shape.threads, pl->csmem, &cbps);
         if (rc) return rc;
         pl->cgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ch.n_items, (int64_t)cbps * std::max(c->sms, 1)));
+    }
+    if (pl->hp.row_plan) {
+        const HostPlan& rh = *pl->hp.row_plan;
+        int rbps = 0;
+        rc = occupancy(c, rh.shape.K, true, use_ext(c, rh), rh.shape.threads, pl->rsmem, &rbps);
+        if (rc) return rc;
+        pl->rgrid = (int)std::max<int64_t>(1, std::min<int64_t>(rh.n_items, (int64_t)rbps * std::max(c->sms, 1)));
     }
     *out = pl;
     return TGP_OK;
@@ -682,8 +709,10 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.out_stride = p.N;
     p.coltab = hp.col_plan ? pl->ctab.p : nullptr;
     p.col_stride = hp.col_stride;
+    p.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
+    p.row_stride = hp.row_stride;
     if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
-    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 2 * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (timed) {
@@ -725,6 +754,33 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         q.max_items_per_cta = (int32_t)std::min<int64_t>(ch.n_items, INT32_MAX);
         q.trig_rad = p.trig_rad;
         CUDA_TRY(launch_eval(q, ch.shape.K, true, use_ext(c, ch), pl->cgrid, ch.shape.threads, pl->csmem, s));
+        c->stats.launches++;
+    }
+    if (hp.row_plan) {
+        // the row tables: phenotypes of their subtrees on one column of H
+        // points (same y coordinates; no x below them)
+        const HostPlan& rh = *hp.row_plan;
+        EvalParams q{};
+        q.code = pl->rcode.p;
+        q.group_off = pl->rgroup_off.p;
+        q.item_group = pl->rgroup_order.p;
+        q.n_items = rh.n_items;
+        q.n_tiles = rh.n_tiles;
+        q.warps_per_tile = rh.shape.threads / 32;
+        q.N = d->H;
+        q.W = 1;
+        q.H = d->H;
+        q.xlo = d->xlo;
+        q.xhi = d->xlo;
+        q.ylo = d->ylo;
+        q.yhi = d->yhi;
+        q.out = pl->rtab.p;
+        q.out_stride = hp.row_stride;
+        q.counter = pl->counter.p + 2;
+        q.n_slots = rh.n_slots;
+        q.max_items_per_cta = (int32_t)std::min<int64_t>(rh.n_items, INT32_MAX);
+        q.trig_rad = p.trig_rad;
+        CUDA_TRY(launch_eval(q, rh.shape.K, true, use_ext(c, rh), pl->rgrid, rh.shape.threads, pl->rsmem, s));
         c->stats.launches++;
     }
     CUDA_TRY(launch_eval(p, hp.shape.K, pheno, use_ext(c, hp), pl->grid, hp.shape.threads, pl->smem, s));

@@ -438,11 +438,11 @@ namespace {
 class GroupGen {
 public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
-             const std::vector<uint8_t>* xfree, const std::vector<int32_t>* col)
+             const std::vector<uint8_t>* xfree, const std::vector<int32_t>* col, const std::vector<int32_t>* row)
         : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
           first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
           cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0), xfree_(xfree),
-          col_(col) {}
+          col_(col), row_(row) {}
 
     int slot_high = 0;                    // slots used by the last run
     void set_kept_cap(int c) { kept_cap_ = c; }
@@ -500,12 +500,14 @@ private:
     std::vector<uint8_t> mark_;    // scratch of sort_touched_descending, all zero between calls
     const std::vector<uint8_t>* xfree_;   // node has no x below it (or nullptr)
     const std::vector<int32_t>* col_;     // column-table entry of a node, -1 (or nullptr: none)
+    const std::vector<int32_t>* row_;     // row-table entry of a node, -1 (or nullptr: none)
 
     const DagNode& N(int32_t n) const { return d_.nodes[n]; }
     bool is_cached(int32_t n) const { return cv_ && cv_->cached[n] >= 0; }
     bool is_col(int32_t n) const { return col_ && (*col_)[n] >= 0; }
-    // loaded (cache or column table): its operands are not evaluated
-    bool is_loaded(int32_t n) const { return is_cached(n) || is_col(n); }
+    bool is_row(int32_t n) const { return row_ && (*row_)[n] >= 0; }
+    // loaded (cache, column or row table): its operands are not evaluated
+    bool is_loaded(int32_t n) const { return is_cached(n) || is_col(n) || is_row(n); }
 
     void emit(int form, int fn, int o1, int o2, int aux, uint32_t imm) {
         IrIns in;
@@ -654,6 +656,8 @@ private:
             emit(F_CLD, 0, 0, 0, cv_->cached[n], 0);
         } else if (is_col(n)) {
             emit(F_COL, 0, 0, 0, (*col_)[n], 0);
+        } else if (is_row(n)) {
+            emit(F_ROW, 0, 0, 0, (*row_)[n], 0);
         } else {
             compute(n);
             if (xfree_ && (*xfree_)[n]) out_.back().uni = 1;   // the instruction that computed n
@@ -819,6 +823,7 @@ Ins encode(const IrIns& in) {
     case F_CLD: opc = OPC_CLD; y = (uint32_t)in.aux; break;
     case F_SEL: opc = OPC_SEL; y = (uint32_t)in.aux | (in.imm << 16); break;
     case F_COL: opc = OPC_COL; y = (uint32_t)in.aux; break;
+    case F_ROW: opc = OPC_ROW; y = (uint32_t)in.aux; break;
     default: opc = OPC_END; break;
     }
     Ins e;
@@ -988,56 +993,74 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
         xfree[n] = f;
     }
-    // Column tables (grids of at least two rows and two columns, no cache
-    // view): the largest costly subtrees with x and no y below them, i.e.
-    // those used by a node that is not one itself, or that are tree roots.
-    std::vector<int32_t> col;
+    // Column and row tables (grids of at least two rows and two columns, no
+    // cache view): the largest costly subtrees with x and no y below them
+    // (one value per column) and with no x below them (one value per row),
+    // i.e. those used by a node evaluated in this plan, or tree roots.  The
+    // tables' own plans are phenotype launches on one row of W points and on
+    // one column of H points.
+    std::vector<int32_t> col, row;
     const int64_t W = shape.W > 0 ? shape.W : shape.N;
-    if (columns && !(cv && cv->active()) && W > 1 && shape.N / W > 1) {
+    const int64_t H = W > 0 ? shape.N / W : 0;
+    if (columns && !(cv && cv->active()) && W > 1 && H > 1) {
         const size_t nn = pop.dag.size();
-        std::vector<uint8_t> yfree(nn, 0), elig(nn, 0), need(nn, 0);
+        std::vector<uint8_t> yfree(nn, 0), celig(nn, 0), relig(nn, 0), cneed(nn, 0), rneed(nn, 0);
         for (size_t n = 0; n < nn; ++n) {
             const DagNode& d = pop.dag.nodes[n];
             bool f = d.op != T_Y;
             for (int c = 0; c < kMaxKids; ++c)
                 if (d.kid[c] >= 0) f = f && yfree[d.kid[c]];
             yfree[n] = f;
-            elig[n] = f && !xfree[n] && !is_leaf(d.op) && d.cost >= kColMinCost;
+            const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost;
+            celig[n] = costly && f && !xfree[n];
+            relig[n] = costly && xfree[n];
         }
-        for (int32_t r : pop.roots) need[r] = elig[r];
+        for (int32_t r : pop.roots) {
+            cneed[r] = celig[r];
+            rneed[r] = relig[r];
+        }
         for (size_t n = 0; n < nn; ++n) {
-            if (elig[n]) continue;
+            if (celig[n] || relig[n]) continue;   // inside a table's subtree (or one)
             for (int c = 0; c < kMaxKids; ++c) {
                 const int32_t k = pop.dag.nodes[n].kid[c];
-                if (k >= 0 && elig[k]) need[k] = 1;
+                if (k < 0) continue;
+                if (celig[k]) cneed[k] = 1;
+                if (relig[k]) rneed[k] = 1;
             }
         }
-        for (size_t n = 0; n < nn; ++n)
-            if (need[n]) plan.col_roots.push_back((int32_t)n);
-        if (!plan.col_roots.empty() && plan.col_roots.size() <= kColMaxEntries) {
-            col.assign(nn, -1);
-            for (size_t e = 0; e < plan.col_roots.size(); ++e) col[plan.col_roots[e]] = (int32_t)e;
-            plan.col_stride = (W + 15) / 16 * 16;
-            // the tables' own plan: phenotypes of the subtrees on one row of W points
+        auto make_tables = [&](const std::vector<uint8_t>& need, std::vector<int32_t>& view,
+                               std::vector<int32_t>& roots, std::shared_ptr<HostPlan>& tplan, int64_t& stride,
+                               int64_t n_points, int64_t row_len) {
+            for (size_t n = 0; n < nn; ++n)
+                if (need[n]) roots.push_back((int32_t)n);
+            if (roots.empty() || roots.size() > kColMaxEntries) {
+                roots.clear();
+                return;
+            }
+            view.assign(nn, -1);
+            for (size_t e = 0; e < roots.size(); ++e) view[roots[e]] = (int32_t)e;
+            stride = (n_points + 15) / 16 * 16;
             std::vector<float> costs;
-            for (int32_t r : plan.col_roots) costs.push_back(pop.dag.nodes[r].cost);
-            PlanShape cs;
-            cs.N = W;
-            cs.W = W;
-            cs.threads = 128;
-            cs.K = W >= (1 << 14) ? 4 : W >= (1 << 12) ? 2 : 1;
-            cs.dedup = shape.dedup;
-            const int64_t tiles = (W + cs.K * cs.threads - 1) / (cs.K * cs.threads);
+            for (int32_t r : roots) costs.push_back(pop.dag.nodes[r].cost);
+            PlanShape ts;
+            ts.N = n_points;
+            ts.W = row_len;
+            ts.threads = 128;
+            // one row: K points of it per thread; one column: a point per thread
+            ts.K = row_len == 1 ? 1 : n_points >= (1 << 14) ? 4 : n_points >= (1 << 12) ? 2 : 1;
+            ts.dedup = shape.dedup;
+            const int64_t tiles = (n_points + ts.K * ts.threads - 1) / (ts.K * ts.threads);
             const int64_t want = 152 * 64;
-            cs.n_groups = (int)std::max<int64_t>(
-                1, std::min<int64_t>((want + tiles - 1) / tiles, (int64_t)plan.col_roots.size()));
-            plan.col_plan = std::make_shared<HostPlan>();
-            build_plan_impl(PlanPop{pop.dag, plan.col_roots, costs, 0}, cs, *plan.col_plan, nullptr, par, false);
-        } else {
-            plan.col_roots.clear();
-        }
+            ts.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles,
+                                                                     (int64_t)roots.size()));
+            tplan = std::make_shared<HostPlan>();
+            build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tplan, nullptr, par, false);
+        };
+        make_tables(cneed, col, plan.col_roots, plan.col_plan, plan.col_stride, W, W);
+        make_tables(rneed, row, plan.row_roots, plan.row_plan, plan.row_stride, H, 1);
     }
     const std::vector<int32_t>* colp = col.empty() ? nullptr : &col;
+    const std::vector<int32_t>* rowp = row.empty() ? nullptr : &row;
 
     const int slot_bytes = shape.K * shape.threads * 4;
     const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
@@ -1046,7 +1069,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         std::vector<std::vector<IrIns>> part(G);
         std::vector<int> slots(G, 0);
         (*par)(G, [&](int g) {
-            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree, colp);
+            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree, colp, rowp);
             slots[g] = plan_group(gen, part[g], pop, groups[g], budget);
         });
         size_t total_ins = 0;
@@ -1058,7 +1081,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             plan.group_off.push_back((int64_t)plan.ir.size());
         }
     } else {
-        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree, colp);
+        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree, colp, rowp);
         for (int g = 0; g < G; ++g) {
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
             plan.group_off.push_back((int64_t)plan.ir.size());

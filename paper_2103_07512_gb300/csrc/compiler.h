@@ -113,6 +113,11 @@ struct HostPlan {
     std::vector<int32_t> col_roots;
     std::shared_ptr<HostPlan> col_plan;
     int64_t col_stride = 0;
+    // Row tables, likewise: subtrees with no x below them have one value per
+    // grid row, evaluated on one column of H points (F_ROW loads them).
+    std::vector<int32_t> row_roots;
+    std::shared_ptr<HostPlan> row_plan;
+    int64_t row_stride = 0;
 };
 
 // Default shape for a grid of N points on a device with `sms` SMs.
@@ -145,8 +150,9 @@ using ParallelFor = std::function<void(int n, const std::function<void(int)>& bo
 // depends on its own trees only, so the result is the same); a cache view
 // keeps the planning serial (a node is stored by the first group that
 // evaluates it).
-// With `columns` (and no cache view, on a grid of at least two rows), the
-// costliest subtrees that have x but no y below them become column tables.
+// With `columns` (and no cache view, on a grid of at least two rows and two
+// columns), the costly subtrees that have x but no y below them become column
+// tables, and those with no x below them row tables.
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr,
                 const ParallelFor* par = nullptr, bool columns = false);
 

@@ -52,6 +52,7 @@ enum Form : int {
     F_CLD,    // A = cache entry aux (HBM)
     F_SEL,    // A = slot aux != 0 ? slot imm : A    (if; both operands in slots)
     F_COL,    // A = column-table entry aux at the thread's columns (a subtree with no y below)
+    F_ROW,    // A = row-table entry aux at the thread's row (a subtree with no x below)
     F_NFORMS
 };
 
@@ -110,6 +111,8 @@ constexpr int kExitCosUniform = 251;
 // evaluated once for the K points.
 constexpr uint32_t kUniformBit = 0x100;
 static_assert(OPC_COL < kExitSinUniform, "exit codes must not be opcodes");
+constexpr int OPC_ROW = 252;                // F_ROW, left to the C++ caller
+static_assert(OPC_ROW > kExitCosUniform && OPC_ROW <= kDispatchMask, "F_ROW code");
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
 // high half), y = immediate bits, slot, or aux.
@@ -172,6 +175,8 @@ struct EvalParams {
     int32_t trig_rad;           // sin/cos/tan in radians (interpreter variant with the rest of Table 1 only)
     const float* coltab;        // column tables (F_COL): entry e at coltab + e * col_stride, or nullptr
     int64_t col_stride;         // floats per column-table entry
+    const float* rowtab;        // row tables (F_ROW): entry e at rowtab + e * row_stride, or nullptr
+    int64_t row_stride;         // floats per row-table entry
     int64_t out_stride;         // floats between the phenotype rows of two trees (N, or a table's stride)
 };
 

@@ -1,6 +1,7 @@
-"""Column tables (subtrees with x but no y below them evaluated once per grid
-column, then loaded): phenotypes and fitness bitwise equal to evaluating every
-subtree at every point, on square, ragged and one-row grids, for every
+"""Column and row tables (subtrees with x but no y below them evaluated once
+per grid column, those with no x below them once per grid row, then loaded):
+phenotypes and fitness bitwise equal to evaluating every subtree at every
+point, on square, ragged, one-row and one-column grids, for every
 points-per-thread value, with every operator, in radians, with a target tensor
 and through a captured graph; and against the oracle."""
 import numpy as np
@@ -32,20 +33,22 @@ def bits(a):
     return b
 
 
-def y_free_heavy(rng, n, funcs=I.FUNCTIONS):
-    """Trees whose subtrees often have x but no y below them."""
-    def tree(d, allow_y):
+def y_free_heavy(rng, n, funcs=I.FUNCTIONS, main=I.X, other=I.Y):
+    """Trees whose subtrees often have `main` but not `other` below them (and
+    the mirror image for half of the trees)."""
+    def tree(d, allow_other, a, b):
         if d == 0 or rng.random() < 0.15:
             r = rng.random()
             if r < 0.45:
-                return I.leaf(I.X)
-            if r < 0.6 and allow_y:
-                return I.leaf(I.Y)
+                return I.leaf(a)
+            if r < 0.6 and allow_other:
+                return I.leaf(b)
             return I.leaf(I.CONST, float(rng.uniform(-1, 1)))
         f = funcs[int(rng.integers(len(funcs)))]
-        ay = allow_y and rng.random() < 0.5
-        return I.node(f, *[tree(d - 1, ay) for _ in range(I.ARITY[f])])
-    return [tree(int(rng.integers(2, 7)), True) for _ in range(n)]
+        ao = allow_other and rng.random() < 0.5
+        return I.node(f, *[tree(d - 1, ao, a, b) for _ in range(I.ARITY[f])])
+    return [tree(int(rng.integers(2, 7)), True, main, other) if i % 2 == 0 else
+            tree(int(rng.integers(2, 7)), True, other, main) for i in range(n)]
 
 
 @pytest.mark.parametrize("W,H", [(64, 48), (33, 17), (129, 65), (7, 5), (100, 1), (1, 100), (1024, 16)])
@@ -96,12 +99,13 @@ def test_columns_against_the_oracle_and_through_a_graph():
     assert_fitness(fit, r64, re, g.N, "columns")
 
 
-def test_column_launch_is_counted():
-    rng = np.random.default_rng(63)
-    tok = I.to_tokens([I.parse_string("add(sin(x), y)")] + y_free_heavy(rng, 20))
+@pytest.mark.parametrize("expr,extra", [("add(sin(x), y)", 2), ("add(cos(y), x)", 2),
+                                        ("mult(sin(x), cos(y))", 4), ("add(x, y)", 0)])
+def test_table_launches_are_counted(expr, extra):
+    tok = I.to_tokens([I.parse_string(expr)])
     g = I.Grid(64, 64)
     with tgp.Context() as a, tgp.Context(columns=False) as b:
         for c in (a, b):
             run(c, tok, g)
-        # phenotype and fitness: two launches each, plus a column pass each with tables
-        assert a.stats()["launches"] == b.stats()["launches"] + 2
+        # phenotype and fitness, each with a column and / or a row pass where there are tables
+        assert a.stats()["launches"] == b.stats()["launches"] + extra

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_layout():
     lay = tgp.debug_layout()
-    assert lay["n_opnd"] == 4 and lay["n_forms"] == 13   # ... F_SEL, F_COL
+    assert lay["n_opnd"] == 4 and lay["n_forms"] == 14   # ... F_SEL, F_COL, F_ROW
 
 
 def test_host_only_context_refuses_device_work(ctx):

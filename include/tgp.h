@@ -131,8 +131,9 @@ enum {
                                  with no x below it once per row (one column of H
                                  points); results are bitwise the same (the same
                                  arithmetic on the same binary32 coordinates).
-                                 These tables are not used with the cross-call
-                                 cache nor by tgp_fitness_noalloc. */
+                                 With the cross-call cache, subtrees that hold a
+                                 cache load or store are not tabled;
+                                 tgp_fitness_noalloc uses no tables. */
 #define TGP_F_TRIG_RADIANS 16 /* sin, cos and tan take their argument in radians
                                  (the footnote of Table 1) instead of multiplied
                                  by pi (Sec. 3.2, the default): CUDA's binary32

@@ -109,11 +109,21 @@ struct Domain {
     int64_t N() const { return (int64_t)W * H; }
 };
 
+// Where one program (a launch's bytecode, group offsets and group order)
+// sits in a plan's device blob.
+struct Prog {
+    const Ins* code = nullptr;
+    const int64_t* group_off = nullptr;
+    const int32_t* group_order = nullptr;
+};
+
 struct Plan {
     HostPlan hp;
-    DevBuf<Ins> code;
-    DevBuf<int64_t> group_off;
-    DevBuf<int32_t> group_order;
+    // the programs of the launch and of its column and row tables, uploaded
+    // together in one copy
+    DevBuf<char> blob;
+    std::vector<char> hblob;
+    Prog prog, cprog, rprog;
     DevBuf<float> partial;
     DevBuf<double> rmse;
     DevBuf<int32_t> counter;
@@ -123,17 +133,10 @@ struct Plan {
     size_t smem = 0;
     DevBuf<float*> table;          // cache entry pointers of the current launch
     std::vector<float*> h_table;
-    // column tables: their plan's buffers and the tables
-    DevBuf<Ins> ccode;
-    DevBuf<int64_t> cgroup_off;
-    DevBuf<int32_t> cgroup_order;
+    // column and row tables and their launch shapes
     DevBuf<float> ctab;
     int cgrid = 0;
     size_t csmem = 0;
-    // row tables, likewise
-    DevBuf<Ins> rcode;
-    DevBuf<int64_t> rgroup_off;
-    DevBuf<int32_t> rgroup_order;
     DevBuf<float> rtab;
     int rgrid = 0;
     size_t rsmem = 0;
@@ -318,17 +321,47 @@ int occupancy(tgp_ctx* c, int K, bool pheno, bool ext, int threads, size_t smem,
 int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     const HostPlan& hp = pl->hp;
     const int warps = hp.shape.threads / 32;
-    CUDA_TRY(pl->code.ensure(hp.code.size()));
-    CUDA_TRY(pl->group_off.ensure(hp.code_off.size()));
-    CUDA_TRY(pl->group_order.ensure(hp.group_order.size()));
+    // one host image of the programs, copied in one transfer
+    struct Seg { const HostPlan* h; size_t code, off, ord; };
+    std::vector<Seg> segs;
+    size_t total = 0;
+    auto place = [&](size_t bytes) {
+        const size_t o = total;
+        total += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const HostPlan* const hps[3] = {&hp, hp.col_plan.get(), hp.row_plan.get()};
+    for (const HostPlan* h : hps) {
+        if (!h) {
+            segs.push_back(Seg{nullptr, 0, 0, 0});
+            continue;
+        }
+        Seg g{h, 0, 0, 0};
+        g.code = place(h->code.size() * sizeof(Ins));
+        g.off = place(h->code_off.size() * sizeof(int64_t));
+        g.ord = place(h->group_order.size() * sizeof(int32_t));
+        segs.push_back(g);
+    }
+    pl->hblob.resize(total);
+    for (const Seg& g : segs) {
+        if (!g.h) continue;
+        std::memcpy(pl->hblob.data() + g.code, g.h->code.data(), g.h->code.size() * sizeof(Ins));
+        std::memcpy(pl->hblob.data() + g.off, g.h->code_off.data(), g.h->code_off.size() * sizeof(int64_t));
+        std::memcpy(pl->hblob.data() + g.ord, g.h->group_order.data(), g.h->group_order.size() * sizeof(int32_t));
+    }
+    CUDA_TRY(pl->blob.ensure(total));
+    CUDA_TRY(cudaMemcpyAsync(pl->blob.p, pl->hblob.data(), total, cudaMemcpyHostToDevice, s));
+    Prog* progs[3] = {&pl->prog, &pl->cprog, &pl->rprog};
+    for (int i = 0; i < 3; ++i) {
+        *progs[i] = Prog();
+        if (!segs[i].h) continue;
+        progs[i]->code = reinterpret_cast<const Ins*>(pl->blob.p + segs[i].code);
+        progs[i]->group_off = reinterpret_cast<const int64_t*>(pl->blob.p + segs[i].off);
+        progs[i]->group_order = reinterpret_cast<const int32_t*>(pl->blob.p + segs[i].ord);
+    }
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
     CUDA_TRY(pl->counter.ensure(3));   // work queues of the launch and of its column and row tables
-    CUDA_TRY(cudaMemcpyAsync(pl->code.p, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(pl->group_off.p, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
-                             cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(pl->group_order.p, hp.group_order.data(), hp.group_order.size() * sizeof(int32_t),
-                             cudaMemcpyHostToDevice, s));
     if (!pl->h_table.empty()) {
         CUDA_TRY(pl->table.ensure(pl->h_table.size()));
         CUDA_TRY(cudaMemcpyAsync(pl->table.p, pl->h_table.data(), pl->h_table.size() * sizeof(float*),
@@ -337,28 +370,12 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     pl->smem = eval_smem_bytes(hp.shape.K, hp.shape.threads, hp.n_slots);
     if (hp.col_plan) {
         const HostPlan& ch = *hp.col_plan;
-        CUDA_TRY(pl->ccode.ensure(ch.code.size()));
-        CUDA_TRY(pl->cgroup_off.ensure(ch.code_off.size()));
-        CUDA_TRY(pl->cgroup_order.ensure(ch.group_order.size()));
         CUDA_TRY(pl->ctab.ensure(hp.col_roots.size() * (size_t)hp.col_stride));
-        CUDA_TRY(cudaMemcpyAsync(pl->ccode.p, ch.code.data(), ch.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->cgroup_off.p, ch.code_off.data(), ch.code_off.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->cgroup_order.p, ch.group_order.data(), ch.group_order.size() * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, s));
         pl->csmem = eval_smem_bytes(ch.shape.K, ch.shape.threads, ch.n_slots);
     }
     if (hp.row_plan) {
         const HostPlan& rh = *hp.row_plan;
-        CUDA_TRY(pl->rcode.ensure(rh.code.size()));
-        CUDA_TRY(pl->rgroup_off.ensure(rh.code_off.size()));
-        CUDA_TRY(pl->rgroup_order.ensure(rh.group_order.size()));
         CUDA_TRY(pl->rtab.ensure(hp.row_roots.size() * (size_t)hp.row_stride));
-        CUDA_TRY(cudaMemcpyAsync(pl->rcode.p, rh.code.data(), rh.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->rgroup_off.p, rh.code_off.data(), rh.code_off.size() * sizeof(int64_t),
-                                 cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(pl->rgroup_order.p, rh.group_order.data(), rh.group_order.size() * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, s));
         pl->rsmem = eval_smem_bytes(rh.shape.K, rh.shape.threads, rh.n_slots);
     }
     return TGP_OK;
@@ -394,7 +411,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         const bool pre = !cached && pop->preplanned && !(pop->preplanned->shape < shape) &&
                          !(shape < pop->preplanned->shape);
         if (pre) pl->hp = std::move(pop->preplanned->plan);
-        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr, &c->par, columns_on(c) && !cached);
+        else build_plan(pop->ir, shape, pl->hp, cached ? cv : nullptr, &c->par, columns_on(c));
         pop->preplanned.reset();
         if (cached) {
             pl->view = *cv;
@@ -407,7 +424,7 @@ int get_plan_shape(tgp_ctx* c, Population* pop, PlanShape shape, bool pheno, cud
         if (cached) {
             // the bytecode depends only on the view; entry pointers may differ
             if (pl->view.cached != cv->cached || pl->view.insert != cv->insert) {
-                build_plan(pop->ir, shape, pl->hp, cv, &c->par);
+                build_plan(pop->ir, shape, pl->hp, cv, &c->par, columns_on(c));
                 pl->view = *cv;
             }
             pl->h_table = *table;
@@ -685,9 +702,9 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         return fail(TGP_E_INVALID, "plan for %lld points in rows of %lld used on a %d x %d grid",
                     (long long)hp.shape.N, (long long)hp.shape.W, d->W, d->H);
     EvalParams p{};
-    p.code = pl->code.p;
-    p.group_off = pl->group_off.p;
-    p.item_group = pl->group_order.p;
+    p.code = pl->prog.code;
+    p.group_off = pl->prog.group_off;
+    p.item_group = pl->prog.group_order;
     p.n_items = hp.n_items;
     p.n_tiles = hp.n_tiles;
     p.warps_per_tile = hp.shape.threads / 32;
@@ -734,9 +751,9 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         // W points (same x coordinates; no y below them)
         const HostPlan& ch = *hp.col_plan;
         EvalParams q{};
-        q.code = pl->ccode.p;
-        q.group_off = pl->cgroup_off.p;
-        q.item_group = pl->cgroup_order.p;
+        q.code = pl->cprog.code;
+        q.group_off = pl->cprog.group_off;
+        q.item_group = pl->cprog.group_order;
         q.n_items = ch.n_items;
         q.n_tiles = ch.n_tiles;
         q.warps_per_tile = ch.shape.threads / 32;
@@ -761,9 +778,9 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         // points (same y coordinates; no x below them)
         const HostPlan& rh = *hp.row_plan;
         EvalParams q{};
-        q.code = pl->rcode.p;
-        q.group_off = pl->rgroup_off.p;
-        q.item_group = pl->rgroup_order.p;
+        q.code = pl->rprog.code;
+        q.group_off = pl->rprog.group_off;
+        q.item_group = pl->rprog.group_order;
         q.n_items = rh.n_items;
         q.n_tiles = rh.n_tiles;
         q.warps_per_tile = rh.shape.threads / 32;

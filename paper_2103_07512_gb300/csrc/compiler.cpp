@@ -909,15 +909,18 @@ constexpr float kColMinCost = 4.f;
 constexpr size_t kColMaxEntries = 16384;
 
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns);
+                            const ParallelFor* par, bool columns, bool table_plan);
 
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
                 const ParallelFor* par, bool columns) {
-    build_plan_impl(PlanPop{pop.dag, pop.roots, pop.tree_cost, pop.tree_nodes}, shape, plan, cv, par, columns);
+    build_plan_impl(PlanPop{pop.dag, pop.roots, pop.tree_cost, pop.tree_nodes}, shape, plan, cv, par, columns,
+                    false);
 }
 
+// table_plan: the plan of column or row tables (their subtrees in id order:
+// the ordering pass would cost more than it saves on these small launches).
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns) {
+                            const ParallelFor* par, bool columns, bool table_plan) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -929,6 +932,9 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     // (sorted by their most expensive subtree that another tree also uses),
     // then the order is cut into G contiguous groups of balanced cost.
     // distinct internal nodes of each tree (flat, tree t at [tree_at[t], tree_at[t+1]))
+    std::vector<int32_t> order(T);
+    std::iota(order.begin(), order.end(), 0);
+    if (!table_plan) {
     std::vector<int32_t> tree_uses(pop.dag.size(), 0), seen(pop.dag.size(), -1);
     std::vector<int32_t> stack, tree_nodes, tree_at(T + 1, 0);
     tree_nodes.reserve((size_t)std::min<int64_t>(pop.tree_nodes, (int64_t)1 << 26));
@@ -956,12 +962,11 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             if (tree_uses[n] >= 2 && c > key_cost[t]) { key_cost[t] = c; key[t] = n; }
         }
     }
-    std::vector<int32_t> order(T);
-    std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         if (key[a] != key[b]) return key[a] > key[b];
         return a < b;
     });
+    }
     double total = 0;
     for (int64_t t = 0; t < T; ++t) total += pop.tree_cost[t] + 1.0;
     std::vector<std::vector<int32_t>> groups(G);
@@ -1000,18 +1005,26 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     // tables' own plans are phenotype launches on one row of W points and on
     // one column of H points.
     std::vector<int32_t> col, row;
+    std::vector<std::function<void()>> table_builds;   // run beside the groups' planning
     const int64_t W = shape.W > 0 ? shape.W : shape.N;
     const int64_t H = W > 0 ? shape.N / W : 0;
-    if (columns && !(cv && cv->active()) && W > 1 && H > 1) {
+    if (columns && W > 1 && H > 1) {
         const size_t nn = pop.dag.size();
-        std::vector<uint8_t> yfree(nn, 0), celig(nn, 0), relig(nn, 0), cneed(nn, 0), rneed(nn, 0);
+        const bool cview = cv && cv->active();
+        std::vector<uint8_t> yfree(nn, 0), celig(nn, 0), relig(nn, 0), cneed(nn, 0), rneed(nn, 0), blocked(nn, 0);
         for (size_t n = 0; n < nn; ++n) {
             const DagNode& d = pop.dag.nodes[n];
             bool f = d.op != T_Y;
+            // a subtree holding a cache load or store is evaluated in this plan
+            bool b = cview && (cv->cached[n] >= 0 || cv->insert[n] >= 0);
             for (int c = 0; c < kMaxKids; ++c)
-                if (d.kid[c] >= 0) f = f && yfree[d.kid[c]];
+                if (d.kid[c] >= 0) {
+                    f = f && yfree[d.kid[c]];
+                    b = b || blocked[d.kid[c]];
+                }
             yfree[n] = f;
-            const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost;
+            blocked[n] = b;
+            const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost && !b;
             celig[n] = costly && f && !xfree[n];
             relig[n] = costly && xfree[n];
         }
@@ -1049,12 +1062,19 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             // one row: K points of it per thread; one column: a point per thread
             ts.K = row_len == 1 ? 1 : n_points >= (1 << 14) ? 4 : n_points >= (1 << 12) ? 2 : 1;
             ts.dedup = shape.dedup;
+            // a small launch: about two items per SM, and at most 8 subtrees
+            // a group (each group is a planner pass on the host; many tables
+            // are planned on the workers)
             const int64_t tiles = (n_points + ts.K * ts.threads - 1) / (ts.K * ts.threads);
-            const int64_t want = 152 * 64;
-            ts.n_groups = (int)std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles,
-                                                                     (int64_t)roots.size()));
+            const int64_t R = (int64_t)roots.size();
+            ts.n_groups = (int)std::max<int64_t>(
+                1, std::min<int64_t>(R, std::max<int64_t>((152 * 2 + tiles - 1) / tiles, (R + 7) / 8)));
             tplan = std::make_shared<HostPlan>();
-            build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tplan, nullptr, par, false);
+            HostPlan* tp = tplan.get();
+            const bool big = R >= 256;
+            table_builds.push_back([&pop, &roots, costs, ts, tp, par, big]() {
+                build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tp, nullptr, big ? par : nullptr, false, true);
+            });
         };
         make_tables(cneed, col, plan.col_roots, plan.col_plan, plan.col_stride, W, W);
         make_tables(rneed, row, plan.row_roots, plan.row_plan, plan.row_stride, H, 1);
@@ -1066,21 +1086,37 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
     plan.group_off.push_back(0);
     if (par && *par && G > 1 && !(cv && cv->active())) {
-        std::vector<std::vector<IrIns>> part(G);
-        std::vector<int> slots(G, 0);
-        (*par)(G, [&](int g) {
-            GroupGen gen(pop.dag, part[g], shape.dedup, budget, nullptr, &xfree, colp, rowp);
-            slots[g] = plan_group(gen, part[g], pop, groups[g], budget);
+        // contiguous runs of groups, one planner (and its per-node arrays)
+        // each, and the tables' plans as tasks of their own
+        const int P = std::min(G, 16);
+        const int NT = (int)table_builds.size();
+        std::vector<std::vector<IrIns>> part(P);
+        std::vector<std::vector<int64_t>> ends(P);
+        std::vector<int> slots(P, 0);
+        (*par)(P + NT, [&](int t) {
+            if (t < NT) {
+                table_builds[t]();
+                return;
+            }
+            t -= NT;
+            const int g0 = (int)((int64_t)G * t / P), g1 = (int)((int64_t)G * (t + 1) / P);
+            GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, &xfree, colp, rowp);
+            for (int g = g0; g < g1; ++g) {
+                slots[t] = std::max(slots[t], plan_group(gen, part[t], pop, groups[g], budget));
+                ends[t].push_back((int64_t)part[t].size());
+            }
         });
         size_t total_ins = 0;
         for (const auto& v : part) total_ins += v.size();
         plan.ir.reserve(total_ins);
-        for (int g = 0; g < G; ++g) {
-            plan.ir.insert(plan.ir.end(), part[g].begin(), part[g].end());
-            plan.n_slots = std::max(plan.n_slots, slots[g]);
-            plan.group_off.push_back((int64_t)plan.ir.size());
+        for (int t = 0; t < P; ++t) {
+            const int64_t base = (int64_t)plan.ir.size();
+            plan.ir.insert(plan.ir.end(), part[t].begin(), part[t].end());
+            plan.n_slots = std::max(plan.n_slots, slots[t]);
+            for (int64_t e : ends[t]) plan.group_off.push_back(base + e);
         }
     } else {
+        for (auto& b : table_builds) b();
         GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree, colp, rowp);
         for (int g = 0; g < G; ++g) {
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));

@@ -150,9 +150,9 @@ using ParallelFor = std::function<void(int n, const std::function<void(int)>& bo
 // depends on its own trees only, so the result is the same); a cache view
 // keeps the planning serial (a node is stored by the first group that
 // evaluates it).
-// With `columns` (and no cache view, on a grid of at least two rows and two
-// columns), the costly subtrees that have x but no y below them become column
-// tables, and those with no x below them row tables.
+// With `columns` (on a grid of at least two rows and two columns), the costly
+// subtrees that have x but no y below them become column tables, and those
+// with no x below them row tables (none holding a node of the cache view).
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv = nullptr,
                 const ParallelFor* par = nullptr, bool columns = false);
 

@@ -236,8 +236,11 @@ def main(argv=None):
     ap.add_argument("--device", type=int, default=0)
     ap.add_argument("--variation", choices=("host", "library"), default="host",
                     help="selection and variation in Python (host) or in the library on the DAG (library)")
+    ap.add_argument("--no-tables", action="store_true",
+                    help="evaluate every subtree at every point (no column or row tables)")
     a = ap.parse_args(argv)
-    with Context(device=a.device, cache_budget_bytes=int(a.cache_gb * 1e9), cache_min_cost=a.min_cost) as ctx:
+    with Context(device=a.device, cache_budget_bytes=int(a.cache_gb * 1e9), cache_min_cost=a.min_cost,
+                 columns=not a.no_tables) as ctx:
         dom = ctx.load_domain(a.grid, a.grid)
         if a.variation == "library":
             ev = DeviceEvolution(ctx, dom, pop_size=a.population, generations=a.generations, seed=a.seed)

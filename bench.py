@@ -325,7 +325,12 @@ def run_ours(args):
                      "traffic": traffic, "kernel_ms": kern_ms,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal unit counts and max clock)",
                      "op_costs": {I.NAMES[i]: round(float(costs[i]), 3) for i in range(len(costs))},
-                     "frac_one_op_per_node": (units / (kern_ms * 1e-3) / 1e12) / peak_tops},
+                     "frac_one_op_per_node": (units / (kern_ms * 1e-3) / 1e12) / peak_tops,
+                     "work_note": "achieved counts the work the trees describe (tree nodes as given x points x "
+                                  "op cost) over the time of the step's launches (the column and row table "
+                                  "launches included); the launches evaluate less: shared subtrees once, "
+                                  "exactly simplified trees, values with no x below them once per thread, "
+                                  "subtrees with no y (no x) below them once per grid column (row)"},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{cpu_info['rows']} of {g.H} rows ({cpu_info['points']} points), all trees, "
                                    f"{cpu_info['seconds']:.1f} s"},

@@ -541,9 +541,29 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     bool any = false;
     for (size_t n = 0; n < n_nodes && !any; ++n) any = ir.dag.nodes[n].cost >= min_cost;
     if (!any) return TGP_OK;
+    // With tables, a subtree with no x or no y below it is evaluated once per
+    // thread, row or column: cheaper than storing and reloading it, so the
+    // cache holds only subtrees of both coordinates.
+    std::vector<uint8_t> flat;
+    if (columns_on(c) && d->W > 1 && d->H > 1) {
+        std::vector<uint8_t> nx(n_nodes, 0), ny(n_nodes, 0);
+        flat.assign(n_nodes, 0);
+        for (size_t n = 0; n < n_nodes; ++n) {
+            const DagNode& dn = ir.dag.nodes[n];
+            bool a = dn.op != T_X, b = dn.op != T_Y;
+            for (int k = 0; k < kMaxKids; ++k)
+                if (dn.kid[k] >= 0) {
+                    a = a && nx[dn.kid[k]];
+                    b = b && ny[dn.kid[k]];
+                }
+            nx[n] = a;
+            ny[n] = b;
+            flat[n] = a || b;
+        }
+    }
     if (!d->cache.empty()) {
         for (size_t n = 0; n < n_nodes; ++n) {
-            if (ir.dag.nodes[n].cost < min_cost) continue;
+            if (ir.dag.nodes[n].cost < min_cost || (!flat.empty() && flat[n])) continue;
             auto it = d->cache.find(pop->gid[n]);
             if (it != d->cache.end() && entry_ready(it->second.get())) {
                 cv.cached[n] = (int32_t)table.size();
@@ -558,7 +578,7 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     std::vector<int32_t> cand;
     if (d->seen.size() > kCacheSeenMax) d->seen.clear();
     for (int32_t n : evaluated_nodes(ir, cv)) {
-        if (ir.dag.nodes[n].cost < min_cost) continue;
+        if (ir.dag.nodes[n].cost < min_cost || (!flat.empty() && flat[n])) continue;
         const int32_t g = pop->gid[n];
         if (d->cache.count(g)) continue;   // stored by a launch still running
         if (d->seen.insert(g).second) continue;   // first evaluation here

@@ -435,6 +435,17 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
     g = I.Grid(4096, 4096)
     out = {}
     rows = {}
+    # untimed: the first launches of each kernel variant load it (lazy module
+    # loading), which would otherwise be charged to the first arm
+    for lib in (False, True):
+        ctx = ctx_cls(device=dev.index)
+        dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+        ev = (DeviceEvolution(ctx, dom, pop_size=50, generations=3, seed=3) if lib else
+              Evolution(gpu_fitness(ctx, dom), pop_size=50, generations=3, seed=3))
+        ev.run()
+        if lib:
+            ev.close()
+        ctx.close()
     for arm, b, mc in (("cache", budget, 0), ("cache_min_cost_8", budget, 8), ("no_cache", 0, 0),
                        ("library_variation", budget, 0), ("library_variation_no_cache", 0, 0)):
         ctx = ctx_cls(device=dev.index, cache_budget_bytes=b, cache_min_cost=mc)

@@ -156,7 +156,9 @@ typedef struct tgp_config {
     int32_t threads_per_block;   /* 0 = automatic; else 32, 64 or 128 */
     int32_t n_groups;            /* 0 = automatic; else trees are split into this many groups */
     int32_t cache_min_cost;      /* subtrees cheaper than this (per point, a binary32 add = 1) are
-                                    never stored in the cache; 0 = 48 */
+                                    never stored in the cache; 0 = 48.  With column and row tables,
+                                    a subtree with no x or no y below it is never stored and counts
+                                    as one add in the cost of the subtrees above it. */
     int32_t plan_threads;        /* host threads that plan a population's tree groups
                                     concurrently (the calling thread included); 0 = up to 8,
                                     1 = serial.  The bytecode does not depend on it. */

@@ -538,32 +538,43 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     // Every stored subtree costs at least min_cost, so cheaper nodes are
     // neither looked up nor candidates.
     const float min_cost = (float)(c->cfg.cache_min_cost > 0 ? c->cfg.cache_min_cost : kCacheMinCost);
-    bool any = false;
-    for (size_t n = 0; n < n_nodes && !any; ++n) any = ir.dag.nodes[n].cost >= min_cost;
-    if (!any) return TGP_OK;
-    // With tables, a subtree with no x or no y below it is evaluated once per
-    // thread, row or column: cheaper than storing and reloading it, so the
-    // cache holds only subtrees of both coordinates.
-    std::vector<uint8_t> flat;
-    if (columns_on(c) && d->W > 1 && d->H > 1) {
-        std::vector<uint8_t> nx(n_nodes, 0), ny(n_nodes, 0);
-        flat.assign(n_nodes, 0);
+    // Per-point cost of each node.  With tables, a subtree with no x or no y
+    // below it is evaluated once per thread, row or column and read back at
+    // about the cost of one operation: such subtrees are never stored (a
+    // table is cheaper than a stored copy) and count as one operation in the
+    // cost of the subtrees above them.
+    std::vector<float> cost(n_nodes);
+    std::vector<uint8_t> flat(n_nodes, 0);
+    const bool tables = columns_on(c) && d->W > 1 && d->H > 1;
+    {
+        std::vector<uint8_t> nx(tables ? n_nodes : 0), ny(tables ? n_nodes : 0);
         for (size_t n = 0; n < n_nodes; ++n) {
             const DagNode& dn = ir.dag.nodes[n];
+            if (!tables) {
+                cost[n] = dn.cost;
+                continue;
+            }
             bool a = dn.op != T_X, b = dn.op != T_Y;
+            float w = op_cost(dn.op);
             for (int k = 0; k < kMaxKids; ++k)
                 if (dn.kid[k] >= 0) {
                     a = a && nx[dn.kid[k]];
                     b = b && ny[dn.kid[k]];
+                    w += cost[dn.kid[k]];
                 }
             nx[n] = a;
             ny[n] = b;
             flat[n] = a || b;
+            cost[n] = flat[n] ? std::min(w, 1.f) : w;
         }
     }
+    auto eligible = [&](size_t n) { return cost[n] >= min_cost && !flat[n]; };
+    bool any = false;
+    for (size_t n = 0; n < n_nodes && !any; ++n) any = eligible(n);
+    if (!any) return TGP_OK;
     if (!d->cache.empty()) {
         for (size_t n = 0; n < n_nodes; ++n) {
-            if (ir.dag.nodes[n].cost < min_cost || (!flat.empty() && flat[n])) continue;
+            if (!eligible(n)) continue;
             auto it = d->cache.find(pop->gid[n]);
             if (it != d->cache.end() && entry_ready(it->second.get())) {
                 cv.cached[n] = (int32_t)table.size();
@@ -578,14 +589,14 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
     std::vector<int32_t> cand;
     if (d->seen.size() > kCacheSeenMax) d->seen.clear();
     for (int32_t n : evaluated_nodes(ir, cv)) {
-        if (ir.dag.nodes[n].cost < min_cost || (!flat.empty() && flat[n])) continue;
+        if (!eligible(n)) continue;
         const int32_t g = pop->gid[n];
         if (d->cache.count(g)) continue;   // stored by a launch still running
         if (d->seen.insert(g).second) continue;   // first evaluation here
         cand.push_back(n);
     }
     std::stable_sort(cand.begin(), cand.end(),
-                     [&](int32_t a, int32_t b) { return ir.dag.nodes[a].cost > ir.dag.nodes[b].cost; });
+                     [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
     const int64_t budget = c->cfg.cache_budget_bytes;
     const int64_t quota = std::min<int64_t>(kCacheMaxInsertsPerCall,
                                             std::max<int64_t>(budget / 4 / bytes, budget >= bytes ? 1 : 0));
@@ -609,7 +620,7 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
                 victims_listed = true;
                 std::unordered_set<int32_t> referenced;
                 for (size_t n = 0; n < n_nodes; ++n)
-                    if (ir.dag.nodes[n].cost >= min_cost) referenced.insert(pop->gid[n]);
+                    if (eligible(n)) referenced.insert(pop->gid[n]);
                 for (auto& dk : c->domains)
                     for (auto& kv : dk.second->cache)
                         if ((dk.second.get() != d || !referenced.count(kv.first)) && entry_ready(kv.second.get())) {
@@ -647,7 +658,7 @@ int prepare_cache(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, CacheV
         }
         c->cache_bytes += (int64_t)e->cap * (int64_t)sizeof(float);
         const int32_t n = cand[i];
-        e->cost = ir.dag.nodes[n].cost;
+        e->cost = cost[n];
         e->last_use = c->epoch;
         cv.insert[n] = (int32_t)table.size();
         table.push_back(e->values);

@@ -119,3 +119,29 @@ def test_non_blocking_calls_with_entries_in_flight():
         s.synchronize()
         for o in outs:
             assert np.array_equal(o.cpu().numpy().view(np.int64), ref.view(np.int64))
+
+
+@pytest.mark.parametrize("columns", [True, False])
+def test_tabled_subtrees_are_not_stored(columns):
+    """With column and row tables, a subtree with no x or no y below it is
+    tabled, never stored, and counts as one add in the cost of the subtrees
+    above it: add(A(x), B(y)) costs 3 there (A and B cost 49 each as trees),
+    so with a store threshold of 4 only cos(add(x, y)) and sin(cos(add(x,
+    y))) are stored.  Without tables every subtree of cost >= 4 is."""
+    exprs = ["sin(cos(sin(mult(x, x))))", "cos(sin(cos(mult(y, y))))",
+             "add(sin(cos(sin(mult(x, x)))), cos(sin(cos(mult(y, y)))))", "sin(cos(add(x, y)))"]
+    tok = I.to_tokens([I.parse_string(e) for e in exprs])
+    g = I.Grid(160, 96)
+    with tgp.Context(cache_budget_bytes=64 * g.N * 4, cache_min_cost=4, columns=columns) as a, \
+            tgp.Context(columns=columns) as b:
+        da, db = a.load_domain(g.W, g.H), b.load_domain(g.W, g.H)
+        pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+        ref = b.fitness(pb, db, tok.n_trees)
+        for _ in range(3):      # seen, stored, loaded
+            got = a.fitness(pa, da, tok.n_trees)
+            assert np.array_equal(got.view(np.int64), ref.view(np.int64))
+        st = a.stats()
+    if columns:
+        assert st["cache_inserts"] == 2 and st["cache_hits"] == 2, st
+    else:
+        assert st["cache_inserts"] == 9 and st["cache_hits"] == 9, st

@@ -378,6 +378,7 @@ def bench_batched(ctx_cls, dev, flush, steps=20):
     torch.cuda.synchronize()
     s0 = ctx.stats()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.nvtx.range_push("timed")                    # profilers can select the timed steps
     for i in range(steps):
         flush.fill_(float(i))
         stream.wait_stream(torch.cuda.current_stream(dev))
@@ -385,6 +386,7 @@ def bench_batched(ctx_cls, dev, flush, steps=20):
         ctx.fitness_graph(pop, dom, rmse, stream=stream)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     s1 = ctx.stats()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     units = int(tok.ops.size) * g.N
@@ -580,9 +582,19 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, evolution and serving measurements")
+    ap.add_argument("--only", choices=["batched_uneven"],
+                    help="measure one other configuration alone and print its line (for profiling it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        import paper_2103_07512_gb300 as tgp
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+        print(json.dumps({"config": args.only, **bench_batched(tgp.Context, dev, flush, steps=args.steps)}))
+        return 0
     return run_ours(args)
 
 

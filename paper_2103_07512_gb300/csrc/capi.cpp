@@ -153,6 +153,7 @@ struct Plan {
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;   // kernel launches the graph holds
     ~GraphEntry() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -1279,6 +1280,7 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
         int64_t before = ctx->stats.launches;
         rc = launch_fitness(ctx, p, pl, d, s, rmse_dev);
         ctx->capturing = false;
+        ge->kernels = ctx->stats.launches - before;
         ctx->stats.launches = before;   // counted when the graph is launched
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(s, &graph);
@@ -1292,7 +1294,7 @@ int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* str
         it = p->graphs.emplace(key, std::move(ge)).first;
     }
     CUDA_TRY(cudaGraphLaunch(it->second->exec, s));
-    ctx->stats.launches += 2;
+    ctx->stats.launches += it->second->kernels;
     return TGP_OK;
 }
 

@@ -109,3 +109,25 @@ def test_table_launches_are_counted(expr, extra):
             run(c, tok, g)
         # phenotype and fitness, each with a column and / or a row pass where there are tables
         assert a.stats()["launches"] == b.stats()["launches"] + extra
+
+
+def test_graph_replays_count_their_table_launches():
+    # a column and a row table: two table launches, the interpreter and the
+    # finalize kernel in every replay, as in a direct call
+    tok = I.to_tokens([I.parse_string("mult(sin(x), cos(y))")])
+    g = I.Grid(64, 64)
+    with tgp.Context() as c:
+        dom = c.load_domain(g.W, g.H)
+        pop = c.compile_tokens(tok)
+        st = torch.cuda.Stream()
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        c.fitness_graph(pop, dom, out, stream=st)      # captured, then launched
+        n0 = c.stats()["launches"]
+        for _ in range(3):
+            c.fitness_graph(pop, dom, out, stream=st)
+        n1 = c.stats()["launches"]
+        c.fitness_dev(pop, dom, out, stream=st)
+        st.synchronize()
+        n2 = c.stats()["launches"]
+    assert n2 - n1 == 4
+    assert n1 - n0 == 3 * 4

@@ -190,7 +190,8 @@ typedef struct tgp_stats {
     int64_t cache_hits;       /* subtree loads served from the cache */
     int64_t cache_inserts;
     int64_t cache_evictions;
-    int64_t launches;         /* kernels launched by the library so far */
+    int64_t launches;         /* kernels launched by the library so far (a graph replay counts
+                                 the kernels it holds) */
     double eval_ms_sum;       /* TGP_F_TIME_KERNELS: summed interpreter kernel time */
     int64_t eval_timed;       /* TGP_F_TIME_KERNELS: launches summed in eval_ms_sum */
     int64_t cache_reserved;   /* HBM reserved for the cache (slabs carved into entries; at most

@@ -23,7 +23,7 @@
  *   - Pagie polynomial target: Eq. 1;
  *   - RMSE fitness against the target: Sec. 4.1 and Table 2.
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Table 1 prints sin and cos swapped; the prose of Sec. 3.2 is followed:
  *     sin(a) := sin(pi*a), cos(a) := cos(pi*a).
  *   - The grid placement is not printed: inclusive linspace, x along columns,
@@ -72,9 +72,13 @@
  *   a / b:   P = (Ea + |a/b| Eb) / (|b| - Eb), unbounded if |b| <= Eb (the
  *            sign or zero test of the denominator is then undecided); 0 for
  *            an exact zero denominator (the protected result is exactly 0)
- *   sin/cos(pi a): P = min(pi Ea, 2), plus 2 ulp of the result (radians:
- *            P = min(Ea, 2); tan likewise with pi replaced by 1)
- *   -a, |a|: Ea;  min/max: max(Ea, Eb)
+ *   sin(pi a): P = min(pi Ea |cos(pi a)| + (pi Ea)^2 / 2, 2) (Taylor's
+ *            theorem: the first derivative at a, and |second| <= pi^2 on the
+ *            interval); cos(pi a) likewise with |sin(pi a)|; plus 2 ulp of
+ *            the result (radians: pi replaced by 1; tan likewise)
+ *   -a, |a|: Ea;  min/max: the error of the operand taken when the two are
+ *            further apart than Ea + Eb (the comparison is then decided),
+ *            else max(Ea, Eb)
  *   tan(pi a): P = pi Ea / (|c| - pi Ea)^2 with c = cos(pi a), unbounded if
  *            |c| <= pi Ea; plus 4 ulp (a quotient of two trig values)
  *   exp(a): P = |v| (e^Ea - 1), plus 2 ulp
@@ -499,15 +503,19 @@ static double err_bound(int op, double a, double b, double c, double ea, double 
         prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);
         e = prop + rnd32(v, prop, 0);
         break;
-    case O_SIN: case O_COS:
-        prop = fmin(k * ea, 2.0);
+    case O_SIN: case O_COS: {
+        /* |derivative| at a, over k: |cos| for sin, |sin| for cos */
+        double slope = op == O_SIN ? fabs(rad ? cos(a) : oracle_cospi(a)) : fabs(rad ? sin(a) : oracle_sinpi(a));
+        prop = fmin(k * ea * slope + 0.5 * (k * ea) * (k * ea), 2.0);
         e = prop + TRIG_ULPS * (2.0 * U32 * (fabs(v) + prop) + TINY32);
         break;
+    }
     case O_NEG: case O_ABS:
         e = ea;
         break;
     case O_MIN: case O_MAX:
-        e = fmax(ea, eb);
+        if (fabs(a - b) > ea + eb) e = (v == a) ? ea : eb;   /* decided comparison: the taken operand */
+        else e = fmax(ea, eb);
         break;
     default:
         return INFINITY;

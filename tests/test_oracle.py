@@ -407,8 +407,8 @@ def test_error_bound_trig_and_division():
     _, _, _, eb = ev_bound(["sin(x)", "sin(add(x, y))", "div(1.0, add(x, 0.3))"], W, H)
     # exact argument: only the 2-ulp allowance of the function
     assert np.all(eb[0] <= 2 * (2 * U32 * np.abs(np.sin(np.pi * X)) + 2.0 ** -149) * (1 + 1e-12))
-    # rounded argument: pi * E(arg) is propagated
-    assert np.all(eb[1] >= np.pi * U32 * np.abs(X + Y) * (1 - 1e-12))
+    # rounded argument: pi |cos(pi a)| E(arg) is propagated
+    assert np.all(eb[1] >= np.pi * U32 * np.abs(X + Y) * np.abs(np.cos(np.pi * (X + Y))) * (1 - 1e-12))
     b = X + np.float32(0.3).astype(np.float64)
     exp = (1.0 * U32 * np.abs(b) / np.abs(b) ** 2) / (1 - U32)   # Eb/|b|^2 leading term
     assert np.all(eb[2] >= exp * 0.99)
@@ -422,6 +422,71 @@ def test_error_bound_unbounded_cases():
     assert np.all(np.isfinite(eb[1]))
     # binary32 overflow
     assert np.all(~np.isfinite(eb[2][[0, 2, 6, 8]]))
+
+
+def _hulp(r):
+    """Half the binary32 spacing at |r| (normal range): the largest error of
+    one correctly rounded binary32 operation whose exact result is r."""
+    m, e = np.frexp(np.abs(np.asarray(r, np.float64)))
+    return np.ldexp(1.0, e - 25)
+
+
+# first-order worst case of a binary32 evaluation of each one- and
+# two-operator tree, written from the derivatives of the tree (each rounding
+# at most half an ulp, sin/cos(pi a) at most 2 ulp): (expression, worst case,
+# mask of the elements where it applies)
+def _worst_cases(X, Y):
+    pi = np.pi
+    s, p, d, q = X + Y, X * Y, X - Y, X / Y
+    sx, cy = np.sin(pi * X), np.cos(pi * Y)
+    c03 = float(np.float32(0.3))
+    with np.errstate(all="ignore"):
+        cases = [
+            ("add(x, y)", _hulp(s), np.ones_like(s, bool)),
+            ("sub(x, y)", _hulp(d), np.ones_like(s, bool)),
+            ("mult(x, y)", _hulp(p), np.ones_like(s, bool)),
+            ("div(x, y)", _hulp(q), np.abs(Y) > 1e-3),
+            ("add(x, 0.3)", _hulp(X + c03), np.ones_like(s, bool)),
+            ("sin(x)", 4 * _hulp(sx), np.ones_like(s, bool)),
+            ("cos(y)", 4 * _hulp(cy), np.ones_like(s, bool)),
+            ("neg(add(x, y))", _hulp(s), np.ones_like(s, bool)),
+            ("abs(sub(x, y))", _hulp(d), np.ones_like(s, bool)),
+            ("sin(add(x, y))", pi * np.abs(np.cos(pi * s)) * _hulp(s) + 4 * _hulp(np.sin(pi * s)),
+             np.ones_like(s, bool)),
+            ("cos(mult(x, y))", pi * np.abs(np.sin(pi * p)) * _hulp(p) + 4 * _hulp(np.cos(pi * p)),
+             np.ones_like(s, bool)),
+            ("mult(add(x, y), x)", np.abs(X) * _hulp(s) + _hulp(s * X), np.ones_like(s, bool)),
+            ("div(x, add(x, y))", np.abs(X / s ** 2) * _hulp(s) + _hulp(X / s), np.abs(s) > 1e-3),
+            ("sub(sin(x), y)", 4 * _hulp(sx) + _hulp(sx - Y), np.ones_like(s, bool)),
+            ("add(mult(x, x), y)", _hulp(X * X) + _hulp(X * X + Y), np.ones_like(s, bool)),
+            ("div(sin(x), y)", 4 * _hulp(sx) / np.abs(Y) + _hulp(sx / Y), np.abs(Y) > 1e-3),
+            ("mult(sin(x), cos(y))", np.abs(cy) * 4 * _hulp(sx) + np.abs(sx) * 4 * _hulp(cy) + _hulp(sx * cy),
+             np.ones_like(s, bool)),
+            # the comparison decided with a margin: the taken operand's error
+            ("min(add(x, y), mult(x, y))", np.where(s < p, _hulp(s), _hulp(p)),
+             np.abs(s - p) > 4 * 2.0 ** -24 * (np.abs(s) + np.abs(p))),
+            ("max(sin(x), cos(y))", np.where(sx > cy, 4 * _hulp(sx), 4 * _hulp(cy)),
+             np.abs(sx - cy) > 16 * 2.0 ** -24 * (np.abs(sx) + np.abs(cy))),
+        ]
+    return cases
+
+
+@pytest.mark.parametrize("W,H,lo,hi", [(37, 29, -5.0, 5.0), (23, 31, -0.9, 0.9), (16, 16, -3.0, 1.75)])
+def test_error_bound_is_tight_on_one_and_two_operator_trees(W, H, lo, hi):
+    """The bound is no looser than twice the first-order worst case of a
+    binary32 evaluation of the tree, and no tighter than it (each term of the
+    bound is at least the matching worst-case term and below twice it)."""
+    X, Y = np_grid(W, H, lo, hi)
+    cases = _worst_cases(X, Y)
+    v64, _, _, eb = ev_bound([c[0] for c in cases], W, H, lo, hi)
+    for i, (expr, worst, mask) in enumerate(cases):
+        m = mask & np.isfinite(eb[i]) & (np.abs(v64[i]) > 1e-30) & (worst > 0)
+        # exact zeros of sin/cos(pi a) at integer or half-integer arguments have no ulp
+        m &= np.abs(X) > 0
+        assert m.mean() > 0.5, expr
+        ratio = eb[i][m] / worst[m]
+        assert ratio.min() >= 1 - 1e-6, (expr, ratio.min())
+        assert ratio.max() <= 2 + 1e-4, (expr, ratio.max())
 
 
 def ev_bound(exprs, W, H, lo=-5.0, hi=5.0):
@@ -638,8 +703,8 @@ def test_radian_error_bound_contains_fp32_faithful_and_propagates():
     W, H = 5, 3
     X, Y = np_grid(W, H)
     _, _, _, e = ev_rad(["sin(add(x, y))", "sin(x)"], W, H, with_bound=True)
-    # rounded argument: |cos| <= 1, so E(arg) itself is propagated (not pi E(arg))
-    assert np.all(e[0] >= U32 * np.abs(X + Y) * (1 - 1e-12))
+    # rounded argument: |cos(a)| E(arg) is propagated (not pi |cos(pi a)| E(arg))
+    assert np.all(e[0] >= U32 * np.abs(X + Y) * np.abs(np.cos(X + Y)) * (1 - 1e-12))
     assert np.all(e[0] < np.pi * U32 * np.abs(X + Y) + 4 * (2 * U32 + 2.0 ** -149))
     assert np.all(e[1] <= 2 * (2 * U32 * np.abs(np.sin(X)) + 2.0 ** -149) * (1 + 1e-12))
 

@@ -53,6 +53,19 @@ MUTANTS = {
     "mdist_not_halved": ("case O_MDIST: return (a + b) / 2.0;", "case O_MDIST: return a + b;"),
     "sign_of_zero_is_one": ("if (a == 0.0) return 0.0;\n    return a;", "if (a == 0.0) return 1.0;\n    return a;"),
     "bound_exp_no_propagation": ("prop = fabs(v) * expm1(ea);", "prop = 0.0;"),
+    # bounds inflated: the tightness pins (twice the first-order worst case) must catch them
+    "bound_rounding_doubled": ("double e = U32 * m;", "double e = 2.0 * U32 * m;"),
+    "bound_trig_four_ulps": ("#define TRIG_ULPS 2.0", "#define TRIG_ULPS 4.0"),
+    "bound_trig_lipschitz_one": ("prop = fmin(k * ea * slope + 0.5 * (k * ea) * (k * ea), 2.0);",
+                                 "prop = fmin(k * ea + 0.5 * (k * ea) * (k * ea), 2.0);"),
+    "bound_mul_inflated": ("prop = fabs(b) * ea + fabs(a) * eb + ea * eb;",
+                           "prop = 2.0 * (fabs(b) * ea + fabs(a) * eb) + ea * eb;"),
+    "bound_div_inflated": ("prop = (ea + fabs(a / b) * eb) / (fabs(b) - eb);",
+                           "prop = 2.0 * (ea + fabs(a / b) * eb) / (fabs(b) - eb);"),
+    "bound_add_inflated": ("case O_ADD: case O_SUB:\n        prop = ea + eb;",
+                           "case O_ADD: case O_SUB:\n        prop = 2.0 * (ea + eb);"),
+    "bound_minmax_always_max": ("if (fabs(a - b) > ea + eb) e = (v == a) ? ea : eb;", "if (0) e = ea;"),
+    "bound_neg_inflated": ("case O_NEG: case O_ABS:\n        e = ea;", "case O_NEG: case O_ABS:\n        e = 2.0 * ea;"),
     "const_imm_order": ("nodes[me].imm = (double)imm[(*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {",
                         "nodes[me].imm = (double)imm[n_imm - 1 - (*imm_pos)++];\n    }\n    for (int c = 0; c < ar; c++) {"),
 }

@@ -256,8 +256,12 @@ int tgp_evaluate(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, 
  * RMSE fitness of every tree against the domain's target (Sec. 4.1):
  *   rmse[t] = sqrt( sum_p (f_t(p) - target(p))^2 / (H*W) ),
  * +inf when the sum is not finite.  Residuals are formed and squared in
- * binary32; per-warp partial sums are added in binary64 in a fixed order, so
- * results are bitwise reproducible.
+ * binary32 and summed in binary32 over a warp's points (a thread's K points,
+ * then a butterfly over the 32 threads: at most 512 squares, relative error
+ * below 2^-19); a sum that would overflow binary32 is formed from
+ * residuals scaled by 2^-80.  The per-warp partials are added in binary64 in
+ * a fixed order, so results are bitwise reproducible, and finite whenever
+ * every element is.
  * rmse_host: host array of n_trees doubles.  blocking != 0: returns after the
  * values are in rmse_host.  blocking == 0: the copy is enqueued on `stream`
  * and rmse_host is valid once the stream has synchronised (pass pinned memory
@@ -279,7 +283,7 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
  * the device's memory for its own pool, code that must not risk the implicit
  * device synchronisation an allocation or free may cause, or code that must
  * not touch the allocator after start-up.  The plan's bytecode, the work-queue
- * head and the per-warp partial sums live in one fixed device array of
+ * head and the per-tile partial sums live in one fixed device array of
  * TGP_NOALLOC_SCRATCH_BYTES (8 MiB) that is part of the library image: every
  * GPU that loads the library holds it until the process exits.
  *   - The caller passes the inputs (a compiled population and a loaded
@@ -291,6 +295,9 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
  *   - Rejects, with TGP_E_INVALID and a message giving the bytes needed, a
  *     population whose bytecode plus partial sums (n_trees * tiles * warps
  *     floats) exceed the array.
+ *   - Plans without the column and row tables of tgp_fitness_dev (they would
+ *     need device memory of their own); the values, and so the results, are
+ *     bitwise the same, the launch does the tabled work at every point.
  *   - All calls share the one array and it keeps the previous call's
  *     contents (the queue head is cleared on every call); calls whose device
  *     work overlaps -- on different streams or from different threads without

@@ -64,6 +64,9 @@ def _load():
         lib.oracle_fitness.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
                                        i32, P, i64, P, P, P, P, P, i32]
         lib.oracle_fitness.restype = ctypes.c_int
+        lib.oracle_fitness_parts.argtypes = [P, P, i64, P, i32, i32, i32, i32, f32, f32, f32, f32,
+                                             i32, P, i64, P, i32, ctypes.c_double, P, P, P, i64, P]
+        lib.oracle_fitness_parts.restype = ctypes.c_int
         lib.oracle_pagie.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.oracle_pagie.restype = ctypes.c_double
         lib.oracle_sinpi.argtypes = [ctypes.c_double]
@@ -173,6 +176,50 @@ def fitness(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pt
     if with_bound:
         return r64, r32, nf, re
     return r64, r32, nf
+
+
+PART_NAMES = ("s64", "s32", "s64_c", "s32_c", "se_c", "n_c", "n_flagged", "n_excluded")
+
+
+def fitness_parts(ops, imm, tree_off, order, W, H, xlo, xhi, ylo, yhi, target=None, pts=None, trig="pi",
+                  tol=1e-4, ex_cap=None):
+    """Sums behind the fitness comparison (see oracle_fitness_parts in
+    tgp_oracle.c): a dict of [T] arrays named by PART_NAMES, plus "ex_tree"
+    and "ex_pt", the (tree, flat point) pairs of the elements that are not
+    comparable (an unbounded error bound, or the FP32-faithful value further
+    than tol (1 + |v64|) from the binary64 one)."""
+    lib = _load()
+    ops, imm, tree_off = _pop_arrays(ops, imm, tree_off)
+    T = tree_off.size - 1
+    if target is None:
+        kind, tv = TARGET_PAGIE, None
+    else:
+        kind, tv = TARGET_VALUES, np.ascontiguousarray(target, dtype=np.float64).reshape(-1)
+        if tv.size != W * H:
+            raise ValueError("target must hold H*W values")
+    if pts is None:
+        n, pts_arr = 0, None
+    else:
+        pts_arr = np.ascontiguousarray(pts, dtype=np.int64)
+        n = pts_arr.size
+    sums = np.zeros((max(T, 1), 8), np.float64)
+    cap = int(ex_cap) if ex_cap is not None else max(1024, (T * (n if pts is not None else W * H)) // 8)
+    while True:
+        ex_tree = np.empty(cap, np.int32)
+        ex_pt = np.empty(cap, np.int64)
+        ex_n = ctypes.c_int64()
+        rc = lib.oracle_fitness_parts(_ptr(ops), _ptr(imm), imm.size, _ptr(tree_off), T, order,
+                                      W, H, xlo, xhi, ylo, yhi, kind, _ptr(tv), n, _ptr(pts_arr), _trig(trig),
+                                      float(tol), _ptr(sums), _ptr(ex_tree), _ptr(ex_pt), cap, ctypes.byref(ex_n))
+        if rc != 0:
+            raise OracleError(f"oracle_fitness_parts failed: {rc}")
+        if ex_n.value <= cap:
+            break
+        cap = ex_n.value
+    out = {k: sums[:T, i].copy() for i, k in enumerate(PART_NAMES)}
+    out["ex_tree"] = ex_tree[:ex_n.value].copy()
+    out["ex_pt"] = ex_pt[:ex_n.value].copy()
+    return out
 
 
 def pagie(x: float, y: float) -> float:

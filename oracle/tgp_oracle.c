@@ -691,5 +691,79 @@ int oracle_fitness(const int32_t* ops, const float* imm, int64_t n_imm, const in
     return OR_OK;
 }
 
+/*
+ * Sums behind the fitness comparison, split by how each element can be
+ * compared with a binary32 evaluation.  An element is "comparable" when its
+ * error bound is finite (every zero or sign test on its path is decided; a
+ * near-singular denominator is then harmless) and the FP32-faithful value
+ * lies within tol * (1 + |v64|) of the binary64 one (else binary32
+ * evaluation is ill-conditioned there); the others are listed.  Sums rather than RMSE
+ * values are returned so that the caller may split the points into chunks
+ * and add.
+ *   sums [n_trees][8]:
+ *     0  sum over all points of (v64 - target)^2
+ *     1  sum over all points of (v32 - target)^2
+ *     2  sum over comparable points of (v64 - target)^2
+ *     3  sum over comparable points of (v32 - target)^2
+ *     4  sum over comparable points of E^2 (E the element's error bound)
+ *     5  number of comparable points
+ *     6  number of points with a near-singular division (comparable or not)
+ *     7  number of points that are not comparable
+ *   ex_tree, ex_pt [ex_cap]: (tree, flat point index) of every element that is
+ *     not comparable, in tree-then-point order; ex_n receives their count
+ *     (the lists hold the first ex_cap of them; NULL with ex_cap 0 to count).
+ * Targets and trig as for oracle_fitness.
+ */
+int oracle_fitness_parts(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                         int32_t n_trees, int32_t order,
+                         int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                         int32_t target_kind, const double* target_vals,
+                         int64_t n_pts, const int64_t* pts, int32_t trig, double tol,
+                         double* sums, int32_t* ex_tree, int64_t* ex_pt, int64_t ex_cap, int64_t* ex_n)
+{
+    if (n_trees < 0 || W <= 0 || H <= 0 || (trig != 0 && trig != 1) || !sums || !ex_n) return OR_ARG;
+    if (target_kind == TG_VALUES && !target_vals) return OR_ARG;
+    if (target_kind != TG_PAGIE && target_kind != TG_VALUES) return OR_ARG;
+    int64_t N = pts ? n_pts : (int64_t)W * (int64_t)H;
+    otree* trees = (otree*)calloc((size_t)(n_trees > 0 ? n_trees : 1), sizeof(otree));
+    if (!trees) return OR_NOMEM;
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, trees);
+    if (rc) { free_population(trees, n_trees); free(trees); return rc; }
+    int64_t nx = 0;
+    for (int32_t t = 0; t < n_trees; t++) {
+        double* s = sums + (size_t)t * 8;
+        for (int k = 0; k < 8; k++) s[k] = 0.0;
+        for (int64_t i = 0; i < N; i++) {
+            int64_t p = pts ? pts[i] : i;
+            float xf, yf;
+            oracle_grid_point(W, H, xlo, xhi, ylo, yhi, p, &xf, &yf);
+            double tv = target_kind == TG_PAGIE ? oracle_pagie((double)xf, (double)yf) : target_vals[p];
+            opoint pt = { (double)xf, (double)yf, 0, trig };
+            double v64, e;
+            float v32;
+            eval_node(trees[t].nodes, trees[t].root, &pt, &v64, &v32, &e);
+            double d64 = v64 - tv, d32 = (double)v32 - tv;
+            s[0] += d64 * d64;
+            s[1] += d32 * d32;
+            int ok32 = (double)v32 == v64 || fabs((double)v32 - v64) <= tol * (1.0 + fabs(v64));
+            s[6] += pt.flag;
+            if (isfinite(e) && ok32) {
+                s[2] += d64 * d64;
+                s[3] += d32 * d32;
+                s[4] += e * e;
+                s[5] += 1.0;
+            } else {
+                s[7] += 1.0;
+                if (nx < ex_cap) { ex_tree[nx] = t; ex_pt[nx] = p; }
+                nx++;
+            }
+        }
+    }
+    *ex_n = nx;
+    free_population(trees, n_trees);
+    free(trees);
+    return OR_OK;
+}
+
 /* Arity of an opcode (-1 if unknown); exported for the tests' brute force. */
 int oracle_arity(int32_t op) { return arity_of(op); }

@@ -154,6 +154,14 @@ __host__ __device__ constexpr int smem_budget_per_cta(int K) {
     return 228 * 1024 / target_ctas_per_sm(K) - 1024 - 64;
 }
 
+// Fitness: a thread's sum of squared residuals of a tree (its K points) that
+// reaches 2^120 (or is not finite) is recomputed from the residuals scaled by
+// 2^-80, so that no square overflows; a warp with such a thread sums in
+// units of 2^-160 and stores its partial negated: its value is then
+// -partial * 2^160.
+constexpr float kSumBig = 0x1p120f;
+constexpr float kResidualScale = 0x1p-80f;
+
 // Parameters of one interpreter launch.
 struct EvalParams {
     const Ins* code;            // all groups back to back
@@ -166,7 +174,7 @@ struct EvalParams {
     int32_t W, H;
     float xlo, xhi, ylo, yhi;
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
-    float* partial;             // [n_trees][n_tiles][warps] fitness partial sums
+    float* partial;             // [n_trees][n_tiles][warps] fitness partial sums (negated: scaled, see kSumBig)
     float* out;                 // [n_trees][N] phenotypes (phenotype launches)
     float* const* cache;        // cache entry pointers (F_CST / F_CLD), or nullptr
     int32_t* counter;           // work-queue head, zero before the launch
@@ -181,7 +189,7 @@ struct EvalParams {
 };
 
 struct FinalizeParams {
-    const float* partial;       // [n_trees][per_tree]
+    const float* partial;       // [n_trees][per_tree] (negated: in units of 2^-160)
     int64_t per_tree;           // n_tiles * warps
     int32_t n_trees;
     double n_points;            // N

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import assert_elements, assert_fitness
+from parity import check_population
 
 pytestmark = pytest.mark.gpu
 
@@ -91,12 +91,7 @@ def test_columns_against_the_oracle_and_through_a_graph():
             ctx.fitness_graph(pop, dom, dev, stream=st)
         torch.cuda.synchronize()
         assert np.array_equal(dev.cpu().numpy().view(np.int64), fit.view(np.int64))
-    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    assert_elements(ph, v64, fl, eb, context="columns", v32=v32)
-    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    assert_fitness(fit, r64, re, g.N, "columns")
+        check_population(ctx, tok, g, fit, "columns", pop=pop, dom=dom)
 
 
 @pytest.mark.parametrize("expr,extra", [("add(sin(x), y)", 2), ("add(cos(y), x)", 2),

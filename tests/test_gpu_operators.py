@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import assert_elements, assert_fitness, assert_fitness_of_phenotype, grid_target
+from parity import check_population
 
 pytestmark = pytest.mark.gpu
 
@@ -36,15 +36,9 @@ def test_all_operators_against_oracle(K):
     g = I.Grid(33, 17)
     with tgp.Context(points_per_thread=K) as ctx:
         ph, fit = device(ctx, tok, g)
-    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    c = assert_elements(ph, v64, fl, eb, context=f"all operators K={K}", v32=v32)
-    assert c["n"] - c["n_excluded"] > 0.6 * c["n"]
-    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    assert_fitness(fit, r64, re, g.N, "all operators")
-    skipped = np.flatnonzero(~np.isfinite(re))
-    assert_fitness_of_phenotype(fit, ph, grid_target(g), skipped, f"all operators K={K}")
+        r = check_population(ctx, tok, g, fit, f"all operators K={K}", budget="operators")
+    c = r["elements"]
+    assert c["n_bound"] + c["n_unbounded"] < 0.4 * c["n"]
 
 
 def test_exactly_rounded_operators_equal_fp32_faithful():
@@ -158,13 +152,7 @@ def test_radian_trigonometry_against_oracle(K):
     g = I.Grid(37, 21)
     with tgp.Context(points_per_thread=K, trig="rad") as ctx:
         ph, fit = device(ctx, tok, g)
-    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
-    c = assert_elements(ph, v64, fl, eb, context=f"radians K={K}", v32=v32)
-    assert c["n"] - c["n_excluded"] > 0.8 * c["n"]
-    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
-    assert_fitness(fit, r64, re, g.N, "radians")
+        check_population(ctx, tok, g, fit, f"radians K={K}", budget="operators", trig="rad")
     xs = np.array([oracle.grid_point(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, p)[0] for p in range(g.N)])
     assert np.allclose(ph[-4], np.sin(xs), rtol=0, atol=2e-7)
     with tgp.Context(points_per_thread=K) as ctx:
@@ -176,8 +164,6 @@ def test_radian_mode_with_cache_and_noalloc_paths():
     rng = np.random.default_rng(55)
     tok = I.to_tokens([I._full(rng, 4, I.FUNCTIONS) for _ in range(40)])
     g = I.Grid(64, 48)
-    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True, trig="rad")
     with tgp.Context(trig="rad", cache_budget_bytes=64 * g.N * 4, cache_min_cost=1) as ctx:
         dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
         pop = ctx.compile_tokens(tok)
@@ -186,7 +172,7 @@ def test_radian_mode_with_cache_and_noalloc_paths():
         ctx.fitness_noalloc(pop, dom, out)
         torch.cuda.synchronize()
         assert ctx.stats()["cache_hits"] > 0
+        check_population(ctx, tok, g, runs[0], "radians, cached", pop=pop, dom=dom, budget="operators", trig="rad")
     for r in runs[1:]:
         assert np.array_equal(r.view(np.int64), runs[0].view(np.int64))
     assert np.array_equal(out.cpu().numpy().view(np.int64), runs[0].view(np.int64))
-    assert_fitness(runs[0], r64, re, g.N, "radians, cached")

@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import assert_fitness
+from parity import check_population
 
 pytestmark = pytest.mark.gpu
 
@@ -52,19 +52,10 @@ def test_server_results_match_oracle():
     with tgp.Context() as ctx, tgp.Server(ctx, streams=3) as srv:
         ids = [submit(srv, j) for j in jobs]
         res = [srv.wait(i)[0] for i in ids]
-    for k, (j, r) in enumerate(zip(jobs, res)):
-        tok, W, H = j["tok"], j["W"], j["H"]
-        if j["target_tokens"] is None:
-            r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5,
-                                           with_bound=True)
-        else:
-            t_ops, t_imm, t_order = j["target_tokens"]
-            t_off = np.array([0, t_ops.size], np.int64)
-            t64, _, _, teb = oracle.evaluate(t_ops, t_imm, t_off, t_order, W, H, -5, 5, -5, 5, with_bound=True)
-            r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, W, H, -5, 5, -5, 5,
-                                           target=t64[0], with_bound=True)
-            re = re + float(np.sqrt(np.mean(teb[0] ** 2)))
-        assert_fitness(r, r64, re, W * H, f"job {k}")
+    with tgp.Context() as ctx:
+        for k, (j, r) in enumerate(zip(jobs, res)):
+            g = I.Grid(j["W"], j["H"])
+            check_population(ctx, j["tok"], g, r, f"job {k}", target_tokens=j["target_tokens"], budget="serving")
 
 
 def test_server_with_subtree_cache_is_bitwise_equal():

@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import assert_elements, assert_fitness
+from parity import check_population
 
 pytestmark = pytest.mark.gpu
 
@@ -76,9 +76,4 @@ def test_simplified_population_matches_oracle():
     g = I.Grid(33, 17)
     with tgp.Context() as ctx:
         ph, fit = phenotypes(ctx, tok, g)
-    v64, v32, fl, eb = oracle.evaluate(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                       g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    assert_elements(ph, v64, fl, eb, context="simplified")
-    r64, _, _, re = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H,
-                                   g.xlo, g.xhi, g.ylo, g.yhi, with_bound=True)
-    assert_fitness(fit, r64, re, g.N, "simplified")
+        check_population(ctx, tok, g, fit, "simplified")

@@ -1,25 +1,31 @@
 #!/usr/bin/env python
 """Benchmark: node-evaluations/s of the fused population evaluator on GB300.
 
-Workload (the single-GPU configuration the headline metric is quoted on):
-100 ramped half-and-half trees (depth 2-8, functions add sub mul div sin cos
-neg abs min max, terminals x, y, const ~ U[-1,1], seed 1) over a 1024x1024
-binary32 grid on [-5,5]^2, RMSE against the Pagie polynomial, population-wide
-subtree DAG on.  One step = one fitness pass over the population.
+Workload (the headline line): 4,096 trees of U{3..255} nodes (depth <= 12,
+~30% of the nodes in subtrees duplicated across trees, functions add sub mul
+div sin cos neg abs min max, terminals x, y, const ~ U[-1,1], seed 2) over a
+256x256 binary32 grid on [-5,5]^2, RMSE against the Pagie polynomial; launch
+shape chosen by the library's autotuner; one step = one replay of the captured
+CUDA graph (column- and row-table launches, interpreter, finalize).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints ONE JSON line.  `value` times the device-resident path (bytecode
-already uploaded, CUDA events around each step, L2 flushed between steps);
-`e2e` times the public API from host tokens (compile -> upload -> kernels ->
-fitness on the host) per step.  --impl reference times the CPU oracle on the
-host cores on a bounded sample of the same workload.
+uploaded, CUDA events around each step, L2 flushed between steps); `e2e`
+times the public API from host tokens (compile -> upload -> kernels -> fitness
+on the host) per step.  The roofline counts the work the step's launches
+evaluate as planned (tgp_plan_work) at the calibrated issue cost of each
+operator, against the measured straight-line binary32 issue peak.  The other
+configurations (100 trees on 1024x1024, phenotypes, the generational run, the
+serving loop) are under `other_configs`.  --impl reference times the CPU
+oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import re
 import shutil
@@ -37,11 +43,11 @@ from paper_2103_07512_gb300 import inputs as I  # noqa: E402
 
 METRIC = "node-evals/s (tree nodes x fitness cases)"
 UNIT = "node-evals/s"
-WORKLOAD = "population_at_scale: 100 RHH trees depth 2-8, 1024x1024 grid, Pagie target, seed 1"
-SM_COUNT_NOMINAL = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-PROFILE = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
+WORKLOAD = ("batched_uneven: 4096 trees of U{3..255} nodes, depth <= 12, ~30% duplicated subtrees, seed 2; "
+            "256x256 grid on [-5,5]^2, Pagie target; CUDA-graph replay, autotuned shape")
+WORKLOAD_C2 = "population_at_scale: 100 RHH trees depth 2-8, 1024x1024 grid, Pagie target, seed 1"
+PROFILE = os.path.join(HERE, "profiles", "eval_kernel_batched_uneven.md")
+PROFILE_C2 = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
 KERNEL_SRCS = [os.path.join(HERE, "paper_2103_07512_gb300", "csrc", f)
                for f in ("kernels.cu", "gen_fastloop.py", "tgp_ir.h")]
 
@@ -65,8 +71,8 @@ def replica_throughput(local_seconds, units_per_rank, world, dist=None, device=N
 
 
 def workload():
-    tok, g = I.population_at_scale(seed=1)
-    return tok, g
+    tok, g, st = I.batched_uneven(seed=2)
+    return tok, g, st
 
 
 # ------------------------------------------------------------------ clocks
@@ -127,11 +133,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
-def profile_traffic():
-    """dram bytes per launch of the interpreter from the committed ncu summary,
+def profile_traffic(path):
+    """dram bytes per launch of the interpreter from a committed ncu summary,
     or None when the kernel source changed since the capture."""
     try:
-        txt = open(PROFILE).read()
+        txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
@@ -144,27 +150,99 @@ def profile_traffic():
     return float(m.group(1))
 
 
-def weighted_work(tok, costs):
-    """sum over tree nodes of the calibrated issue cost of their operator."""
+def tree_work(tok, costs):
+    """sum over tree nodes (as given) of the calibrated issue cost of their operator."""
     counts = np.bincount(tok.ops, minlength=len(costs))
     return float(np.dot(counts[:len(costs)], costs))
 
 
-def cpu_oracle_rate(tok, g, target_seconds=12.0):
-    """The oracle as it stands, single thread, on a bounded sample of rows."""
+def executed_work(ctx, pop, dom, costs):
+    """Lane-instructions of binary32 issue the step's launches evaluate as
+    planned: every operator evaluation (at every point, once per thread for
+    values with no x below them, once per column or row for tables) at its
+    calibrated cost, plus a subtract, multiply and add per residual."""
+    w, roots = ctx.plan_work(pop, dom)
+    return float(np.dot(w, costs) + 3.0 * roots), w, roots
+
+
+def roofline(work, tree_units_cost, node_units, ms, peak_add, peak_fma, traffic, costs, w):
+    achieved = work / (ms * 1e-3) / 1e12
+    peak = peak_add / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T lane-instructions/s (binary32 issue)",
+            "frac": achieved / peak, "traffic": traffic, "kernel_ms": ms,
+            "peak_source": "measured in this run: straight-line binary32 add chains on every SM "
+                           f"(tgp_calibrate_peak; fused multiply-add chains {peak_fma / 1e12:.2f} T/s); "
+                           "MEASURED_PEAKS.json has no binary32 entry",
+            "work_lane_instr_per_step": work,
+            "work_source": "tgp_plan_work: operator evaluations the step's launches plan (at every point; once "
+                           "per thread for values with no x below them; once per column or row for the table "
+                           "launches) x the operator's calibrated issue cost (tgp_calibrate_op_costs, binary32 "
+                           "add = 1), plus 3 per residual at tree roots",
+            "evaluations_per_step": {I.NAMES[i]: float(w[i]) for i in range(len(w)) if w[i]},
+            "op_costs": {I.NAMES[i]: round(float(costs[i]), 3) for i in range(len(costs))},
+            "frac_trees_as_given": (tree_units_cost / (ms * 1e-3) / 1e12) / peak,
+            "frac_one_op_per_node": (node_units / (ms * 1e-3) / 1e12) / peak}
+
+
+def _oracle_rows(args):
+    import oracle
+    ops, imm, off, order, W, H, pts = args
+    oracle.fitness(ops, imm, off, order, W, H, -5.0, 5.0, -5.0, 5.0, pts=pts)
+    return pts.size
+
+
+def cpu_oracle_rate(tok, g, target_seconds=12.0, cores=1):
+    """The oracle as it stands on a bounded sample of grid rows, all trees:
+    single-threaded (cores=1) or split over `cores` processes by rows."""
     import oracle
     oracle.build()
     nodes = int(tok.ops.size)
-    rows = 8
-    while True:
-        pts = np.arange(rows * g.W, dtype=np.int64)
-        t0 = time.perf_counter()
-        oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
-        dt = time.perf_counter() - t0
-        if dt >= target_seconds / 4 or rows >= g.H:
-            break
-        rows = min(g.H, rows * max(2, int(target_seconds / 4 / max(dt, 1e-3))))
-    return nodes * pts.size / dt, {"rows": rows, "points": int(pts.size), "seconds": dt}
+    rows = 1
+    pool = mp.get_context("spawn").Pool(cores) if cores > 1 else None
+    try:
+        while True:
+            pts = np.arange(rows * g.W, dtype=np.int64)
+            parts = np.array_split(pts, max(1, min(cores * 4, pts.size))) if cores > 1 else [pts]
+            jobs = [(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, p) for p in parts]
+            t0 = time.perf_counter()
+            if pool:
+                pool.map(_oracle_rows, jobs)
+            else:
+                _oracle_rows(jobs[0])
+            dt = time.perf_counter() - t0
+            if dt >= target_seconds / 4 or rows >= g.H:
+                break
+            rows = min(g.H, rows * max(2, int(target_seconds / 4 / max(dt, 1e-3))))
+    finally:
+        if pool:
+            pool.close()
+    return nodes * pts.size / dt, {"rows": rows, "points": int(pts.size), "seconds": dt, "cores": cores}
+
+
+def perop_rate(tok, g, dev, flush, n_trees=None, reps=3):
+    """The per-operator materialising baseline (PyTorch eager, one op per
+    tree node) on the same GPU, on all trees or the first n_trees."""
+    import torch
+    from paper_2103_07512_gb300.perop import PerOpEvaluator
+    per = PerOpEvaluator(g, device=dev)
+    trees = I.from_tokens(tok)
+    if n_trees is not None:
+        trees = trees[:n_trees]
+    nodes = sum(I.size(t) for t in trees)
+    per.fitness(trees)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    pe = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pr = per.fitness(trees)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pe.append(a.elapsed_time(b))
+    ms = float(np.median(pe))
+    return nodes * g.N / (ms * 1e-3), ms, pr.cpu().numpy().astype(np.float64), len(trees), nodes
 
 
 # ------------------------------------------------------------------ arms
@@ -175,10 +253,10 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    tok, g = workload()
+    tok, g, _ = workload()
     nodes = int(tok.ops.size)
-    rows = max(1, min(g.H, args.ref_rows))
-    pts = np.arange(rows * g.W, dtype=np.int64)
+    npts = max(1, min(g.N, args.ref_points))
+    pts = np.arange(npts, dtype=np.int64)
     for _ in range(args.warmup):
         oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
     t0 = time.perf_counter()
@@ -186,7 +264,8 @@ def run_reference(args):
         oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, pts=pts)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = nodes * pts.size / dt
-    sample = f"{rows} of {g.H} grid rows ({pts.size} points) per step, all {tok.n_trees} trees, binary64 + FP32-faithful walk"
+    sample = (f"the first {pts.size} of {g.N} grid points (row 0) per step, all {tok.n_trees} trees, "
+              "binary64 + FP32-faithful walk, one thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -200,7 +279,6 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import paper_2103_07512_gb300 as tgp
-    from paper_2103_07512_gb300.perop import PerOpEvaluator
 
     rank, local, world = env_rank()
     dist = None
@@ -209,31 +287,33 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    tok, g = workload()
+    tok, g, wst = workload()
     T = tok.n_trees
     nodes = int(tok.ops.size)
     units = nodes * g.N                                   # node-evals per step
 
-    ctx = tgp.Context(device=local, time_kernels=True)
+    ctx = tgp.Context(device=local)
     dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     pop = ctx.compile_tokens(tok)
+    K, G, tune_ms = ctx.autotune(pop, dom)
     st = ctx.stats()
     dag_internal = st["dag_internal"]
     costs = ctx.calibrate_op_costs()
-    work = weighted_work(tok, costs) * g.N               # lane-instructions per step
+    peak_add, peak_fma = ctx.calibrate_peak()
     rmse = torch.empty(T, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)                       # graphs are captured on a created stream
 
     for _ in range(max(args.warmup, 3)):
-        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+        ctx.fitness_graph(pop, dom, rmse, stream=stream)
     torch.cuda.synchronize()
+    work, w_ops, w_roots = executed_work(ctx, pop, dom, costs)
     clocks = ClockSampler(local)
     # keep the GPU busy ~1.5 s before the timed region so the clock record sees load
     t_heat = time.perf_counter()
     while time.perf_counter() - t_heat < 1.5:
         for _ in range(20):
-            ctx.fitness_dev(pop, dom, rmse, stream=stream)
+            ctx.fitness_graph(pop, dom, rmse, stream=stream)
         torch.cuda.synchronize()
     s0 = ctx.stats()
     if dist:
@@ -243,8 +323,9 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")                    # profilers can select the timed steps
     for i in range(args.steps):
         flush.fill_(float(i))                               # evict L2 between steps (untimed)
+        stream.wait_stream(torch.cuda.current_stream(dev))
         evs[i][0].record(stream)
-        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+        ctx.fitness_graph(pop, dom, rmse, stream=stream)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -255,11 +336,11 @@ def run_ours(args):
     step_s, value = replica_throughput(float(np.sum([a.elapsed_time(b) for a, b in evs])) / args.steps * 1e-3,
                                        units, world, dist, dev)
     step_ms = step_s * 1e3
-    kern_ms = (s1["eval_ms_sum"] - s0["eval_ms_sum"]) / max(1, s1["eval_timed"] - s0["eval_timed"])
     launches = int(s1["launches"] - s0["launches"])
+    fit_dev = rmse.cpu().numpy()
 
     # -------- end to end through the public API from host tokens
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(args.steps, 10))
     h2d = d2h = 0
     e2e_times = []
     compile_times = []
@@ -279,28 +360,14 @@ def run_ours(args):
         h2d = (s["code_instrs"] + 1) * 8 + (s["n_groups"] + 1) * 8 + s["n_groups"] * 4
         d2h = 8 * T
     e2e_s, e2e_value = replica_throughput(float(np.mean(e2e_times)), units, world, dist, dev)
+    e2e_same = bool(np.array_equal(fit.view(np.int64), fit_dev.view(np.int64)))
 
-    # -------- per-operator materialising baseline on the same GPU
-    per = PerOpEvaluator(g, device=dev)
-    trees = I.from_tokens(tok)
-    for _ in range(2):
-        per.fitness(trees)
-    torch.cuda.synchronize()
-    pe = []
-    for i in range(3):
-        flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pr = per.fitness(trees)
-        b.record(stream)
-        torch.cuda.synchronize()
-        pe.append(a.elapsed_time(b))
-    perop_ms = float(np.median(pe))
-    perop_value = units / (perop_ms * 1e-3)
-    fit_dev = rmse.cpu().numpy()
-    pr = pr.cpu().numpy().astype(np.float64)
-    fin = np.isfinite(fit_dev) & np.isfinite(pr)
-    perop_agree = float(np.mean(np.abs(fit_dev[fin] - pr[fin]) <= 1e-3 * np.abs(fit_dev[fin]) + 1e-5)) if fin.any() else None
+    # -------- per-operator materialising baseline on the same GPU (a sample of the trees)
+    perop_trees = 256
+    pv, pms, pr, pn, pnodes = perop_rate(tok, g, dev, flush, n_trees=perop_trees)
+    fin = np.isfinite(fit_dev[:pn]) & np.isfinite(pr)
+    perop_agree = float(np.mean(np.abs(fit_dev[:pn][fin] - pr[fin]) <= 1e-3 * np.abs(fit_dev[:pn][fin]) + 1e-5)) \
+        if fin.any() else None
 
     if rank != 0:
         return 0
@@ -308,49 +375,40 @@ def run_ours(args):
     # -------- CPU oracle baseline (rank 0, bounded sample)
     cpu_value, cpu_info = cpu_oracle_rate(tok, g, target_seconds=args.cpu_seconds)
 
-    peak_tops = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    achieved_tops = work / (kern_ms * 1e-3) / 1e12
-    traffic = profile_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "trees": T, "tree_nodes": nodes, "dag_internal_nodes": int(dag_internal),
+                   "dup_fraction": round(float(wst["dup_fraction"]), 4),
                    "points": g.N, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "points_per_thread": int(s1["points_per_thread"]),
-                   "threads_per_block": int(s1["threads_per_block"]), "groups": int(s1["n_groups"])},
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
-                     "unit": "TOP/s (binary32 lane-instructions)", "frac": achieved_tops / peak_tops,
-                     "traffic": traffic, "kernel_ms": kern_ms,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal unit counts and max clock)",
-                     "op_costs": {I.NAMES[i]: round(float(costs[i]), 3) for i in range(len(costs))},
-                     "frac_one_op_per_node": (units / (kern_ms * 1e-3) / 1e12) / peak_tops,
-                     "work_note": "achieved counts the work the trees describe (tree nodes as given x points x "
-                                  "op cost) over the time of the step's launches (the column and row table "
-                                  "launches included); the launches evaluate less: shared subtrees once, "
-                                  "exactly simplified trees, values with no x below them once per thread, "
-                                  "subtrees with no y (no x) below them once per grid column (row)"},
+                   "autotuned": {"points_per_thread": K, "groups": G,
+                                 "threads_per_block": int(s1["threads_per_block"]), "kernel_ms": tune_ms},
+                   "graph": True, "gpu_launches_per_step": launches / args.steps},
+        "roofline": roofline(work, tree_work(tok, costs) * g.N, units, step_ms, peak_add, peak_fma,
+                             profile_traffic(PROFILE), costs, w_ops),
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{cpu_info['rows']} of {g.H} rows ({cpu_info['points']} points), all trees, "
-                                   f"{cpu_info['seconds']:.1f} s"},
+                         "sample": f"{cpu_info['rows']} of {g.H} rows ({cpu_info['points']} points), all "
+                                   f"{T} trees, {cpu_info['seconds']:.1f} s, one thread"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_s * 1e3, "compile_ms": 1e3 * float(np.mean(compile_times)),
-                "fitness_call_ms": 1e3 * (float(np.mean(e2e_times)) - float(np.mean(compile_times)))},
-        "perop_baseline": {"value": perop_value, "unit": UNIT, "ms_per_step": perop_ms,
-                           "speedup": value / perop_value, "fitness_agreement": perop_agree,
+                "fitness_call_ms": 1e3 * (float(np.mean(e2e_times)) - float(np.mean(compile_times))),
+                "bitwise_equal_to_graph_replay": e2e_same,
+                "path": "tgp_compile_population from host tokens, then tgp_fitness (blocking) into host memory"},
+        "perop_baseline": {"value": pv, "unit": UNIT, "ms_per_step": pms, "speedup": value / pv,
+                           "sample": f"the first {pn} of {T} trees ({pnodes} nodes) on all {g.N} points",
+                           "fitness_agreement": perop_agree,
                            "fitness_agreement_note": "fraction of trees whose RMSE agrees within 1e-3 relative; "
                                                      "the per-op baseline forms sin(pi a) as sin(a * pi) in binary32 "
-                                                     "(as an eager framework would), which loses accuracy for large a",
-                           "launches_per_step": per.launches // 5},
+                                                     "(as an eager framework would), which loses accuracy for large a"},
         "dag_node_evals_per_s": world * int(dag_internal) * g.N / (step_ms * 1e-3),
         "gpu_launches": launches,
         "clocks": clk,
     }
     if not args.no_extras and world == 1:
         line["other_configs"] = {
-            "phenotype": bench_phenotype(ctx, pop, dom, tok, g, dev, flush),
-            "batched_uneven": bench_batched(tgp.Context, dev, flush),
+            "population_at_scale": bench_population_at_scale(tgp.Context, dev, flush, costs, peak_add, peak_fma),
             "evolution": bench_evolution(tgp.Context, dev),
             "serving": bench_serving(tgp, dev),
         }
@@ -360,46 +418,45 @@ def run_ours(args):
     return 0
 
 
-def bench_batched(ctx_cls, dev, flush, steps=20):
-    """Batched uneven trees: 4096 trees of 3..255 nodes (30% duplicated
-    subtrees) on a 256x256 grid, shape chosen by the autotuner, each step one
-    replay of the captured CUDA graph (memset + interpreter + finalize)."""
+def bench_population_at_scale(ctx_cls, dev, flush, costs, peak_add, peak_fma, steps=50):
+    """100 RHH trees (depth 2-8) on 1024x1024, population-wide DAG: direct
+    launches (tgp_fitness_dev) timed with CUDA events; the interpreter's own
+    time from the library's kernel events; phenotypes to HBM."""
     import torch
-    tok, g, st = I.batched_uneven(seed=2)
-    ctx = ctx_cls(device=dev.index)
+    tok, g = I.population_at_scale(seed=1)
+    ctx = ctx_cls(device=dev.index, time_kernels=True)
     dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     pop = ctx.compile_tokens(tok)
-    K, G, tune_ms = ctx.autotune(pop, dom)
     rmse = torch.empty(tok.n_trees, dtype=torch.float64, device=dev)
-    stream = torch.cuda.Stream(dev)          # graphs are captured on a created stream
-    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
     for _ in range(5):
-        ctx.fitness_graph(pop, dom, rmse, stream=stream)
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
     torch.cuda.synchronize()
     s0 = ctx.stats()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.nvtx.range_push("timed")                    # profilers can select the timed steps
     for i in range(steps):
         flush.fill_(float(i))
-        stream.wait_stream(torch.cuda.current_stream(dev))
         evs[i][0].record(stream)
-        ctx.fitness_graph(pop, dom, rmse, stream=stream)
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
     s1 = ctx.stats()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    kern_ms = (s1["eval_ms_sum"] - s0["eval_ms_sum"]) / max(1, s1["eval_timed"] - s0["eval_timed"])
     units = int(tok.ops.size) * g.N
-    st1 = ctx.stats()
+    work, w_ops, _ = executed_work(ctx, pop, dom, costs)
+    out = {"workload": WORKLOAD_C2, "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "tree_nodes": int(tok.ops.size), "dag_internal_nodes": int(s1["dag_internal"]),
+           "points_per_thread": int(s1["points_per_thread"]), "threads_per_block": int(s1["threads_per_block"]),
+           "groups": int(s1["n_groups"]),
+           "roofline": roofline(work, tree_work(tok, costs) * g.N, units, kern_ms, peak_add, peak_fma,
+                                profile_traffic(PROFILE_C2), costs, w_ops),
+           "l2": "flushed between steps"}
+    out["roofline"]["kernel_ms_note"] = ("interpreter and table launches, CUDA events the library records "
+                                         "around them on the stream (TGP_F_TIME_KERNELS)")
+    out["phenotype"] = bench_phenotype(ctx, pop, dom, tok, g, dev, flush)
     ctx.close()
-    return {"workload": "batched_uneven: 4096 trees of U{3..255} nodes, depth <= 12, 256x256 grid, seed 2",
-            "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "tree_nodes": int(tok.ops.size), "dag_internal_nodes": int(st1["dag_internal"]),
-            "dup_fraction": round(float(st["dup_fraction"]), 4),
-            "autotuned": {"points_per_thread": K, "groups": G, "threads_per_block": int(st1["threads_per_block"]),
-                          "kernel_ms": tune_ms},
-            "gpu_launches_per_step": (s1["launches"] - s0["launches"]) / steps,
-            "graph": True, "l2": "flushed between steps"}
+    return out
 
 
 def bench_phenotype(ctx, pop, dom, tok, g, dev, flush, steps=20):
@@ -457,8 +514,14 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
         else:
             ev = Evolution(gpu_fitness(ctx, dom), pop_size=50, generations=generations, seed=3)
         got = []
+        keep = {}
+
+        def on_gen(gen, r):
+            got.append(r.copy())
+            if arm == "cache" and gen.index in (0, 25, 49):
+                keep[gen.index] = I.to_tokens(ev.population)
         t0 = time.perf_counter()
-        ev.run(lambda gen, r: got.append(r.copy()))
+        ev.run(on_gen)
         total = time.perf_counter() - t0
         fit_s = sum(h.seconds for h in ev.history)
         nodes = sum(h.nodes for h in ev.history)
@@ -475,6 +538,18 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
         if arm.startswith("library_variation"):
             ev.close()
         ctx.close()
+        if keep:   # the oracle on all host cores beside the GPU, on the same generations
+            cores = os.cpu_count() or 1
+            orc = {}
+            for gi, tk in sorted(keep.items()):
+                v, info = cpu_oracle_rate(tk, g, target_seconds=4.0, cores=cores)
+                gpu_v = int(tk.ops.size) * g.N / ev.history[gi].seconds
+                orc[str(gi)] = {"oracle_node_evals_per_s": v, "gpu_node_evals_per_s": gpu_v,
+                                "gpu_over_oracle": gpu_v / v,
+                                "sample": f"{info['rows']} of {g.H} rows, all 50 trees, {info['seconds']:.1f} s"}
+            out["oracle_beside_gpu"] = {"cores": cores, "generations": orc,
+                                        "note": "oracle split over rows in `cores` spawned processes; the GPU "
+                                                "rate is that generation's compile + fitness call"}
     same = all(np.array_equal(a.view(np.int64), c.view(np.int64))
                for arm, ref in (("cache", "no_cache"), ("cache_min_cost_8", "no_cache"),
                                 ("library_variation", "library_variation_no_cache"))
@@ -579,10 +654,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--ref-points", type=int, default=128,
+                    help="grid points per step of the reference arm (a bounded sample, all trees)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, evolution and serving measurements")
-    ap.add_argument("--only", choices=["batched_uneven"],
+                    help="skip the other configurations (1024x1024 population, evolution, serving)")
+    ap.add_argument("--only", choices=["population_at_scale"],
                     help="measure one other configuration alone and print its line (for profiling it)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -593,7 +669,13 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-        print(json.dumps({"config": args.only, **bench_batched(tgp.Context, dev, flush, steps=args.steps)}))
+        with tgp.Context(device=0) as c:
+            costs = c.calibrate_op_costs()
+            pa, pf = c.calibrate_peak()
+        torch.cuda.nvtx.range_push("timed")
+        r = bench_population_at_scale(tgp.Context, dev, flush, costs, pa, pf, steps=args.steps)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"config": args.only, **r}))
         return 0
     return run_ours(args)
 

@@ -103,7 +103,9 @@ enum {
 /* tgp_config.flags */
 #define TGP_F_HOST_ONLY 1     /* no device: compile and inspect plans only (for
                                  machines without a GPU); device calls fail with
-                                 TGP_E_INVALID.  Plans assume 152 SMs. */
+                                 TGP_E_INVALID (a domain with the Pagie target,
+                                 which holds no device memory, may be loaded for
+                                 tgp_plan_work).  Plans assume 152 SMs. */
 #define TGP_F_NO_DEDUP 2      /* evaluate every tree as a tree: a shared subtree
                                  is recomputed at each use instead of being held
                                  (the uncached reference; results are bitwise
@@ -363,6 +365,30 @@ int tgp_debug_layout(int32_t* out, int32_t n);
  * accounting only.
  */
 int tgp_calibrate_op_costs(tgp_ctx* ctx, double* cost_out);
+
+/*
+ * The binary32 issue peak of the device, measured: the rate, in lane
+ * operations per second, of a straight-line kernel of independent binary32
+ * add chains on every SM (the unit tgp_calibrate_op_costs expresses costs in),
+ * and of the same with fused multiply-adds.  Synchronous; for roofline
+ * accounting only.
+ */
+int tgp_calibrate_peak(tgp_ctx* ctx, double* add_lane_ops_per_s, double* fma_lane_ops_per_s);
+
+/*
+ * The work the fitness launches of `pop` on `domain` evaluate, as planned
+ * (host side; builds the plan if the population has none for the domain's
+ * grid): work_out[op] = evaluations of operator op (TGP_OP_*), summed over
+ * the launch's points for instructions evaluated at every point, over its
+ * threads for values with no x below them (evaluated once per thread), and
+ * over the W (H) points of the column (row) table launches;
+ * work_out[TGP_N_OPS] = residuals formed at tree roots (one per tree and
+ * point: a subtract, a multiply and an add each).  Shared subtrees count once
+ * per evaluation the plan makes of them, loads from tables or the cache not
+ * at all.  work_out: host array of TGP_N_OPS + 1 doubles.  The plan ignores
+ * the subtree cache (the plan of a cache-free context).
+ */
+int tgp_plan_work(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, double* work_out);
 
 /* ------------------------------------------------------------------------
  * Generational step on the host (TensorGP, Sec. 3 and Table 2).

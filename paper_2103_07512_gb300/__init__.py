@@ -28,7 +28,7 @@ N_OPS = 24
 EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tgp_release_domain",
            "tgp_compile_population", "tgp_release_population", "tgp_evaluate", "tgp_fitness",
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
-           "tgp_calibrate_op_costs", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune",
+           "tgp_calibrate_op_costs", "tgp_calibrate_peak", "tgp_plan_work", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune",
            "tgp_server_create", "tgp_server_destroy", "tgp_server_submit", "tgp_server_wait",
            "tgp_server_stats_get", "tgp_evolve", "tgp_population_tokens"]
 
@@ -136,6 +136,8 @@ def lib():
             "tgp_debug_plan": [P, i64, i64, P, i64, P, P, i64, P],
             "tgp_debug_layout": [P, i32],
             "tgp_calibrate_op_costs": [P, P],
+            "tgp_calibrate_peak": [P, P, P],
+            "tgp_plan_work": [P, i64, i64, P],
             "tgp_fitness_noalloc": [P, i64, i64, P, P],
             "tgp_fitness_graph": [P, i64, i64, P, P],
             "tgp_autotune": [P, i64, i64, P, P, P, P],
@@ -356,6 +358,21 @@ class Context:
         self._check(self._L.tgp_debug_plan(self._h, pop, n_points, _ptr(ins), n.value, ctypes.byref(n),
                                            _ptr(off), off.size, ctypes.byref(g)))
         return ins, off
+
+    def calibrate_peak(self):
+        """tgp_calibrate_peak: measured binary32 lane operations per second
+        of straight-line add chains and of fused multiply-add chains."""
+        a = ctypes.c_double()
+        f = ctypes.c_double()
+        self._check(self._L.tgp_calibrate_peak(self._h, ctypes.byref(a), ctypes.byref(f)))
+        return a.value, f.value
+
+    def plan_work(self, pop, dom):
+        """tgp_plan_work: evaluations per operator the fitness launches plan
+        ([N_OPS] float64), and the residuals formed at tree roots."""
+        w = np.zeros(N_OPS + 1, np.float64)
+        self._check(self._L.tgp_plan_work(self._h, pop, dom, _ptr(w)))
+        return w[:N_OPS], float(w[N_OPS])
 
     def calibrate_op_costs(self):
         c = np.zeros(N_OPS, np.float64)

@@ -936,7 +936,9 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
     if (!std::isfinite(xlo) || !std::isfinite(xhi) || !std::isfinite(ylo) || !std::isfinite(yhi))
         return fail(TGP_E_INVALID, "domain bounds must be finite");
     std::lock_guard<std::mutex> g(ctx->mu);
-    int rc = set_device(ctx);
+    int rc = TGP_OK;
+    // a host-only context may hold Pagie domains (no device memory) for planning
+    if (!(ctx->host_only && target_kind == TGP_TARGET_PAGIE)) rc = set_device(ctx);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     auto d = std::make_unique<Domain>();
@@ -1415,6 +1417,80 @@ int tgp_debug_layout(int32_t* out, int32_t n) {
     if (!out || n < 2) return fail(TGP_E_INVALID, "need an array of at least 2");
     out[0] = kNOpnd;
     out[1] = F_NFORMS;
+    return TGP_OK;
+}
+
+int tgp_plan_work(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, double* work_out) {
+    if (!ctx || !work_out) return fail(TGP_E_INVALID, "ctx / work_out is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    const PlanShape shape = choose_shape(ctx, p->ir, d->N(), d->W);
+    HostPlan built;
+    const HostPlan* hp = nullptr;
+    auto it = p->plans.find(shape);
+    if (it != p->plans.end()) {
+        hp = &it->second->hp;
+    } else {
+        build_plan(p->ir, shape, built, nullptr, &ctx->par, columns_on(ctx));
+        hp = &built;
+    }
+    for (int i = 0; i <= TGP_N_OPS; ++i) work_out[i] = 0.0;
+    // one program's instructions, each evaluated `per_point` or `per_thread` times
+    auto count = [&](const HostPlan& h, double per_point, double per_thread, bool roots) {
+        for (const IrIns& in : h.ir) {
+            const double n = in.uni ? per_thread : per_point;
+            switch (in.form) {
+            case F_AO: case F_OA: case F_TT: case F_UA: case F_UT: work_out[in.fn] += n; break;
+            case F_SEL: work_out[T_IF] += n; break;
+            case F_ROOT: if (roots) work_out[TGP_N_OPS] += per_point; break;
+            default: break;   // loads, stores, table and cache traffic, end
+            }
+        }
+    };
+    const double N = (double)d->N();
+    count(*hp, N, (double)plan_chunks(hp->shape), true);
+    if (hp->col_plan) count(*hp->col_plan, (double)d->W, (double)plan_chunks(hp->col_plan->shape), false);
+    if (hp->row_plan) count(*hp->row_plan, (double)d->H, (double)plan_chunks(hp->row_plan->shape), false);
+    return TGP_OK;
+}
+
+int tgp_calibrate_peak(tgp_ctx* ctx, double* add_lane_ops_per_s, double* fma_lane_ops_per_s) {
+    if (!ctx || !add_lane_ops_per_s || !fma_lane_ops_per_s) return fail(TGP_E_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    const int threads = 256, grid = ctx->sms * 8, iters = 8192;
+    DevBuf<float> in, out;
+    CUDA_TRY(in.ensure(256));
+    CUDA_TRY(out.ensure((size_t)grid * threads));
+    std::vector<float> h(256);
+    for (int i = 0; i < 256; ++i) h[i] = 1.0f + (float)i / 256.0f;
+    CUDA_TRY(cudaMemcpy(in.p, h.data(), 256 * sizeof(float), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    // lane operations of one launch: 8 chains x 16 unrolled x iters per thread
+    const double ops = (double)grid * threads * iters * 16.0 * 8.0;
+    double best[2] = {0.0, 0.0};
+    const int kinds[2] = {0, 12};   // calib_kernel: add chains, fused multiply-add chains
+    for (int k = 0; k < 2; ++k) {
+        for (int rep = 0; rep < 4; ++rep) {   // a warm-up and three timed launches, best kept
+            CUDA_TRY(cudaEventRecord(e0, 0));
+            CUDA_TRY(launch_calib(kinds[k], in.p, out.p, iters, grid, threads, 0));
+            CUDA_TRY(cudaEventRecord(e1, 0));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            ctx->stats.launches++;
+            if (rep > 0) best[k] = std::max(best[k], ops / (ms * 1e-3));
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *add_lane_ops_per_s = best[0];
+    *fma_lane_ops_per_s = best[1];
     return TGP_OK;
 }
 

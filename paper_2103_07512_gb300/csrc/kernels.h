@@ -21,7 +21,8 @@ size_t eval_smem_bytes(int K, int threads, int n_slots);
 // Per-tree binary64 reduction of the fitness partials and sqrt(sum / N).
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 
-// Straight-line chains of one operator (0 add, 1 div, 2 sin, 3 cos, 4 mul, 5 min).
+// Straight-line chains of one operator (0 add, 1 div, 2 sin, 3 cos, 4 mul, 5 min,
+// 6 exp, 7 log, 8 pow, 9 tan, 10 sqrt, 11 mod, 12 fused multiply-add).
 cudaError_t launch_calib(int opk, const float* in, float* out, int iters, int grid, int threads, cudaStream_t s);
 
 }  // namespace tgp

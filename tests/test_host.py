@@ -43,9 +43,35 @@ def test_layout():
 
 
 def test_host_only_context_refuses_device_work(ctx):
-    with pytest.raises(tgp.TgpError) as e:
-        ctx.load_domain(4, 4)
-    assert e.value.code == tgp.E_INVALID
+    dom = ctx.load_domain(4, 4)          # a Pagie domain holds no device memory (planning only)
+    pop = ctx.compile_tokens(I.to_tokens([I.parse_string("add(x, y)")]))
+    for call in (lambda: ctx.fitness(pop, dom, 1),
+                 lambda: ctx.load_domain(4, 4, target=np.zeros(16, np.float32))):
+        with pytest.raises(tgp.TgpError) as e:
+            call()
+        assert e.value.code == tgp.E_INVALID
+
+
+@pytest.mark.parametrize("columns", [False, True])
+def test_plan_work_counts_evaluations(columns):
+    """tgp_plan_work: every instruction counted once per point, per thread for
+    values with no x below them, per column / row for tabled subtrees."""
+    W, H, K = 16, 4, 8
+    N, chunks = W * H, H * ((W + K - 1) // K)
+    with tgp.Context(host_only=True, points_per_thread=K, threads_per_block=32, columns=columns) as c:
+        dom = c.load_domain(W, H)
+        pop = c.compile_tokens(I.to_tokens([I.parse_string("add(mult(x, y), sin(y))"),
+                                            I.parse_string("div(cos(x), 0.5)")]))
+        w, roots = c.plan_work(pop, dom)
+    assert roots == 2 * N
+    assert w[I.MUL] == N and w[I.ADD] == N
+    # sin(y): no x below, once per thread; with tables, once per grid row
+    assert w[I.SIN] == (H if columns else chunks)
+    # cos(x): no y below, at every point; with tables, once per grid column (then div(cos(x), 0.5)
+    # is tabled whole: the table holds the root's subtree)
+    assert w[I.COS] == (W if columns else N)
+    assert w[I.DIV] == (W if columns else N)
+    assert w.sum() == w[[I.MUL, I.ADD, I.SIN, I.COS, I.DIV]].sum()
 
 
 # ---------------------------------------------------------------- validation

@@ -301,7 +301,7 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
  *     need device memory of their own); the values, and so the results, are
  *     bitwise the same, the launch does the tabled work at every point.
  *   - All calls share the one array and it keeps the previous call's
- *     contents (the queue head is cleared on every call); calls whose device
+ *     contents (the queue heads are cleared on every call); calls whose device
  *     work overlaps -- on different streams or from different threads without
  *     ordering -- race on it and give wrong results.
  * Allocates no device memory and calls no allocating library routine.

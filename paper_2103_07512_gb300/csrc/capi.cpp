@@ -300,6 +300,9 @@ PlanShape choose_shape(tgp_ctx* c, const PopIR& ir, int64_t N, int64_t W) {
     return s;
 }
 
+// Work queues of a launch: one per SM.
+int n_queues(const tgp_ctx* c) { return std::max(1, std::min(c->sms, kMaxQueues)); }
+
 bool trig_radians(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_TRIG_RADIANS) != 0; }
 bool columns_on(const tgp_ctx* c) { return (c->cfg.flags & TGP_F_NO_COLUMNS) == 0; }
 // Radian trigonometry runs in the interpreter variant with the rest of Table 1.
@@ -362,7 +365,7 @@ int upload_plan(Plan* pl, int64_t T, cudaStream_t s) {
     }
     CUDA_TRY(pl->partial.ensure((size_t)std::max<int64_t>(T, 1) * hp.n_tiles * warps));
     CUDA_TRY(pl->rmse.ensure((size_t)std::max<int64_t>(T, 1)));
-    CUDA_TRY(pl->counter.ensure(3));   // work queues of the launch and of its column and row tables
+    CUDA_TRY(pl->counter.ensure(3 * kQueueWords));   // work queues of the launch and of its column and row tables
     if (!pl->h_table.empty()) {
         CUDA_TRY(pl->table.ensure(pl->h_table.size()));
         CUDA_TRY(cudaMemcpyAsync(pl->table.p, pl->h_table.data(), pl->h_table.size() * sizeof(float*),
@@ -752,6 +755,8 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.out = out;
     p.cache = pl->h_table.empty() ? nullptr : pl->table.p;
     p.counter = pl->counter.p;
+    p.n_queues = n_queues(c);
+    p.local_items = queue_local_items(p.n_items, p.n_queues);
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     p.trig_rad = trig_radians(c) ? 1 : 0;
@@ -761,7 +766,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
     p.row_stride = hp.row_stride;
     if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
-    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * sizeof(int32_t), s));
+    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * kQueueWords * sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (timed) {
@@ -798,7 +803,9 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         q.yhi = d->ylo;
         q.out = pl->ctab.p;
         q.out_stride = hp.col_stride;
-        q.counter = pl->counter.p + 1;
+        q.counter = pl->counter.p + kQueueWords;
+        q.n_queues = p.n_queues;
+        q.local_items = queue_local_items(q.n_items, q.n_queues);
         q.n_slots = ch.n_slots;
         q.max_items_per_cta = (int32_t)std::min<int64_t>(ch.n_items, INT32_MAX);
         q.trig_rad = p.trig_rad;
@@ -825,7 +832,9 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         q.yhi = d->yhi;
         q.out = pl->rtab.p;
         q.out_stride = hp.row_stride;
-        q.counter = pl->counter.p + 2;
+        q.counter = pl->counter.p + 2 * kQueueWords;
+        q.n_queues = p.n_queues;
+        q.local_items = queue_local_items(q.n_items, q.n_queues);
         q.n_slots = rh.n_slots;
         q.max_items_per_cta = (int32_t)std::min<int64_t>(rh.n_items, INT32_MAX);
         q.trig_rad = p.trig_rad;

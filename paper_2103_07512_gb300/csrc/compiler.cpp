@@ -832,6 +832,12 @@ Ins encode(const IrIns& in) {
     return e;
 }
 
+int64_t queue_local_items(int64_t n_items, int n_queues) {
+    const int64_t Q = std::max(1, n_queues);
+    if (n_items < 8 * Q) return 0;
+    return n_items * 3 / 4 / Q * Q;
+}
+
 PlanShape default_shape(const PopIR& pop, int64_t N, int sms) {
     PlanShape s;
     s.N = N;

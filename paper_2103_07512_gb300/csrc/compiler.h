@@ -158,6 +158,11 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
 
 Ins encode(const IrIns& in);
 
+// Items of a launch that go to the per-SM chunks of its work queues (three
+// quarters of them, a multiple of n_queues; none for launches of fewer than
+// 8 items per queue); the rest go to the global queue.
+int64_t queue_local_items(int64_t n_items, int n_queues);
+
 // The node of one token with operands k (as the parser makes it: clip is
 // lowered to max(min(z, x), y); simplified when `simplify`).
 int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits, bool simplify);

@@ -7,7 +7,7 @@
 // device (cudaMalloc / cudaFree may wait for all work in flight), or a caller
 // that must not touch the allocator once it has started.  For them this entry
 // point keeps everything the fitness kernels need beyond their inputs and
-// outputs -- the bytecode of the plan, the work-queue head and the per-warp
+// outputs -- the bytecode of the plan, the work-queue heads and the per-warp
 // partial sums -- in one fixed array of device memory that is part of the
 // library image: every GPU that loads the library holds it until the process
 // exits, and no call allocates device memory.
@@ -76,7 +76,8 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     const int warps = hp.shape.threads / 32;
     const size_t n_partial = (size_t)T * hp.n_tiles * warps;
     const size_t off_counter = 0;
-    const size_t off_code = align256(sizeof(int32_t));
+    const int Q = std::max(1, std::min(v.sms, kMaxQueues));   // work queues, one per SM
+    const size_t off_code = align256(kQueueWords * sizeof(int32_t));
     const size_t off_goff = off_code + align256(hp.code.size() * sizeof(Ins));
     const size_t off_gord = off_goff + align256(hp.code_off.size() * sizeof(int64_t));
     const size_t off_part = off_gord + align256(hp.group_order.size() * sizeof(int32_t));
@@ -104,11 +105,11 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
             return internal::set_error(TGP_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-    // The array keeps the previous call's contents: the queue head must start
+    // The array keeps the previous call's contents: the queue heads must start
     // at zero; code and offsets are overwritten; every partial the finalize
     // reads is written by this launch.  Copies from pageable host memory
     // return once staged, so the host plan may go out of scope afterwards.
-    NA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), s));
+    NA_TRY(cudaMemsetAsync(counter, 0, kQueueWords * sizeof(int32_t), s));
     NA_TRY(cudaMemcpyAsync(code, hp.code.data(), hp.code.size() * sizeof(Ins), cudaMemcpyHostToDevice, s));
     NA_TRY(cudaMemcpyAsync(goff, hp.code_off.data(), hp.code_off.size() * sizeof(int64_t),
                            cudaMemcpyHostToDevice, s));
@@ -140,6 +141,8 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.out = nullptr;
     p.cache = nullptr;
     p.counter = counter;
+    p.n_queues = Q;
+    p.local_items = queue_local_items(hp.n_items, Q);
     p.n_slots = hp.n_slots;
     p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
     p.trig_rad = v.trig_radians ? 1 : 0;

@@ -162,6 +162,15 @@ __host__ __device__ constexpr int smem_budget_per_cta(int K) {
 constexpr float kSumBig = 0x1p120f;
 constexpr float kResidualScale = 0x1p-80f;
 
+// Work queues of one launch: the first local_items items are cut into one
+// contiguous chunk per SM (at most kMaxQueues), so that the CTAs of an SM
+// take consecutive items (the same tree group, so the same bytecode, which
+// then stays in that SM's L1); the rest are handed out by one global queue
+// (dynamic balance at the end).  A chunk that no SM took (SM ids beyond the
+// queue count) is drained last by any CTA.
+constexpr int kMaxQueues = 256;
+constexpr int kQueueWords = kMaxQueues + 1;   // chunk heads, then the global head
+
 // Parameters of one interpreter launch.
 struct EvalParams {
     const Ins* code;            // all groups back to back
@@ -177,7 +186,9 @@ struct EvalParams {
     float* partial;             // [n_trees][n_tiles][warps] fitness partial sums (negated: scaled, see kSumBig)
     float* out;                 // [n_trees][N] phenotypes (phenotype launches)
     float* const* cache;        // cache entry pointers (F_CST / F_CLD), or nullptr
-    int32_t* counter;           // work-queue head, zero before the launch
+    int32_t* counter;           // [kQueueWords] work-queue heads, zero before the launch
+    int32_t n_queues;           // chunk q holds items [q L / n_queues, (q+1) L / n_queues)
+    int64_t local_items;        // L: items in the per-SM chunks; [L, n_items) in the global queue
     int32_t n_slots;            // shared-memory value slots per thread
     int32_t max_items_per_cta;  // bound on the work-queue loop
     int32_t trig_rad;           // sin/cos/tan in radians (interpreter variant with the rest of Table 1 only)

@@ -565,13 +565,14 @@ def bench_evolution(ctx_cls, dev, generations=50, budget=20 * 10**9):
 
 
 def _serve_run(tgp, ctx, jobs, rate, seconds, rng, streams, clients=4):
-    """Offers `jobs` (cycled) at Poisson times of the given rate for about
+    """Offers the next jobs of the iterator `jobs` at Poisson times of the given rate for about
     `seconds`: `clients` submitting threads take the arrivals in turn (each
     submit validates, hash-conses and plans its job in the caller's thread)
     and one collector thread per client waits for the results.  Returns the
     latency percentiles and throughput of the run."""
     import threading
     n = max(1, int(rate * seconds))
+    mine_jobs = [next(jobs) for _ in range(n)]
     gaps = rng.exponential(1.0 / rate, size=n)
     when = np.cumsum(gaps) - gaps[0]
     srv = tgp.Server(ctx, streams=streams)
@@ -586,7 +587,7 @@ def _serve_run(tgp, ctx, jobs, rate, seconds, rng, streams, clients=4):
             dt = t0 + when[k] - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            j = jobs[k % len(jobs)]
+            j = mine_jobs[k]
             i = srv.submit(j["tok"], j["W"], j["H"], target_tokens=j["target_tokens"])
             mine.append((i, int(j["tok"].ops.size) * j["W"] * j["H"]))
         for i, units in mine:
@@ -611,7 +612,9 @@ def _serve_run(tgp, ctx, jobs, rate, seconds, rng, streams, clients=4):
     return {"offered_jobs_per_s": rate, "jobs": n, "arrival_span_s": (last_sub - first) * 1e-9,
             "span_s": span, "jobs_per_s": n / span, "node_evals_per_s": units / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_batch_jobs": n / max(1, st["batches"]), "max_in_flight": int(st["max_in_flight"]),
+            "mean_batch_jobs": n / max(1, st["batches"]), "max_batch_jobs": int(st["max_batch_jobs"]),
+            "max_batch_domains": int(st["max_batch_domains"]), "max_in_flight": int(st["max_in_flight"]),
+            "domains_loaded": int(st["domains_loaded"]),
             "drain_s": (last - last_sub) * 1e-9,
             "worker_busy_frac": st["worker_busy_ns"] * 1e-9 / span,
             "domain_load_frac": st["domain_load_ns"] * 1e-9 / span,
@@ -627,7 +630,9 @@ def bench_serving(tgp, dev, streams=4, seconds=2.5):
     (completions at least 95% of the offered rate) with a queue that drains
     within 0.1 s of the last arrival."""
     rng = np.random.default_rng(4)
-    jobs = I.serving_jobs(800, seed=4, pool=32)
+    # 32 populations, each job a fresh draw of grid and target (so domains are
+    # loaded and admitted at the offered rate); every run takes jobs not yet used
+    jobs = iter(I.serving_jobs(6000, seed=4, pool=32))
     ctx = tgp.Context(device=dev.index, cache_budget_bytes=8 * 10**9, time_kernels=True)
     # warm the resident domains and plans, then a burst to measure capacity
     _serve_run(tgp, ctx, jobs, rate=1e4, seconds=32 / 1e4, rng=rng, streams=streams)
@@ -641,8 +646,8 @@ def bench_serving(tgp, dev, streams=4, seconds=2.5):
     st = ctx.stats()
     ctx.close()
     return {"workload": "serving: Poisson jobs, U{10..1000} RHH trees depth 2-10, square grids 2^12..2^22 "
-                        "points log-uniform, Pagie or random depth-4 target tree, seed 4 (800 jobs over 32 "
-                        "distinct populations, cycled)",
+                        "points log-uniform, Pagie or random depth-4 target tree, seed 4 (32 distinct "
+                        "populations; every job a fresh draw of grid side and target, no job offered twice)",
             "streams": streams, "capacity_jobs_per_s": cap, "burst": burst, "sweep": runs,
             "sustained": best, "cache_hits": int(st["cache_hits"]), "cache_inserts": int(st["cache_inserts"])}
 

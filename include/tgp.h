@@ -461,11 +461,15 @@ int tgp_population_tokens(tgp_ctx* ctx, tgp_handle pop, int32_t* ops, int64_t ca
  * A server owns a worker thread on a context.  tgp_server_submit copies and
  * validates a job (tokens, grid, target) in the caller's thread and queues
  * it; the worker admits queued jobs in arrival order when a launch slot (one
- * CUDA stream) is free and the job's device memory fits the HBM budget, and
- * fuses every queued job on the same domain (same grid and target) into one
- * population launch -- continuous batching at launch granularity: jobs that
- * arrive while others run join the next launch on their domain, and launches
- * on different slots overlap on the device.  Domains stay resident on the
+ * CUDA stream) is free and the job's device memory fits the HBM budget.  One
+ * launch takes the head of the queue, every queued job on the same domain
+ * (same grid and target; their trees become one population), and queued jobs
+ * on other domains whose launch shape is the head's (points per thread and
+ * threads per block, as tgp_fitness_dev would choose them) -- one interpreter
+ * launch over all their domains (up to 64), each domain's items carrying its
+ * own grid, target and program.  This is continuous batching at launch
+ * granularity: jobs that arrive while others run join the next launch, and
+ * launches on different slots overlap on the device.  Domains stay resident on the
  * device between jobs (least recently used ones not in use are released when
  * the budget needs room), and so does the context's subtree cache (the
  * context's cache_budget_bytes).  A job's RMSE values do not depend on which
@@ -521,7 +525,8 @@ typedef struct tgp_server_stats {
     int64_t queued;              /* jobs waiting for admission */
     int64_t worker_busy_ns;      /* host time the worker spent preparing and enqueueing launches */
     int64_t domain_load_ns;      /* part of it spent loading domains */
-    int64_t reserved[3];
+    int64_t max_batch_domains;   /* most domains fused into one launch */
+    int64_t reserved[2];
 } tgp_server_stats;
 
 /* Starts a server on ctx (a device context; the server uses it from its

@@ -730,59 +730,14 @@ int finish_call(Plan* pl, CallCache& cc, cudaStream_t s) {
     return TGP_OK;
 }
 
-int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, cudaStream_t s) {
+// The column and row table launches of a plan (phenotypes of the tabled
+// subtrees on one row of W points and on one column of H points), on `s`.
+// The plan's queue heads (pl->counter) must be zero.
+int launch_tables(tgp_ctx* c, Plan* pl, const Domain* d, int32_t trig_rad, cudaStream_t s) {
     const HostPlan& hp = pl->hp;
-    // the plan's work units cover the grid only for the row length it was built for
-    if (hp.shape.N != d->N() || hp.shape.W != d->W)
-        return fail(TGP_E_INVALID, "plan for %lld points in rows of %lld used on a %d x %d grid",
-                    (long long)hp.shape.N, (long long)hp.shape.W, d->W, d->H);
     EvalParams p{};
-    p.code = pl->prog.code;
-    p.group_off = pl->prog.group_off;
-    p.item_group = pl->prog.group_order;
-    p.n_items = hp.n_items;
-    p.n_tiles = hp.n_tiles;
-    p.warps_per_tile = hp.shape.threads / 32;
-    p.N = d->N();
-    p.W = d->W;
-    p.H = d->H;
-    p.xlo = d->xlo;
-    p.xhi = d->xhi;
-    p.ylo = d->ylo;
-    p.yhi = d->yhi;
-    p.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
-    p.partial = pl->partial.p;
-    p.out = out;
-    p.cache = pl->h_table.empty() ? nullptr : pl->table.p;
-    p.counter = pl->counter.p;
+    p.trig_rad = trig_rad;
     p.n_queues = n_queues(c);
-    p.local_items = queue_local_items(p.n_items, p.n_queues);
-    p.n_slots = hp.n_slots;
-    p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
-    p.trig_rad = trig_radians(c) ? 1 : 0;
-    p.out_stride = p.N;
-    p.coltab = hp.col_plan ? pl->ctab.p : nullptr;
-    p.col_stride = hp.col_stride;
-    p.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
-    p.row_stride = hp.row_stride;
-    if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
-    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * kQueueWords * sizeof(int32_t), s));
-    const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (timed) {
-        if (c->ev_pending.size() >= 4096) {
-            int rc = drain_events(c);
-            if (rc) return rc;
-        }
-        if (c->ev_free.empty()) {
-            CUDA_TRY(cudaEventCreate(&ev.first));
-            CUDA_TRY(cudaEventCreate(&ev.second));
-        } else {
-            ev = c->ev_free.back();
-            c->ev_free.pop_back();
-        }
-        CUDA_TRY(cudaEventRecord(ev.first, s));
-    }
     if (hp.col_plan) {
         // the column tables first: phenotypes of their subtrees on one row of
         // W points (same x coordinates; no y below them)
@@ -841,6 +796,64 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
         CUDA_TRY(launch_eval(q, rh.shape.K, true, use_ext(c, rh), pl->rgrid, rh.shape.threads, pl->rsmem, s));
         c->stats.launches++;
     }
+    return TGP_OK;
+}
+
+int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, cudaStream_t s) {
+    const HostPlan& hp = pl->hp;
+    // the plan's work units cover the grid only for the row length it was built for
+    if (hp.shape.N != d->N() || hp.shape.W != d->W)
+        return fail(TGP_E_INVALID, "plan for %lld points in rows of %lld used on a %d x %d grid",
+                    (long long)hp.shape.N, (long long)hp.shape.W, d->W, d->H);
+    EvalParams p{};
+    p.code = pl->prog.code;
+    p.group_off = pl->prog.group_off;
+    p.item_group = pl->prog.group_order;
+    p.n_items = hp.n_items;
+    p.n_tiles = hp.n_tiles;
+    p.warps_per_tile = hp.shape.threads / 32;
+    p.N = d->N();
+    p.W = d->W;
+    p.H = d->H;
+    p.xlo = d->xlo;
+    p.xhi = d->xhi;
+    p.ylo = d->ylo;
+    p.yhi = d->yhi;
+    p.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+    p.partial = pl->partial.p;
+    p.out = out;
+    p.cache = pl->h_table.empty() ? nullptr : pl->table.p;
+    p.counter = pl->counter.p;
+    p.n_queues = n_queues(c);
+    p.local_items = queue_local_items(p.n_items, p.n_queues);
+    p.n_slots = hp.n_slots;
+    p.max_items_per_cta = (int32_t)std::min<int64_t>(hp.n_items, INT32_MAX);
+    p.trig_rad = trig_radians(c) ? 1 : 0;
+    p.out_stride = p.N;
+    p.coltab = hp.col_plan ? pl->ctab.p : nullptr;
+    p.col_stride = hp.col_stride;
+    p.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
+    p.row_stride = hp.row_stride;
+    if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
+    CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * kQueueWords * sizeof(int32_t), s));
+    const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (timed) {
+        if (c->ev_pending.size() >= 4096) {
+            int rc = drain_events(c);
+            if (rc) return rc;
+        }
+        if (c->ev_free.empty()) {
+            CUDA_TRY(cudaEventCreate(&ev.first));
+            CUDA_TRY(cudaEventCreate(&ev.second));
+        } else {
+            ev = c->ev_free.back();
+            c->ev_free.pop_back();
+        }
+        CUDA_TRY(cudaEventRecord(ev.first, s));
+    }
+    int rc = launch_tables(c, pl, d, p.trig_rad, s);
+    if (rc) return rc;
     CUDA_TRY(launch_eval(p, hp.shape.K, pheno, use_ext(c, hp), pl->grid, hp.shape.threads, pl->smem, s));
     if (timed) {
         CUDA_TRY(cudaEventRecord(ev.second, s));
@@ -1052,6 +1065,119 @@ int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr
     p->ir = std::move(ir);
     p->preplanned = std::move(pre);
     adopt_ir(ctx, p);
+    return TGP_OK;
+}
+
+int launch_shape(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, int* K, int* threads) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    const PlanShape sh = choose_shape(ctx, p->ir, d->N(), d->W);
+    *K = sh.K;
+    *threads = sh.threads;
+    return TGP_OK;
+}
+
+int fitness_fused(tgp_ctx* ctx, const std::vector<FusedSegment>& segs, void* stream, SegParams* segs_dev,
+                  int32_t* counter_dev) {
+    if (!ctx || !segs_dev || !counter_dev) return fail(TGP_E_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<SegParams> hs;
+    std::vector<Plan*> plans;
+    std::vector<const Domain*> doms;
+    int K = 0, threads = 0;
+    bool ext = false;
+    size_t smem = 0;
+    int64_t items = 0;
+    for (const FusedSegment& f : segs) {
+        Population* p = find(ctx->pops, f.pop);
+        Domain* d = find(ctx->domains, f.domain);
+        if (!p || !d || !f.rmse_dev) return fail(TGP_E_INVALID, "unknown population or domain handle, or NULL rmse_dev");
+        if (p->ir.roots.empty()) continue;
+        Plan* pl = nullptr;
+        rc = get_plan(ctx, p, d, false, s, &pl);
+        if (rc) return rc;
+        const HostPlan& hp = pl->hp;
+        if (plans.empty()) {
+            K = hp.shape.K;
+            threads = hp.shape.threads;
+        } else if (hp.shape.K != K || hp.shape.threads != threads) {
+            return fail(TGP_E_INVALID, "fused segments plan to different launch shapes (%d x %d, %d x %d)", K,
+                        threads, hp.shape.K, hp.shape.threads);
+        }
+        ext = ext || use_ext(ctx, hp);
+        smem = std::max(smem, pl->smem);
+        SegParams sp{};
+        sp.code = pl->prog.code;
+        sp.group_off = pl->prog.group_off;
+        sp.item_group = pl->prog.group_order;
+        sp.item0 = items;
+        sp.n_tiles = hp.n_tiles;
+        sp.W = d->W;
+        sp.H = d->H;
+        sp.xlo = d->xlo;
+        sp.xhi = d->xhi;
+        sp.ylo = d->ylo;
+        sp.yhi = d->yhi;
+        sp.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+        sp.partial = pl->partial.p;
+        sp.coltab = hp.col_plan ? pl->ctab.p : nullptr;
+        sp.col_stride = hp.col_stride;
+        sp.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
+        sp.row_stride = hp.row_stride;
+        hs.push_back(sp);
+        plans.push_back(pl);
+        doms.push_back(d);
+        items += hp.n_items;
+    }
+    if (plans.empty()) return TGP_OK;
+    const int32_t trig = trig_radians(ctx) ? 1 : 0;
+    for (size_t i = 0; i < plans.size(); ++i) {   // each domain's target, then its tables
+        const Domain* d = doms[i];
+        if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
+        if (plans[i]->hp.col_plan || plans[i]->hp.row_plan) {
+            CUDA_TRY(cudaMemsetAsync(plans[i]->counter.p, 0, 3 * kQueueWords * sizeof(int32_t), s));
+            rc = launch_tables(ctx, plans[i], d, trig, s);
+            if (rc) return rc;
+        }
+    }
+    // the segment table (staged from host memory before this call returns)
+    CUDA_TRY(cudaMemcpyAsync(segs_dev, hs.data(), hs.size() * sizeof(SegParams), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(counter_dev, 0, kQueueWords * sizeof(int32_t), s));
+    EvalParams p{};
+    p.n_items = items;
+    p.warps_per_tile = threads / 32;
+    p.counter = counter_dev;
+    p.n_queues = n_queues(ctx);
+    p.local_items = queue_local_items(items, p.n_queues);
+    p.max_items_per_cta = (int32_t)std::min<int64_t>(items, INT32_MAX);
+    p.trig_rad = trig;
+    p.segs = segs_dev;
+    p.n_segs = (int32_t)hs.size();
+    int bps = 0;
+    rc = occupancy(ctx, K, false, ext, threads, smem, &bps);
+    if (rc) return rc;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)bps * std::max(ctx->sms, 1)));
+    CUDA_TRY(launch_eval(p, K, false, ext, grid, threads, smem, s));
+    ctx->stats.launches++;
+    size_t k = 0;
+    for (const FusedSegment& f : segs) {
+        Population* pop = find(ctx->pops, f.pop);
+        if (pop->ir.roots.empty()) continue;
+        FinalizeParams fp{};
+        fp.partial = plans[k]->partial.p;
+        fp.per_tree = (int64_t)plans[k]->hp.n_tiles * (threads / 32);
+        fp.n_trees = (int32_t)pop->ir.roots.size();
+        fp.n_points = (double)doms[k]->N();
+        fp.rmse = f.rmse_dev;
+        CUDA_TRY(launch_finalize(fp, s));
+        ctx->stats.launches++;
+        ++k;
+    }
     return TGP_OK;
 }
 

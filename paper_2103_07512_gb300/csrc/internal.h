@@ -3,6 +3,7 @@
 #pragma once
 #include <memory>
 #include <mutex>
+#include <vector>
 
 #include "../../include/tgp.h"
 #include "compiler.h"
@@ -66,6 +67,28 @@ int replace_population(tgp_ctx* ctx, tgp_handle pop, PopIR&& ir, std::shared_ptr
 // Device bytes one fitness launch of `ir` on N points in rows of W needs
 // beyond its domain (partial sums, bytecode, results).
 int64_t estimate_bytes(tgp_ctx* ctx, const PopIR& ir, int64_t N, int64_t W);
+
+// One population on one domain in a fused launch: its RMSE values go to
+// rmse_dev (n_trees doubles of device memory).
+struct FusedSegment {
+    tgp_handle pop = 0;
+    tgp_handle domain = 0;
+    double* rmse_dev = nullptr;
+};
+
+// The fitness of several populations, each on its own domain, as tgp_fitness_dev
+// would compute them, in one interpreter launch on `stream` (preceded by the
+// domains' table launches, followed by one finalize per segment).  Every
+// population must plan to the same points per thread and threads per block
+// on its domain; results are then bitwise those of separate calls.
+// segs_dev: device memory for segs.size() SegParams; counter_dev: kQueueWords
+// int32 of device memory (both the caller's, not used by concurrent launches).
+int fitness_fused(tgp_ctx* ctx, const std::vector<FusedSegment>& segs, void* stream, SegParams* segs_dev,
+                  int32_t* counter_dev);
+
+// The launch shape (points per thread, threads per block) tgp_fitness_dev
+// would use for `pop` on `domain`.
+int launch_shape(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, int* K, int* threads);
 
 // Records the calling thread's error message; returns `code`.
 int set_error(int code, const char* fmt, ...);

@@ -1,6 +1,6 @@
 // server.cpp -- serving loop: evaluation jobs arrive over time, are admitted
-// by device memory, fused per domain into population launches, and run on
-// several streams at once.
+// by device memory, fused (per domain into populations, across domains into
+// one interpreter launch) and run on several streams at once.
 //
 // Threads and locks.  Callers submit and wait; one worker thread admits and
 // launches; a CUDA host function enqueued after each launch's result copy
@@ -86,16 +86,29 @@ struct Job {
     tgp_job_info info{};
 };
 
+// Domains one fused launch may span at most.
+constexpr int kMaxSegments = 64;
+
+// One domain of a launch: its resident entry and the batch's jobs on it.
+struct Segment {
+    DomainKey key;
+    Resident* dom = nullptr;
+    bool load = false;   // the launch loads the domain first
+    std::vector<Job*> jobs;
+};
+
 struct Slot {
     tgp_server* srv = nullptr;
     cudaStream_t stream = nullptr;
-    tgp_handle pop = 0;
+    std::vector<tgp_handle> pops;   // one population per segment, kept for their buffers
     double* d_rmse = nullptr;
     double* h_rmse = nullptr;
     size_t cap = 0;
+    SegParams* d_segs = nullptr;    // segment table of a fused launch
+    int32_t* d_counter = nullptr;   // its work-queue heads
     bool busy = false;
-    std::vector<Job*> jobs;
-    Resident* dom = nullptr;
+    std::vector<Job*> jobs;         // segment by segment
+    std::vector<Resident*> doms;
     int64_t bytes = 0;
 };
 
@@ -149,8 +162,12 @@ void CUDART_CB on_launch_done(void* arg) {
     }
     s->jobs.clear();
     s->busy = false;
-    s->dom->in_use--;
-    s->dom->last_use = ++srv->tick;
+    const int64_t tick = ++srv->tick;
+    for (Resident* r : s->doms) {
+        r->in_use--;
+        r->last_use = tick;
+    }
+    s->doms.clear();
     srv->st.bytes_in_use -= s->bytes;
     s->bytes = 0;
     srv->in_flight--;
@@ -170,20 +187,24 @@ void fail_jobs(tgp_server* srv, Slot* s, int rc) {
     }
     s->jobs.clear();
     s->busy = false;
-    s->dom->in_use--;
+    for (Resident* r : s->doms) r->in_use--;
+    s->doms.clear();
     srv->st.bytes_in_use -= s->bytes;
     s->bytes = 0;
     srv->in_flight--;
     srv->done.notify_all();
 }
 
-// Enqueues one launch: loads the domain if needed, merges the jobs' trees
-// into one population, runs the fitness and copies the RMSE values back.
-// Called by the worker without srv->mu.
-int launch(tgp_server* srv, Slot* s, std::vector<Job*>& batch, const DomainKey& key, bool load) {
+// Enqueues one launch: loads the segments' domains that are not resident,
+// merges each segment's jobs into one population, runs the fitness of all
+// segments (one fused interpreter launch when there are several) and copies
+// the RMSE values back.  Called by the worker without srv->mu.
+int launch(tgp_server* srv, Slot* s, std::vector<Segment>& segs) {
     tgp_ctx* ctx = srv->ctx;
     SRV_TRY(cudaSetDevice(srv->device));
-    if (load) {
+    for (Segment& sg : segs) {
+        if (!sg.load) continue;
+        const DomainKey& key = sg.key;
         tgp_target_tokens tt{};
         const void* target = nullptr;
         if (key.kind == TGP_TARGET_TOKENS) {
@@ -202,23 +223,13 @@ int launch(tgp_server* srv, Slot* s, std::vector<Job*>& batch, const DomainKey& 
                                        false, &h);
         if (rc) return rc;
         std::lock_guard<std::mutex> g(srv->mu);
-        s->dom->h = h;
+        sg.dom->h = h;
         srv->st.domains_loaded++;
         srv->st.domain_load_ns += now_ns() - t0;
     }
-    PopIR ir;
-    std::shared_ptr<internal::PrePlan> pre;
-    if (batch.size() == 1) {
-        ir = std::move(batch[0]->ir);
-        pre = std::move(batch[0]->plan);
-    } else {
-        for (Job* j : batch) {
-            append_population(ir, j->ir);
-            j->ir = PopIR();
-            j->plan.reset();
-        }
-    }
-    const size_t T = ir.roots.size();
+    size_t T = 0;
+    for (const Segment& sg : segs)
+        for (const Job* j : sg.jobs) T += (size_t)j->n_trees;
     if (T > s->cap) {
         if (s->d_rmse) cudaFree(s->d_rmse);
         if (s->h_rmse) cudaFreeHost(s->h_rmse);
@@ -229,12 +240,35 @@ int launch(tgp_server* srv, Slot* s, std::vector<Job*>& batch, const DomainKey& 
         SRV_TRY(cudaMallocHost(&s->h_rmse, T * sizeof(double)));
         s->cap = T;
     }
-    int rc = s->pop ? internal::replace_population(ctx, s->pop, std::move(ir), std::move(pre))
-                    : internal::adopt_population(ctx, std::move(ir), &s->pop, std::move(pre));
-    if (rc) return rc;
+    std::vector<internal::FusedSegment> fused;
+    size_t off = 0;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        Segment& sg = segs[i];
+        PopIR ir;
+        std::shared_ptr<internal::PrePlan> pre;
+        if (sg.jobs.size() == 1) {
+            ir = std::move(sg.jobs[0]->ir);
+            pre = std::move(sg.jobs[0]->plan);
+        } else {
+            for (Job* j : sg.jobs) {
+                append_population(ir, j->ir);
+                j->ir = PopIR();
+                j->plan.reset();
+            }
+        }
+        const size_t nt = ir.roots.size();
+        if (i == s->pops.size()) s->pops.push_back(0);
+        int rc = s->pops[i] ? internal::replace_population(ctx, s->pops[i], std::move(ir), std::move(pre))
+                            : internal::adopt_population(ctx, std::move(ir), &s->pops[i], std::move(pre));
+        if (rc) return rc;
+        fused.push_back(internal::FusedSegment{s->pops[i], sg.dom->h, s->d_rmse + off});
+        off += nt;
+    }
     const int64_t t = now_ns();
-    for (Job* j : batch) j->info.launch_ns = t;
-    rc = tgp_fitness_dev(ctx, s->pop, s->dom->h, s->stream, s->d_rmse);
+    for (const Segment& sg : segs)
+        for (Job* j : sg.jobs) j->info.launch_ns = t;
+    int rc = segs.size() == 1 ? tgp_fitness_dev(ctx, fused[0].pop, fused[0].domain, s->stream, s->d_rmse)
+                              : internal::fitness_fused(ctx, fused, s->stream, s->d_segs, s->d_counter);
     if (rc) return rc;
     SRV_TRY(cudaMemcpyAsync(s->h_rmse, s->d_rmse, T * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SRV_TRY(cudaLaunchHostFunc(s->stream, on_launch_done, s));
@@ -318,57 +352,97 @@ void worker_main(tgp_server* srv) {
         if (!resident && srv->domains.size() >= kMaxResidentDomains) {
             if (release_idle_domains(srv, lk, kResidentLowMark, 0, nullptr)) continue;
         }
-        // the batch: the head and every later queued job on the same domain
-        std::vector<Job*> batch{head};
+        // the batch: the head, every later queued job on the head's domain,
+        // and queued jobs on other domains (resident, or loadable within the
+        // budget) that plan to the head's launch shape -- one fused launch
+        std::vector<Segment> segs(1);
+        segs.reserve(kMaxSegments);
+        segs[0].key = key;
+        segs[0].jobs.push_back(head);
         int64_t trees = head->n_trees;
         int64_t bytes = need;
+        const bool fusable = head->plan != nullptr;
+        const int hK = fusable ? head->plan->shape.K : 0, hT = fusable ? head->plan->shape.threads : 0;
         for (auto it = std::next(srv->pending.begin()); it != srv->pending.end(); ++it) {
             Job* j = *it;
-            if (j->key < key || key < j->key) continue;
             if (trees + j->n_trees > srv->cfg.max_batch_trees) continue;
-            if (srv->st.bytes_in_use + bytes + j->est > budget) continue;
-            batch.push_back(j);
+            Segment* sg = nullptr;
+            for (Segment& x : segs)
+                if (!(x.key < j->key) && !(j->key < x.key)) { sg = &x; break; }
+            int64_t add = j->est;
+            if (!sg) {
+                if (!fusable || !j->plan || j->plan->shape.K != hK || j->plan->shape.threads != hT) continue;
+                if ((int)segs.size() >= kMaxSegments) continue;
+                auto jr = srv->domains.find(j->key);
+                if (jr != srv->domains.end()) {
+                    if (jr->second.h == 0) continue;   // being loaded by a launch in flight
+                } else {
+                    add += j->dom_bytes;
+                }
+            }
+            if (srv->st.bytes_in_use + bytes + add > budget) continue;
+            if (!sg) {
+                segs.emplace_back();
+                segs.back().key = j->key;
+                sg = &segs.back();
+            }
+            sg->jobs.push_back(j);
             trees += j->n_trees;
-            bytes += j->est;
+            bytes += add;
         }
-        for (Job* j : batch) srv->pending.erase(std::find(srv->pending.begin(), srv->pending.end(), j));
-        Resident* r;
-        if (resident) {
-            r = &rit->second;
-        } else {
-            r = &srv->domains[key];
-            r->bytes = head->dom_bytes;
-            srv->st.domains_resident = (int64_t)srv->domains.size();
+        size_t n_jobs = 0;
+        for (Segment& sg : segs)
+            for (Job* j : sg.jobs) {
+                srv->pending.erase(std::find(srv->pending.begin(), srv->pending.end(), j));
+                ++n_jobs;
+            }
+        int64_t dom_new = 0;   // bytes of the domains this launch loads
+        slot->jobs.clear();
+        slot->doms.clear();
+        for (Segment& sg : segs) {
+            auto dit = srv->domains.find(sg.key);
+            if (dit == srv->domains.end()) {
+                Resident& r = srv->domains[sg.key];
+                r.bytes = sg.jobs[0]->dom_bytes;
+                dom_new += r.bytes;
+                sg.dom = &r;
+                sg.load = true;
+            } else {
+                sg.dom = &dit->second;
+            }
+            sg.dom->in_use++;
+            slot->doms.push_back(sg.dom);
+            for (Job* j : sg.jobs) slot->jobs.push_back(j);
         }
-        r->in_use++;
+        srv->st.domains_resident = (int64_t)srv->domains.size();
         slot->busy = true;
-        slot->jobs = batch;
-        slot->dom = r;
-        slot->bytes = bytes - (resident ? 0 : head->dom_bytes);
+        slot->bytes = bytes - dom_new;
         srv->st.bytes_in_use += bytes;
         srv->st.max_bytes_in_use = std::max(srv->st.max_bytes_in_use, srv->st.bytes_in_use);
         const int64_t bno = srv->st.batches++;
-        srv->st.max_batch_jobs = std::max<int64_t>(srv->st.max_batch_jobs, (int64_t)batch.size());
+        srv->st.max_batch_jobs = std::max<int64_t>(srv->st.max_batch_jobs, (int64_t)n_jobs);
+        srv->st.max_batch_domains = std::max<int64_t>(srv->st.max_batch_domains, (int64_t)segs.size());
         srv->in_flight++;
         srv->st.max_in_flight = std::max<int64_t>(srv->st.max_in_flight, srv->in_flight);
-        for (Job* j : batch) {
+        for (Job* j : slot->jobs) {
             j->info.batch = bno;
-            j->info.batch_jobs = (int32_t)batch.size();
+            j->info.batch_jobs = (int32_t)n_jobs;
         }
-        const DomainKey kcopy = key;
         lk.unlock();
         const int64_t t_busy = now_ns();
-        int rc = launch(srv, slot, batch, kcopy, !resident);
+        int rc = launch(srv, slot, segs);
         if (rc) cudaStreamSynchronize(slot->stream);   // nothing of this launch still runs
         lk.lock();
         srv->st.worker_busy_ns += now_ns() - t_busy;
         if (rc) {
-            fail_jobs(srv, slot, rc);   // drops the launch's use and bytes
-            if (!resident && r->h == 0) {   // the domain never loaded
-                srv->st.bytes_in_use -= r->bytes;
-                srv->domains.erase(kcopy);
-                srv->st.domains_resident = (int64_t)srv->domains.size();
+            fail_jobs(srv, slot, rc);   // drops the launch's uses and bytes
+            for (Segment& sg : segs) {
+                if (sg.load && sg.dom->h == 0) {   // the domain never loaded
+                    srv->st.bytes_in_use -= sg.dom->bytes;
+                    srv->domains.erase(sg.key);
+                }
             }
+            srv->st.domains_resident = (int64_t)srv->domains.size();
         }
     }
 }
@@ -413,6 +487,8 @@ int tgp_server_create(tgp_ctx* ctx, const tgp_server_config* cfg, tgp_server** o
         SRV_TRY(cudaMalloc(&s->d_rmse, cap * sizeof(double)));
         SRV_TRY(cudaMallocHost(&s->h_rmse, cap * sizeof(double)));
         s->cap = cap;
+        SRV_TRY(cudaMalloc(&s->d_segs, kMaxSegments * sizeof(SegParams)));
+        SRV_TRY(cudaMalloc(&s->d_counter, kQueueWords * sizeof(int32_t)));
         srv->slots.push_back(std::move(s));
     }
     tgp_server* raw = srv.get();
@@ -432,10 +508,13 @@ int tgp_server_destroy(tgp_server* srv) {
     cudaSetDevice(srv->device);
     for (auto& s : srv->slots) {
         if (s->stream) cudaStreamSynchronize(s->stream);
-        if (s->pop) tgp_release_population(srv->ctx, s->pop);
+        for (tgp_handle p : s->pops)
+            if (p) tgp_release_population(srv->ctx, p);
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->d_rmse) cudaFree(s->d_rmse);
         if (s->h_rmse) cudaFreeHost(s->h_rmse);
+        if (s->d_segs) cudaFree(s->d_segs);
+        if (s->d_counter) cudaFree(s->d_counter);
     }
     for (auto& kv : srv->domains)
         if (kv.second.h) tgp_release_domain(srv->ctx, kv.second.h);

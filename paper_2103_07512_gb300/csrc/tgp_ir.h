@@ -142,7 +142,7 @@ struct IrIns {
 #define TGP_MINB4 10
 #endif
 #ifndef TGP_MINB2
-#define TGP_MINB2 12
+#define TGP_MINB2 10
 #endif
 __host__ __device__ constexpr int target_ctas_per_sm(int K) {
     return K >= 16 ? TGP_MINB16 : K >= 8 ? TGP_MINB8 : K >= 4 ? TGP_MINB4 : TGP_MINB2;
@@ -171,6 +171,25 @@ constexpr float kResidualScale = 0x1p-80f;
 constexpr int kMaxQueues = 256;
 constexpr int kQueueWords = kMaxQueues + 1;   // chunk heads, then the global head
 
+// One domain of a launch that fuses several (fitness only): its items are
+// [item0, next segment's item0); its own program, grid, target, partial sums
+// and tables.
+struct SegParams {
+    const Ins* code;
+    const int64_t* group_off;
+    const int32_t* item_group;
+    int64_t item0;
+    int32_t n_tiles;
+    int32_t W, H;
+    float xlo, xhi, ylo, yhi;
+    const float* target;        // [N] or nullptr for the inline Pagie polynomial
+    float* partial;             // [its trees][n_tiles][warps]
+    const float* coltab;
+    int64_t col_stride;
+    const float* rowtab;
+    int64_t row_stride;
+};
+
 // Parameters of one interpreter launch.
 struct EvalParams {
     const Ins* code;            // all groups back to back
@@ -197,6 +216,8 @@ struct EvalParams {
     const float* rowtab;        // row tables (F_ROW): entry e at rowtab + e * row_stride, or nullptr
     int64_t row_stride;         // floats per row-table entry
     int64_t out_stride;         // floats between the phenotype rows of two trees (N, or a table's stride)
+    const SegParams* segs;      // a launch fusing several domains: [n_segs] segments, or nullptr
+    int32_t n_segs;             // (the fields above from code to row_stride are then unused)
 };
 
 struct FinalizeParams {

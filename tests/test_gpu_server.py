@@ -7,7 +7,7 @@ import pytest
 import oracle
 import paper_2103_07512_gb300 as tgp
 from paper_2103_07512_gb300 import inputs as I
-from parity import check_population
+from parity import check_population, oracle_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -42,9 +42,56 @@ def test_alone_equals_in_mix():
             st = srv.stats()
         assert st["completed"] == len(jobs) and st["failed"] == 0
         assert st["batches"] < len(jobs) and st["max_batch_jobs"] > 1
+        assert st["max_batch_domains"] > 1          # launches fused jobs of different domains
         for k, (a, (m, info)) in enumerate(zip(alone, mixed)):
             assert np.array_equal(a.view(np.int64), m.view(np.int64)), f"job {k}"
             assert info["submit_ns"] <= info["launch_ns"] <= info["done_ns"]
+
+
+def test_fused_domains_alone_equals_in_mix():
+    """Jobs on many different grids of one launch shape (K = 8: 2^18 points
+    and more) and both target kinds, queued at once: fused across domains
+    into few launches, each result bitwise that of the job alone."""
+    rng = np.random.default_rng(47)
+    jobs = []
+    for k in range(12):
+        side = int(rng.integers(512, 800))
+        tok = I.to_tokens(I.ramped_half_and_half(int(rng.integers(10, 40)), 2, 6, rng))
+        target = None
+        if k % 3 == 0:
+            tt = I.to_tokens([I._full(rng, 3, I.FUNCTIONS)])
+            target = (tt.ops, tt.imm, tt.order)
+        jobs.append({"tok": tok, "W": side, "H": side + k, "target_tokens": target})
+    with tgp.Context() as ctx:
+        with tgp.Server(ctx, streams=1) as srv:
+            alone = [srv.wait(submit(srv, j))[0] for j in jobs]
+        with tgp.Server(ctx, streams=1) as srv:    # one slot: the queue builds up behind the first launch
+            ids = [submit(srv, j) for j in jobs]
+            mixed = [srv.wait(i) for i in ids]
+            st = srv.stats()
+    assert st["completed"] == len(jobs) and st["max_batch_domains"] >= 3, st
+    for k, (a, (m, info)) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(a.view(np.int64), m.view(np.int64)), f"job {k}"
+    assert max(info["batch_jobs"] for _, info in mixed) >= 3
+
+
+def test_server_large_job_matches_oracle():
+    """A job at the serving workload's upper end (1,000 RHH trees of depth
+    2-10 on 2048x2048 = 2^22 points) through the server: every tree on 16,384
+    sampled points, and 48 sampled trees' fitness over all points, against the
+    oracle."""
+    rng = np.random.default_rng(48)
+    tok = I.to_tokens(I.ramped_half_and_half(1000, 2, 10, rng))
+    g = I.Grid(2048, 2048)
+    oracle_pool()
+    with tgp.Context() as ctx:
+        with tgp.Server(ctx, streams=2) as srv:
+            r, info = srv.wait(submit(srv, {"tok": tok, "W": g.W, "H": g.H, "target_tokens": None}))
+        pts = np.concatenate([np.sort(rng.choice(g.N, 16384, replace=False)), [0, g.N - 1]])
+        trees = np.sort(rng.choice(tok.n_trees, 48, replace=False))
+        c = check_population(ctx, tok, g, r, "serving, 1000 trees on 2^22 points", budget="serving", elem_pts=pts,
+                             fit_trees=trees, point_chunks=8)
+    assert c["fitness"]["trees"] == 48
 
 
 def test_server_results_match_oracle():

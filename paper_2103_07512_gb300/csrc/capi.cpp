@@ -96,6 +96,7 @@ struct Domain {
     float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
     int32_t kind = TGP_TARGET_PAGIE;
     DevBuf<float> target;
+    DevBuf<float> pagie_x;   // Pagie: x^4/(1+x^4) per column, padded to a multiple of 16
     // cross-call subtree cache of this domain, keyed by the node's id in the
     // context-wide DAG (exact structural identity)
     std::unordered_map<int32_t, std::unique_ptr<CacheEntry>> cache;
@@ -820,6 +821,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.ylo = d->ylo;
     p.yhi = d->yhi;
     p.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+    p.pagie_x = d->pagie_x.p;
     p.partial = pl->partial.p;
     p.out = out;
     p.cache = pl->h_table.empty() ? nullptr : pl->table.p;
@@ -942,6 +944,7 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     v->W = d->W; v->H = d->H;
     v->xlo = d->xlo; v->xhi = d->xhi; v->ylo = d->ylo; v->yhi = d->yhi;
     v->target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+    v->pagie_x = d->pagie_x.p;
     v->shape = choose_shape(ctx, p->ir, d->N(), d->W);
     v->sms = ctx->sms;
     v->device = ctx->device;
@@ -969,6 +972,19 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
     const int64_t N = d->N();
     if (target_kind == TGP_TARGET_PAGIE) {
         if (target) return fail(TGP_E_INVALID, "target must be NULL for the Pagie target");
+        if (!ctx->host_only) {   // the x part of Eq. 1 once per column
+            const int32_t n = (W + 15) / 16 * 16;
+            CUDA_TRY(d->pagie_x.ensure((size_t)n));
+            CUDA_TRY(launch_pagie_columns(W, xlo, xhi, d->pagie_x.p, n, s));
+            if (sync) {
+                CUDA_TRY(cudaStreamSynchronize(s));
+            } else {   // later uses of the domain, on any stream, wait for it
+                auto f = std::make_shared<Fence>();
+                CUDA_TRY(cudaEventCreateWithFlags(&f->ev, cudaEventDisableTiming));
+                CUDA_TRY(cudaEventRecord(f->ev, s));
+                d->ready = std::move(f);
+            }
+        }
     } else if (target_kind == TGP_TARGET_TENSOR) {
         if (!target) return fail(TGP_E_INVALID, "target tensor is NULL");
         CUDA_TRY(d->target.ensure((size_t)N));
@@ -1124,6 +1140,7 @@ int fitness_fused(tgp_ctx* ctx, const std::vector<FusedSegment>& segs, void* str
         sp.ylo = d->ylo;
         sp.yhi = d->yhi;
         sp.target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
+        sp.pagie_x = d->pagie_x.p;
         sp.partial = pl->partial.p;
         sp.coltab = hp.col_plan ? pl->ctab.p : nullptr;
         sp.col_stride = hp.col_stride;

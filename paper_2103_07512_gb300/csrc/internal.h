@@ -17,6 +17,7 @@ struct View {
     int32_t W = 0, H = 0;
     float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
     const float* target = nullptr;   // device target tensor, nullptr for Pagie
+    const float* pagie_x = nullptr;  // Pagie: the x part per column (nullptr: formed inline)
     PlanShape shape;                 // the shape tgp_fitness would use
     int sms = 0;
     int device = 0;

@@ -18,6 +18,10 @@ cudaError_t eval_occupancy(int K, bool pheno, bool ext, int threads, size_t smem
 // slots, K points per thread.
 size_t eval_smem_bytes(int K, int threads, int n_slots);
 
+// The x part of Eq. 1, x^4 / (1 + x^4) in binary32, at the n_out first columns
+// of a grid of W columns on [xlo, xhi] (columns past W - 1 take column W - 1).
+cudaError_t launch_pagie_columns(int32_t W, float xlo, float xhi, float* out, int32_t n_out, cudaStream_t s);
+
 // Per-tree binary64 reduction of the fitness partials and sqrt(sum / N).
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 

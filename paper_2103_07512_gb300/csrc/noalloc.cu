@@ -137,6 +137,7 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.ylo = v.ylo;
     p.yhi = v.yhi;
     p.target = v.target;
+    p.pagie_x = v.pagie_x;
     p.partial = partial;
     p.out = nullptr;
     p.cache = nullptr;

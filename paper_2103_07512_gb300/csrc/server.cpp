@@ -565,7 +565,9 @@ int tgp_server_submit(tgp_server* srv, const tgp_job* job, int64_t* job_id) {
     // the bytecode is planned here, in the caller's thread, for a launch of
     // this job alone (a fused launch is planned again by the worker)
     internal::preplan(srv->ctx, j->ir, key.N(), key.W, &j->plan);
-    j->dom_bytes = key.kind == TGP_TARGET_TOKENS ? key.N() * (int64_t)sizeof(float) : 0;
+    // a token target's values, and the Pagie column table (x part per column)
+    j->dom_bytes = (key.kind == TGP_TARGET_TOKENS ? key.N() * (int64_t)sizeof(float) : 0) +
+                   (key.W + 15) / 16 * 16 * (int64_t)sizeof(float);
     if (j->est + j->dom_bytes > srv->cfg.hbm_budget_bytes)
         return internal::set_error(TGP_E_BUDGET, "job needs %lld bytes of device memory; the budget is %lld",
                                    (long long)(j->est + j->dom_bytes), (long long)srv->cfg.hbm_budget_bytes);

@@ -183,6 +183,7 @@ struct SegParams {
     int32_t W, H;
     float xlo, xhi, ylo, yhi;
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
+    const float* pagie_x;       // Pagie: x^4/(1+x^4) per column (see EvalParams)
     float* partial;             // [its trees][n_tiles][warps]
     const float* coltab;
     int64_t col_stride;
@@ -202,6 +203,8 @@ struct EvalParams {
     int32_t W, H;
     float xlo, xhi, ylo, yhi;
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
+    const float* pagie_x;       // Pagie: its x part x^4/(1+x^4) at every column, padded to a
+                                // multiple of 16 (the y part is formed per thread), or nullptr
     float* partial;             // [n_trees][n_tiles][warps] fitness partial sums (negated: scaled, see kSumBig)
     float* out;                 // [n_trees][N] phenotypes (phenotype launches)
     float* const* cache;        // cache entry pointers (F_CST / F_CLD), or nullptr

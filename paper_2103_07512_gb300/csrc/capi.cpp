@@ -1308,7 +1308,7 @@ int tgp_compile_population(tgp_ctx* ctx, const int32_t* ops, const float* imm, i
     if (!ctx || !pop_out) return fail(TGP_E_INVALID, "ctx / pop_out is NULL");
     auto pop = std::make_unique<Population>();
     std::string err;
-    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err, simplify_on(ctx));
+    int rc = parse_population(ops, imm, n_imm, tree_off, n_trees, order, pop->ir, err, simplify_on(ctx), &ctx->par);
     if (rc) return fail(rc == -2 ? TGP_E_TOKENS : TGP_E_INVALID, "%s", err.c_str());
     std::lock_guard<std::mutex> g(ctx->mu);
     adopt_ir(ctx, pop.get());

@@ -334,24 +334,17 @@ void append_population(PopIR& dst, const PopIR& src) {
     dst.tree_nodes += src.tree_nodes;
 }
 
-int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
-                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify) {
-    if (n_trees < 0 || n_trees > (1 << 24)) { fmt(err, "n_trees %lld out of range", n_trees); return -1; }
-    if (order != 0 && order != 1) { fmt(err, "order %lld is neither prefix (0) nor postfix (1)", order); return -1; }
-    if (n_imm < 0) { fmt(err, "n_imm %lld is negative", n_imm); return -1; }
-    if (n_trees > 0 && (!ops || !tree_off)) { err = "ops / tree_off must not be NULL"; return -1; }
-    if (n_imm > 0 && !imm) { err = "imm must not be NULL when n_imm > 0"; return -1; }
-    out = PopIR();
-    out.roots.resize(n_trees);
-    out.tree_size.resize(n_trees);
-    out.tree_cost.resize(n_trees);
-    if (n_trees > 0 && tree_off[0] != 0) { fmt(err, "tree_off[0] = %lld, must be 0", tree_off[0]); return -2; }
+// Decodes and hash-conses trees [t0, t1) into `dag` (their constants start
+// at imm[imm0]); fills roots, tree_size, tree_cost and the token count of
+// those trees (indexed from t0).  Returns 0, or -2 with a message.
+static int parse_trees(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off, int32_t t0,
+                       int32_t t1, int64_t imm0, int32_t order, bool simplify, Dag& dag, int32_t* roots,
+                       int32_t* tree_size, float* tree_cost, int64_t* tokens, std::string& err) {
     std::vector<int32_t> stack;
     std::vector<int32_t> dstack;   // depth of each stacked subtree as given (before simplification)
-    int64_t imm_pos = 0;
-    if (n_trees > 0 && tree_off[n_trees] > 0 && tree_off[n_trees] < (int64_t)1 << 26)
-        out.dag.reserve((size_t)tree_off[n_trees]);   // at most one node per token (two for clip)
-    for (int32_t t = 0; t < n_trees; ++t) {
+    int64_t imm_pos = imm0;
+    *tokens = 0;
+    for (int32_t t = t0; t < t1; ++t) {
         int64_t b = tree_off[t], e = tree_off[t + 1];
         int64_t n = e - b;
         if (n <= 0) { fmt(err, "tree %lld is empty (tree_off not increasing)", t); return -2; }
@@ -389,7 +382,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                 for (int a = ar - 1; a >= 0; --a) { k[a] = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[ip++]; std::memcpy(&bits, &v, 4); }
                 dstack.push_back(d);
-                stack.push_back(make_node(out.dag, op, k, bits, simplify));
+                stack.push_back(make_node(dag, op, k, bits, simplify));
             }
         } else {            // prefix: scan backwards, first popped = first operand
             int64_t ip = imm_pos + nconst;
@@ -405,7 +398,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                 for (int a = 0; a < ar; ++a) { k[a] = stack.back(); stack.pop_back(); }
                 if (op == T_CONST) { float v = imm[--ip]; std::memcpy(&bits, &v, 4); }
                 dstack.push_back(d);
-                stack.push_back(make_node(out.dag, op, k, bits, simplify));
+                stack.push_back(make_node(dag, op, k, bits, simplify));
             }
         }
         if (stack.size() != 1) {
@@ -418,13 +411,110 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
             return -2;
         }
         imm_pos += nconst;
-        out.roots[t] = root;
-        out.tree_size[t] = (int32_t)n;
-        out.tree_cost[t] = out.dag.nodes[root].cost;
-        out.tree_nodes += n;
+        roots[t - t0] = root;
+        tree_size[t - t0] = (int32_t)n;
+        tree_cost[t - t0] = dag.nodes[root].cost;
+        *tokens += n;
     }
-    if (imm_pos != n_imm) {
-        fmt(err, "stream has %lld CONST tokens but n_imm = %lld", imm_pos, n_imm);
+    return 0;
+}
+
+// Tokens from which a population is parsed in chunks of trees on the
+// planning workers.
+constexpr int64_t kParallelParseTokens = 1 << 16;
+
+int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify,
+                     const ParallelFor* par) {
+    if (n_trees < 0 || n_trees > (1 << 24)) { fmt(err, "n_trees %lld out of range", n_trees); return -1; }
+    if (order != 0 && order != 1) { fmt(err, "order %lld is neither prefix (0) nor postfix (1)", order); return -1; }
+    if (n_imm < 0) { fmt(err, "n_imm %lld is negative", n_imm); return -1; }
+    if (n_trees > 0 && (!ops || !tree_off)) { err = "ops / tree_off must not be NULL"; return -1; }
+    if (n_imm > 0 && !imm) { err = "imm must not be NULL when n_imm > 0"; return -1; }
+    out = PopIR();
+    out.roots.resize(n_trees);
+    out.tree_size.resize(n_trees);
+    out.tree_cost.resize(n_trees);
+    if (n_trees > 0 && tree_off[0] != 0) { fmt(err, "tree_off[0] = %lld, must be 0", tree_off[0]); return -2; }
+    const int64_t total = n_trees > 0 ? tree_off[n_trees] : 0;
+    int n_chunks = 1;
+    if (par && *par && total >= kParallelParseTokens && n_trees >= 64) {
+        // offsets must increase for the split (a bad offset is reported by the serial parse)
+        bool ok = true;
+        for (int32_t t = 0; t < n_trees && ok; ++t) ok = tree_off[t + 1] > tree_off[t];
+        if (ok) n_chunks = (int)std::min<int64_t>(32, std::min<int64_t>(n_trees / 16, total / (kParallelParseTokens / 4)));
+    }
+    if (n_chunks <= 1) {
+        if (total > 0 && total < (int64_t)1 << 26) out.dag.reserve((size_t)total);   // at most one node per token (two for clip)
+        int64_t tokens = 0;
+        int rc = parse_trees(ops, imm, n_imm, tree_off, 0, n_trees, 0, order, simplify, out.dag, out.roots.data(),
+                             out.tree_size.data(), out.tree_cost.data(), &tokens, err);
+        if (rc) return rc;
+        out.tree_nodes = tokens;
+    } else {
+        // Chunks of consecutive trees are decoded and hash-consed into DAGs of
+        // their own concurrently; their nodes are then interned into the
+        // population DAG chunk by chunk in creation order, which creates the
+        // population's nodes in the order, and with the ids, of a serial
+        // parse (operands of commutative operators are put back in the
+        // canonical order of the population's ids).
+        std::vector<int32_t> t_at(n_chunks + 1);
+        for (int c = 0; c <= n_chunks; ++c) {   // chunks of about equal token counts
+            const int64_t want = total * c / n_chunks;
+            t_at[c] = (int32_t)(std::upper_bound(tree_off, tree_off + n_trees + 1, want) - tree_off - 1);
+        }
+        t_at[0] = 0;
+        t_at[n_chunks] = n_trees;
+        for (int c = 1; c <= n_chunks; ++c) t_at[c] = std::max(t_at[c], t_at[c - 1]);
+        // constants before each chunk
+        std::vector<int64_t> imm_at(n_chunks + 1, 0);
+        (*par)(n_chunks, [&](int c) {
+            int64_t k = 0;
+            for (int64_t i = tree_off[t_at[c]]; i < tree_off[t_at[c + 1]]; ++i) k += ops[i] == T_CONST;
+            imm_at[c + 1] = k;
+        });
+        for (int c = 0; c < n_chunks; ++c) imm_at[c + 1] += imm_at[c];
+        std::vector<Dag> dags(n_chunks);
+        std::vector<int> rcs(n_chunks, 0);
+        std::vector<std::string> errs(n_chunks);
+        std::vector<int64_t> toks(n_chunks, 0);
+        (*par)(n_chunks, [&](int c) {
+            const int64_t n = tree_off[t_at[c + 1]] - tree_off[t_at[c]];
+            dags[c].reserve((size_t)std::max<int64_t>(n, 1));
+            rcs[c] = parse_trees(ops, imm, n_imm, tree_off, t_at[c], t_at[c + 1], imm_at[c], order, simplify, dags[c],
+                                 out.roots.data() + t_at[c], out.tree_size.data() + t_at[c],
+                                 out.tree_cost.data() + t_at[c], &toks[c], errs[c]);
+        });
+        for (int c = 0; c < n_chunks; ++c) {   // the first failing tree's message, as a serial parse gives
+            if (rcs[c]) {
+                err = errs[c];
+                return rcs[c];
+            }
+        }
+        size_t nodes = 0;
+        for (const Dag& d : dags) nodes += d.size();
+        out.dag.reserve(nodes);
+        std::vector<int32_t> id;
+        for (int c = 0; c < n_chunks; ++c) {
+            const Dag& d = dags[c];
+            id.assign(d.size(), -1);
+            for (size_t i = 0; i < d.size(); ++i) {
+                const DagNode& x = d.nodes[i];
+                int32_t k[kMaxKids];
+                for (int j = 0; j < kMaxKids; ++j) k[j] = x.kid[j] >= 0 ? id[x.kid[j]] : -1;
+                if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && k[1] < k[0])
+                    std::swap(k[0], k[1]);
+                id[i] = out.dag.intern(x.op, k[0], k[1], x.imm, k[2]);
+            }
+            for (int32_t t = t_at[c]; t < t_at[c + 1]; ++t) out.roots[t] = id[out.roots[t]];
+            out.tree_nodes += toks[c];
+        }
+    }
+    if (n_trees > 0 && total != out.tree_nodes) { err = "internal: token count"; return -1; }
+    int64_t nconst_all = 0;
+    for (int64_t i = 0; i < total; ++i) nconst_all += ops[i] == T_CONST;
+    if (nconst_all != n_imm) {
+        fmt(err, "stream has %lld CONST tokens but n_imm = %lld", nconst_all, n_imm);
         return -2;
     }
     if (simplify) compact(out);

@@ -56,8 +56,12 @@ struct PopIR {
 // Validates and hash-conses a token population.  Returns 0, or -2 (tokens) /
 // -1 (argument) with a message in err.  With `simplify`, every node goes
 // through intern_simplified (limits apply to the trees as given).
+// With `par` (and a large population), chunks of trees are parsed
+// concurrently; the result equals a serial parse (same nodes, same ids).
+using ParallelFor = std::function<void(int n, const std::function<void(int)>& body)>;
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
-                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify = true);
+                     int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify = true,
+                     const ParallelFor* par = nullptr);
 
 // Hash-conses one node after exact algebraic simplification (constant
 // folding, identities, canonical operand order; see compiler.cpp).  The
@@ -142,9 +146,8 @@ struct CacheView {
 std::vector<int32_t> evaluated_nodes(const PopIR& pop, const CacheView& cv);
 
 // Partitions the trees into shape.n_groups groups and emits their bytecode.
-// Runs body(i) for every i in [0, n), possibly concurrently, and returns
-// when all calls have returned.
-using ParallelFor = std::function<void(int n, const std::function<void(int)>& body)>;
+// A ParallelFor runs body(i) for every i in [0, n), possibly concurrently,
+// and returns when all calls have returned.
 
 // With `par`, the tree groups are planned concurrently (each group's plan
 // depends on its own trees only, so the result is the same); a cache view

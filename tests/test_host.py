@@ -561,6 +561,37 @@ def test_concurrent_group_planning_gives_the_serial_bytecode(name):
             assert len(oa) > 2 or n_points == 1
 
 
+@pytest.mark.parametrize("simplify", [True, False])
+@pytest.mark.parametrize("order", [I.PREFIX, I.POSTFIX])
+def test_parallel_parse_equals_serial(simplify, order):
+    """A large population parsed in chunks of trees on the context's workers
+    gives the serial parse's DAG: the same nodes with the same ids (so the
+    same exported tokens and bytecode)."""
+    tok, g = I.batched_uneven()[:2]
+    tok = I.convert_order(tok, order)
+    with tgp.Context(host_only=True, plan_threads=1, simplify=simplify) as a, \
+            tgp.Context(host_only=True, simplify=simplify) as b:
+        pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+        sa, sb = a.stats(), b.stats()
+        assert sa["dag_nodes"] == sb["dag_nodes"] and sa["dag_internal"] == sb["dag_internal"]
+        ta, tb = a.population_tokens(pa), b.population_tokens(pb)
+        assert np.array_equal(ta.ops, tb.ops) and np.array_equal(ta.imm.view(np.int32), tb.imm.view(np.int32))
+        ia, oa = a.debug_plan(pa, g.N)
+        ib, ob = b.debug_plan(pb, g.N)
+        assert np.array_equal(ia, ib) and np.array_equal(oa, ob)
+    # a malformed tree deep in the stream gives the serial parse's message
+    bad = I.Tokens(tok.ops.copy(), tok.imm, tok.tree_off, tok.order)
+    t = 3000
+    bad.ops[bad.tree_off[t]:bad.tree_off[t + 1]][0] = 99
+    with tgp.Context(host_only=True, plan_threads=1) as a, tgp.Context(host_only=True) as b:
+        msgs = []
+        for c in (a, b):
+            with pytest.raises(tgp.TgpError) as e:
+                c.compile_tokens(bad)
+            msgs.append(str(e.value))
+        assert msgs[0] == msgs[1] and "tree 3000" in msgs[0]
+
+
 def test_column_flag_is_accepted_and_debug_plans_have_no_column_loads():
     tok = I.to_tokens([I.parse_string("add(sin(x), mult(y, cos(x)))")])
     for cols in (True, False):

@@ -1007,6 +1007,43 @@ constexpr size_t kColMaxEntries = 16384;
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
                             const ParallelFor* par, bool columns, bool table_plan);
 
+// Encodes groups [0, n) of `ir` (group g at [off[g], off[g + 1])) onto
+// `code`, appending each group's end offset (code.size() after it) to
+// `code_off`.  A store followed by the start of a new subexpression is one
+// word.  Returns whether the interpreter variant with the rest of Table 1 is
+// needed.
+static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int n, std::vector<Ins>& code,
+                          std::vector<int64_t>& code_off) {
+    bool ext = false;
+    for (int g = 0; g < n; ++g) {
+        for (int64_t i = off[g]; i < off[g + 1]; ++i) {
+            const IrIns& in = ir[i];
+            const bool form_fn = in.form == F_AO || in.form == F_OA || in.form == F_TT || in.form == F_UA ||
+                                 in.form == F_UT;
+            if (in.form == F_SEL || (form_fn && in.fn >= T_TAN)) ext = true;
+            if (in.form == F_ST && i + 1 < off[g + 1] && in.aux >= 0 && in.aux < (1 << 15)) {
+                const IrIns& nx = ir[i + 1];
+                int fused = -1;
+                if (nx.form == F_TT && bin_index(nx.fn) >= 0 && bin_index(nx.fn) < kNHotBin)
+                    fused = OPC_STT + bin_index(nx.fn) * 9 + nx.o1 * 3 + nx.o2;
+                else if (nx.form == F_UT && un_index(nx.fn) >= 0 && un_index(nx.fn) < kNHotUn)
+                    fused = OPC_SUT + un_index(nx.fn) * 3 + nx.o1;
+                if (fused >= 0) {
+                    if (nx.form == F_SEL || nx.fn >= T_TAN) ext = true;
+                    Ins e = encode(nx);
+                    e.x = (uint32_t)fused | (e.x & kUniformBit) | ((uint32_t)in.aux << kStoreSlotShift);
+                    code.push_back(e);
+                    ++i;
+                    continue;
+                }
+            }
+            code.push_back(encode(in));
+        }
+        code_off.push_back((int64_t)code.size());
+    }
+    return ext;
+}
+
 void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
                 const ParallelFor* par, bool columns) {
     build_plan_impl(PlanPop{pop.dag, pop.roots, pop.tree_cost, pop.tree_nodes}, shape, plan, cv, par, columns,
@@ -1031,37 +1068,55 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     std::vector<int32_t> order(T);
     std::iota(order.begin(), order.end(), 0);
     if (!table_plan) {
-    std::vector<int32_t> tree_uses(pop.dag.size(), 0), seen(pop.dag.size(), -1);
-    std::vector<int32_t> stack, tree_nodes, tree_at(T + 1, 0);
-    tree_nodes.reserve((size_t)std::min<int64_t>(pop.tree_nodes, (int64_t)1 << 26));
-    for (int64_t t = 0; t < T; ++t) {
-        tree_at[t] = (int32_t)tree_nodes.size();
-        stack.assign(1, pop.roots[t]);
-        while (!stack.empty()) {
-            int32_t n = stack.back();
-            stack.pop_back();
-            if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
-            seen[n] = (int32_t)t;
-            tree_uses[n]++;
-            tree_nodes.push_back(n);
-            for (int c = 0; c < kMaxKids; ++c)
-                if (pop.dag.nodes[n].kid[c] >= 0) stack.push_back(pop.dag.nodes[n].kid[c]);
-        }
-    }
-    tree_at[T] = (int32_t)tree_nodes.size();
-    std::vector<int32_t> key(T, -1);
-    std::vector<float> key_cost(T, 0.f);
-    for (int64_t t = 0; t < T; ++t) {
-        for (int32_t i = tree_at[t]; i < tree_at[t + 1]; ++i) {
-            const int32_t n = tree_nodes[i];
-            const float c = pop.dag.nodes[n].cost;
-            if (tree_uses[n] >= 2 && c > key_cost[t]) { key_cost[t] = c; key[t] = n; }
-        }
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        if (key[a] != key[b]) return key[a] > key[b];
-        return a < b;
-    });
+        // distinct internal nodes of each tree (contiguous chunks of trees
+        // on the workers), then the number of trees using each node
+        const bool many = par && *par && T >= 512;
+        const int C = many ? (int)std::min<int64_t>(16, T / 256) : 1;
+        std::vector<int32_t> tree_uses(pop.dag.size(), 0);
+        std::vector<std::vector<int32_t>> nodes_of(C), at_of(C);
+        auto walk = [&](int c) {
+            const int64_t t0 = T * c / C, t1 = T * (c + 1) / C;
+            std::vector<int32_t> seen(pop.dag.size(), -1), stack;
+            std::vector<int32_t>& tree_nodes = nodes_of[c];
+            std::vector<int32_t>& tree_at = at_of[c];
+            for (int64_t t = t0; t < t1; ++t) {
+                tree_at.push_back((int32_t)tree_nodes.size());
+                stack.assign(1, pop.roots[t]);
+                while (!stack.empty()) {
+                    int32_t n = stack.back();
+                    stack.pop_back();
+                    if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
+                    seen[n] = (int32_t)t;
+                    tree_nodes.push_back(n);
+                    for (int k = 0; k < kMaxKids; ++k)
+                        if (pop.dag.nodes[n].kid[k] >= 0) stack.push_back(pop.dag.nodes[n].kid[k]);
+                }
+            }
+            tree_at.push_back((int32_t)tree_nodes.size());
+        };
+        // the costliest node of each tree that another tree also uses
+        std::vector<int32_t> key(T, -1);
+        auto keys = [&](int c) {
+            const int64_t t0 = T * c / C, t1 = T * (c + 1) / C;
+            for (int64_t t = t0; t < t1; ++t) {
+                float key_cost = 0.f;
+                for (int32_t i = at_of[c][t - t0]; i < at_of[c][t - t0 + 1]; ++i) {
+                    const int32_t n = nodes_of[c][i];
+                    const float cost = pop.dag.nodes[n].cost;
+                    if (tree_uses[n] >= 2 && cost > key_cost) { key_cost = cost; key[t] = n; }
+                }
+            }
+        };
+        if (C > 1) (*par)(C, walk);
+        else walk(0);
+        for (const auto& v : nodes_of)
+            for (int32_t n : v) tree_uses[n]++;
+        if (C > 1) (*par)(C, keys);
+        else keys(0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            if (key[a] != key[b]) return key[a] > key[b];
+            return a < b;
+        });
     }
     double total = 0;
     for (int64_t t = 0; t < T; ++t) total += pop.tree_cost[t] + 1.0;
@@ -1186,9 +1241,13 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         // each, and the tables' plans as tasks of their own
         const int P = std::min(G, 16);
         const int NT = (int)table_builds.size();
+        // each run is planned and encoded on its own; the runs are then
+        // placed back to back (offsets shifted)
         std::vector<std::vector<IrIns>> part(P);
-        std::vector<std::vector<int64_t>> ends(P);
+        std::vector<std::vector<int64_t>> ends(P), cends(P);
+        std::vector<std::vector<Ins>> pcode(P);
         std::vector<int> slots(P, 0);
+        std::vector<uint8_t> pext(P, 0);
         (*par)(P + NT, [&](int t) {
             if (t < NT) {
                 table_builds[t]();
@@ -1197,19 +1256,30 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             t -= NT;
             const int g0 = (int)((int64_t)G * t / P), g1 = (int)((int64_t)G * (t + 1) / P);
             GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, &xfree, colp, rowp);
+            ends[t].push_back(0);
             for (int g = g0; g < g1; ++g) {
                 slots[t] = std::max(slots[t], plan_group(gen, part[t], pop, groups[g], budget));
                 ends[t].push_back((int64_t)part[t].size());
             }
+            pcode[t].reserve(part[t].size());
+            pext[t] = encode_groups(part[t], ends[t].data(), g1 - g0, pcode[t], cends[t]);
         });
-        size_t total_ins = 0;
-        for (const auto& v : part) total_ins += v.size();
-        plan.ir.reserve(total_ins);
+        size_t total_ins = 0, total_code = 1;
         for (int t = 0; t < P; ++t) {
-            const int64_t base = (int64_t)plan.ir.size();
+            total_ins += part[t].size();
+            total_code += pcode[t].size();
+        }
+        plan.ir.reserve(total_ins);
+        plan.code.reserve(total_code);
+        plan.code_off.assign(1, 0);
+        for (int t = 0; t < P; ++t) {
+            const int64_t base = (int64_t)plan.ir.size(), cbase = (int64_t)plan.code.size();
             plan.ir.insert(plan.ir.end(), part[t].begin(), part[t].end());
+            plan.code.insert(plan.code.end(), pcode[t].begin(), pcode[t].end());
             plan.n_slots = std::max(plan.n_slots, slots[t]);
-            for (int64_t e : ends[t]) plan.group_off.push_back(base + e);
+            plan.ext = plan.ext || pext[t];
+            for (size_t i = 1; i < ends[t].size(); ++i) plan.group_off.push_back(base + ends[t][i]);
+            for (int64_t e : cends[t]) plan.code_off.push_back(cbase + e);
         }
     } else {
         for (auto& b : table_builds) b();
@@ -1218,42 +1288,15 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
             plan.group_off.push_back((int64_t)plan.ir.size());
         }
+        plan.code.reserve(plan.ir.size() + 1);
+        plan.code_off.assign(1, 0);
+        plan.ext = encode_groups(plan.ir, plan.group_off.data(), G, plan.code, plan.code_off);
     }
     plan.group_order.resize(G);
     std::iota(plan.group_order.begin(), plan.group_order.end(), 0);
     std::stable_sort(plan.group_order.begin(), plan.group_order.end(),
                      [&](int32_t a, int32_t b) { return plan.group_cost[a] > plan.group_cost[b]; });
     plan.n_items = (int64_t)G * plan.n_tiles;
-    plan.code.reserve(plan.ir.size() + 1);
-    for (const IrIns& in : plan.ir) {
-        // the interpreter variant with the rest of Table 1 is needed
-        const bool form_fn = in.form == F_AO || in.form == F_OA || in.form == F_TT || in.form == F_UA || in.form == F_UT;
-        if (in.form == F_SEL || (form_fn && in.fn >= T_TAN)) plan.ext = true;
-    }
-    // a store followed by the start of a new subexpression is one word
-    plan.code_off.assign(1, 0);
-    for (int g = 0; g < G; ++g) {
-        for (int64_t i = plan.group_off[g]; i < plan.group_off[g + 1]; ++i) {
-            const IrIns& in = plan.ir[i];
-            if (in.form == F_ST && i + 1 < plan.group_off[g + 1] && in.aux >= 0 && in.aux < (1 << 15)) {
-                const IrIns& nx = plan.ir[i + 1];
-                int fused = -1;
-                if (nx.form == F_TT && bin_index(nx.fn) >= 0 && bin_index(nx.fn) < kNHotBin)
-                    fused = OPC_STT + bin_index(nx.fn) * 9 + nx.o1 * 3 + nx.o2;
-                else if (nx.form == F_UT && un_index(nx.fn) >= 0 && un_index(nx.fn) < kNHotUn)
-                    fused = OPC_SUT + un_index(nx.fn) * 3 + nx.o1;
-                if (fused >= 0) {
-                    Ins e = encode(nx);
-                    e.x = (uint32_t)fused | (e.x & kUniformBit) | ((uint32_t)in.aux << kStoreSlotShift);
-                    plan.code.push_back(e);
-                    ++i;
-                    continue;
-                }
-            }
-            plan.code.push_back(encode(in));
-        }
-        plan.code_off.push_back((int64_t)plan.code.size());
-    }
     plan.code.push_back(encode(IrIns{F_END, 0, 0, 0, 0, 0}));
 }
 

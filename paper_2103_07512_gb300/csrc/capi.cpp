@@ -833,9 +833,7 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.trig_rad = trig_radians(c) ? 1 : 0;
     p.out_stride = p.N;
     p.coltab = hp.col_plan ? pl->ctab.p : nullptr;
-    p.col_stride = hp.col_stride;
     p.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
-    p.row_stride = hp.row_stride;
     if (d->ready && !fence_done(d->ready)) CUDA_TRY(cudaStreamWaitEvent(s, d->ready->ev, 0));
     CUDA_TRY(cudaMemsetAsync(pl->counter.p, 0, 3 * kQueueWords * sizeof(int32_t), s));
     const bool timed = (c->cfg.flags & TGP_F_TIME_KERNELS) != 0 && !c->capturing;
@@ -1143,9 +1141,7 @@ int fitness_fused(tgp_ctx* ctx, const std::vector<FusedSegment>& segs, void* str
         sp.pagie_x = d->pagie_x.p;
         sp.partial = pl->partial.p;
         sp.coltab = hp.col_plan ? pl->ctab.p : nullptr;
-        sp.col_stride = hp.col_stride;
         sp.rowtab = hp.row_plan ? pl->rtab.p : nullptr;
-        sp.row_stride = hp.row_stride;
         hs.push_back(sp);
         plans.push_back(pl);
         doms.push_back(d);

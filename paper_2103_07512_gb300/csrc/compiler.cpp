@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <numeric>
 
@@ -1009,12 +1010,19 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
 
 // Encodes groups [0, n) of `ir` (group g at [off[g], off[g + 1])) onto
 // `code`, appending each group's end offset (code.size() after it) to
-// `code_off`.  A store followed by the start of a new subexpression is one
-// word.  Returns whether the interpreter variant with the rest of Table 1 is
-// needed.
-static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int n, std::vector<Ins>& code,
-                          std::vector<int64_t>& code_off) {
+// `code_off`.  A store followed by the start of a new subexpression, or by a
+// table load, is one word.  A table load's word holds the offset of its entry
+// (entry * the table's stride).  Returns whether the interpreter variant with
+// the rest of Table 1 is needed.
+static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int n, int64_t col_stride,
+                          int64_t row_stride, std::vector<Ins>& code, std::vector<int64_t>& code_off) {
     bool ext = false;
+    auto enc = [&](const IrIns& in) {
+        Ins e = encode(in);
+        if (in.form == F_COL) e.y = (uint32_t)((int64_t)in.aux * col_stride);
+        if (in.form == F_ROW) e.y = (uint32_t)((int64_t)in.aux * row_stride);
+        return e;
+    };
     for (int g = 0; g < n; ++g) {
         for (int64_t i = off[g]; i < off[g + 1]; ++i) {
             const IrIns& in = ir[i];
@@ -1028,16 +1036,19 @@ static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int 
                     fused = OPC_STT + bin_index(nx.fn) * 9 + nx.o1 * 3 + nx.o2;
                 else if (nx.form == F_UT && un_index(nx.fn) >= 0 && un_index(nx.fn) < kNHotUn)
                     fused = OPC_SUT + un_index(nx.fn) * 3 + nx.o1;
+                else if (nx.form == F_COL)
+                    fused = OPC_STC;
+                else if (nx.form == F_ROW)
+                    fused = OPC_STR;
                 if (fused >= 0) {
-                    if (nx.form == F_SEL || nx.fn >= T_TAN) ext = true;
-                    Ins e = encode(nx);
+                    Ins e = enc(nx);
                     e.x = (uint32_t)fused | (e.x & kUniformBit) | ((uint32_t)in.aux << kStoreSlotShift);
                     code.push_back(e);
                     ++i;
                     continue;
                 }
             }
-            code.push_back(encode(in));
+            code.push_back(enc(in));
         }
         code_off.push_back((int64_t)code.size());
     }
@@ -1197,13 +1208,15 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                                int64_t n_points, int64_t row_len) {
             for (size_t n = 0; n < nn; ++n)
                 if (need[n]) roots.push_back((int32_t)n);
-            if (roots.empty() || roots.size() > kColMaxEntries) {
+            const int64_t st = (n_points + 15) / 16 * 16;
+            // (an entry's offset, entry * stride, is a 32-bit bytecode word)
+            if (roots.empty() || roots.size() > kColMaxEntries || (int64_t)roots.size() * st > (int64_t)UINT32_MAX) {
                 roots.clear();
                 return;
             }
             view.assign(nn, -1);
             for (size_t e = 0; e < roots.size(); ++e) view[roots[e]] = (int32_t)e;
-            stride = (n_points + 15) / 16 * 16;
+            stride = st;
             std::vector<float> costs;
             for (int32_t r : roots) costs.push_back(pop.dag.nodes[r].cost);
             PlanShape ts;
@@ -1262,7 +1275,8 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                 ends[t].push_back((int64_t)part[t].size());
             }
             pcode[t].reserve(part[t].size());
-            pext[t] = encode_groups(part[t], ends[t].data(), g1 - g0, pcode[t], cends[t]);
+            pext[t] = encode_groups(part[t], ends[t].data(), g1 - g0, plan.col_stride, plan.row_stride, pcode[t],
+                                    cends[t]);
         });
         size_t total_ins = 0, total_code = 1;
         for (int t = 0; t < P; ++t) {
@@ -1290,7 +1304,8 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         }
         plan.code.reserve(plan.ir.size() + 1);
         plan.code_off.assign(1, 0);
-        plan.ext = encode_groups(plan.ir, plan.group_off.data(), G, plan.code, plan.code_off);
+        plan.ext = encode_groups(plan.ir, plan.group_off.data(), G, plan.col_stride, plan.row_stride, plan.code,
+                                 plan.code_off);
     }
     plan.group_order.resize(G);
     std::iota(plan.group_order.begin(), plan.group_order.end(), 0);

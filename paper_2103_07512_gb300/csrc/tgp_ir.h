@@ -99,7 +99,9 @@ constexpr int OPC_FUSED_END = OPC_SUT + kNHotUn * 3;
 // valid target (codes without a form leave the loop).
 constexpr int kDispatchMask = 255;
 constexpr int kStoreSlotShift = 16;
-constexpr int OPC_COL = OPC_FUSED_END;   // F_COL, left to the C++ caller
+// F_COL: A = the thread's K values of a column table entry; y = the entry's
+// first float in the table (entry index * the table's stride).
+constexpr int OPC_COL = OPC_FUSED_END;
 static_assert(OPC_COL < kDispatchMask + 1, "opcodes must fit the dispatch byte");
 // Codes with which the dispatch loop leaves for sin / cos of a value that all
 // of a thread's points share (y, an immediate), held in A[0]; never in bytecode.
@@ -111,8 +113,13 @@ constexpr int kExitCosUniform = 251;
 // evaluated once for the K points.
 constexpr uint32_t kUniformBit = 0x100;
 static_assert(OPC_COL < kExitSinUniform, "exit codes must not be opcodes");
-constexpr int OPC_ROW = 252;                // F_ROW, left to the C++ caller
+// F_ROW: A = the row table entry's value at the thread's row; y as F_COL.
+constexpr int OPC_ROW = 252;
 static_assert(OPC_ROW > kExitCosUniform && OPC_ROW <= kDispatchMask, "F_ROW code");
+// Fused "store, then load a table entry": slot x >> 16 = A, then F_COL / F_ROW.
+constexpr int OPC_STC = 253;
+constexpr int OPC_STR = 254;
+static_assert(OPC_STR <= kDispatchMask, "fused table codes");
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
 // high half), y = immediate bits, slot, or aux.
@@ -185,10 +192,8 @@ struct SegParams {
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
     const float* pagie_x;       // Pagie: x^4/(1+x^4) per column (see EvalParams)
     float* partial;             // [its trees][n_tiles][warps]
-    const float* coltab;
-    int64_t col_stride;
+    const float* coltab;        // its column and row tables (see EvalParams)
     const float* rowtab;
-    int64_t row_stride;
 };
 
 // Parameters of one interpreter launch.
@@ -214,13 +219,11 @@ struct EvalParams {
     int32_t n_slots;            // shared-memory value slots per thread
     int32_t max_items_per_cta;  // bound on the work-queue loop
     int32_t trig_rad;           // sin/cos/tan in radians (interpreter variant with the rest of Table 1 only)
-    const float* coltab;        // column tables (F_COL): entry e at coltab + e * col_stride, or nullptr
-    int64_t col_stride;         // floats per column-table entry
-    const float* rowtab;        // row tables (F_ROW): entry e at rowtab + e * row_stride, or nullptr
-    int64_t row_stride;         // floats per row-table entry
+    const float* coltab;        // column tables (F_COL words hold the offset of their entry), or nullptr
+    const float* rowtab;        // row tables (F_ROW words likewise), or nullptr
     int64_t out_stride;         // floats between the phenotype rows of two trees (N, or a table's stride)
     const SegParams* segs;      // a launch fusing several domains: [n_segs] segments, or nullptr
-    int32_t n_segs;             // (the fields above from code to row_stride are then unused)
+    int32_t n_segs;             // (the fields above from code to rowtab are then unused)
 };
 
 struct FinalizeParams {

@@ -459,6 +459,88 @@ def bench_population_at_scale(ctx_cls, dev, flush, costs, peak_add, peak_fma, st
     return out
 
 
+def run_sharded(args):
+    """The 1024x1024 population's fitness with the grid's rows split over the
+    ranks (strong scaling: the same job on N GPUs).  Each rank evaluates its
+    band (tgp_fitness_sse_dev); the [T] sums are all-gathered and added in
+    rank order (shard.reduce_band_sse).  A step is one band launch plus the
+    exchange; value = the whole grid's node-evals / the slowest rank's step."""
+    import torch
+    import paper_2103_07512_gb300 as tgp
+    from paper_2103_07512_gb300 import shard
+
+    rank, local, world = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tok, g = I.population_at_scale(seed=1)
+    T = tok.n_trees
+    row0, n_rows = shard.band_rows(g.H, rank, world)
+    ctx = tgp.Context(device=local)
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi, rows=(row0, n_rows))
+    pop = ctx.compile_tokens(tok)
+    sse = torch.empty(T, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    group = None
+
+    def step():
+        ctx.fitness_sse_dev(pop, dom, sse, stream=stream)
+        return shard.reduce_band_sse(sse, g.N, group=group)
+
+    for _ in range(max(args.warmup, 3)):
+        rmse = step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    t_heat = time.perf_counter()
+    while time.perf_counter() - t_heat < 1.5:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))                               # evict L2 between steps (untimed)
+        evs[i][0].record(stream)
+        rmse = step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    local_s = float(np.mean([a.elapsed_time(b) for a, b in evs])) * 1e-3
+    t = torch.tensor([local_s], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_s = float(t.item())
+    units = int(tok.ops.size) * g.N
+    # one rank alone holds every row: its result is tgp_fitness_dev's, bitwise
+    same = None
+    if world == 1:
+        ref = torch.empty(T, dtype=torch.float64, device=dev)
+        ctx.fitness_dev(pop, dom, ref, stream=stream)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(ref.view(torch.int64), rmse.view(torch.int64)))
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": units / step_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_C2 + ", rows sharded over the ranks", "trees": T, "points": g.N,
+                       "rows_per_rank": [shard.band_rows(g.H, r, world)[1] for r in range(world)],
+                       "exchange": "all_gather of [T] binary64 sums, added in rank order",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "clocks": clk, "single_rank_equals_fitness_dev_bitwise": same}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def bench_phenotype(ctx, pop, dom, tok, g, dev, flush, steps=20):
     """Tensor phenotypes of the headline population (Sec. 3.1): every tree's
     value at every point written to HBM ([T, H*W] binary32, float4 stores)."""
@@ -663,11 +745,15 @@ def main():
                     help="grid points per step of the reference arm (a bounded sample, all trees)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other configurations (1024x1024 population, evolution, serving)")
+    ap.add_argument("--sharded", action="store_true",
+                    help="the 1024x1024 population with its rows split over the ranks (strong scaling)")
     ap.add_argument("--only", choices=["population_at_scale"],
                     help="measure one other configuration alone and print its line (for profiling it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sharded:
+        return run_sharded(args)
     if args.only:
         import torch
         import paper_2103_07512_gb300 as tgp

@@ -226,6 +226,21 @@ const char* tgp_last_error(const tgp_ctx* ctx);
 int tgp_load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
                     int32_t target_kind, const void* target, tgp_handle* domain_out);
 
+/*
+ * Loads rows row0 .. row0 + n_rows - 1 of the W x H grid of tgp_load_domain
+ * as a domain of W x n_rows points: the points, their flat order within the
+ * band and their binary32 coordinates are exactly those of the full grid's
+ * rows (y = ylo + row*((yhi-ylo)/(H-1)) with the full grid's row index and H).
+ * For fitness sharded by rows over several GPUs (the fitness cases of
+ * Sec. 3.1 split into contiguous bands, one per process; see
+ * tgp_fitness_sse_dev).  A TGP_TARGET_TENSOR target holds the band's
+ * n_rows*W values; a token target is evaluated on the band's points.
+ * Errors: TGP_E_INVALID unless 0 <= row0, n_rows >= 1, row0 + n_rows <= H.
+ */
+int tgp_load_domain_rows(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                         int32_t row0, int32_t n_rows, int32_t target_kind, const void* target,
+                         tgp_handle* domain_out);
+
 /* Releases a domain and the device memory it holds. */
 int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain);
 
@@ -275,6 +290,17 @@ int tgp_fitness(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream,
 /* As tgp_fitness, but writes the n_trees doubles to device memory rmse_dev
  * and never synchronises (suitable for CUDA graph capture). */
 int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev);
+
+/*
+ * The sums under the square root of tgp_fitness_dev: writes
+ * sse_dev[t] = sum over the domain's points of (f_t(p) - target(p))^2, formed
+ * and added exactly as for the RMSE (same partials, same fixed binary64
+ * order), +inf when not finite.  sse_dev: device array of n_trees doubles.
+ * Asynchronous on `stream`; never synchronises.  With a grid split by rows
+ * (tgp_load_domain_rows), each GPU computes its band's sums; the RMSE of
+ * Sec. 4.1 over the whole grid is sqrt((sum of the bands' values) / (W*H)).
+ */
+int tgp_fitness_sse_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* sse_dev);
 
 /*
  * tgp_fitness_noalloc -- the fitness of tgp_fitness_dev, computed without

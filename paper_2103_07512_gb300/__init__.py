@@ -30,7 +30,8 @@ EXPORTS = ["tgp_create", "tgp_destroy", "tgp_last_error", "tgp_load_domain", "tg
            "tgp_fitness_dev", "tgp_stats_get", "tgp_debug_plan", "tgp_debug_layout",
            "tgp_calibrate_op_costs", "tgp_calibrate_peak", "tgp_plan_work", "tgp_fitness_noalloc", "tgp_fitness_graph", "tgp_autotune",
            "tgp_server_create", "tgp_server_destroy", "tgp_server_submit", "tgp_server_wait",
-           "tgp_server_stats_get", "tgp_evolve", "tgp_population_tokens"]
+           "tgp_server_stats_get", "tgp_evolve", "tgp_population_tokens", "tgp_load_domain_rows",
+           "tgp_fitness_sse_dev"]
 
 
 class TgpError(RuntimeError):
@@ -126,6 +127,8 @@ def lib():
             "tgp_create": [P, P],
             "tgp_destroy": [P],
             "tgp_load_domain": [P, i32, i32, f32, f32, f32, f32, i32, P, P],
+            "tgp_load_domain_rows": [P, i32, i32, f32, f32, f32, f32, i32, i32, i32, P, P],
+            "tgp_fitness_sse_dev": [P, i64, i64, P, P],
             "tgp_release_domain": [P, i64],
             "tgp_compile_population": [P, P, P, i64, P, i32, i32, P],
             "tgp_release_population": [P, i64],
@@ -231,11 +234,25 @@ class Context:
     # ---------------------------------------------------------------- ABI
 
     def load_domain(self, W, H, xlo=-5.0, xhi=5.0, ylo=-5.0, yhi=5.0, target=None,
-                    target_tokens=None):
+                    target_tokens=None, rows=None):
         """tgp_load_domain: Pagie target by default; `target` = float32 [H*W]
-        array (numpy or torch, host or device); `target_tokens` = (ops, imm, order)."""
+        array (numpy or torch, host or device); `target_tokens` = (ops, imm, order).
+        rows = (row0, n_rows): tgp_load_domain_rows, the band of rows row0 ..
+        row0 + n_rows - 1 of the W x H grid (`target` then holds the band's
+        n_rows*W values)."""
         out = ctypes.c_int64()
         keep = None
+        if rows is not None:
+            row0, n_rows = int(rows[0]), int(rows[1])
+
+            def load(kind, tgt):
+                return self._L.tgp_load_domain_rows(self._h, W, H, xlo, xhi, ylo, yhi, row0, n_rows, kind, tgt,
+                                                    ctypes.byref(out))
+        else:
+            n_rows = H
+
+            def load(kind, tgt):
+                return self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, kind, tgt, ctypes.byref(out))
         if target_tokens is not None:
             ops, imm, order = target_tokens
             ops = np.ascontiguousarray(ops, np.int32)
@@ -243,19 +260,16 @@ class Context:
             tt = TargetTokens(ops.ctypes.data, imm.ctypes.data if imm.size else None,
                               ops.size, imm.size, order)
             keep = (ops, imm, tt)
-            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_TOKENS,
-                                         ctypes.byref(tt), ctypes.byref(out))
+            rc = load(TARGET_TOKENS, ctypes.byref(tt))
         elif target is not None:
             if isinstance(target, np.ndarray):
                 target = np.ascontiguousarray(target, np.float32)
-                if target.size != W * H:
-                    raise ValueError("target must hold H*W values")
+                if target.size != W * n_rows:
+                    raise ValueError("target must hold one value per point of the domain")
             keep = target
-            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_TENSOR,
-                                         _ptr(target), ctypes.byref(out))
+            rc = load(TARGET_TENSOR, _ptr(target))
         else:
-            rc = self._L.tgp_load_domain(self._h, W, H, xlo, xhi, ylo, yhi, TARGET_PAGIE, None,
-                                         ctypes.byref(out))
+            rc = load(TARGET_PAGIE, None)
         del keep
         self._check(rc)
         return out.value
@@ -322,6 +336,11 @@ class Context:
     def fitness_dev(self, pop, dom, out, stream=None):
         """tgp_fitness_dev: RMSE into a device float64 buffer (torch tensor)."""
         self._check(self._L.tgp_fitness_dev(self._h, pop, dom, _stream(stream), _ptr(out)))
+
+    def fitness_sse_dev(self, pop, dom, out, stream=None):
+        """tgp_fitness_sse_dev: sums of squared residuals (binary64) into a
+        device float64 buffer (torch tensor)."""
+        self._check(self._L.tgp_fitness_sse_dev(self._h, pop, dom, _stream(stream), _ptr(out)))
 
     def fitness_graph(self, pop, dom, out, stream=None):
         """tgp_fitness_graph: RMSE into a device float64 buffer through a

@@ -93,6 +93,7 @@ struct Population;
 
 struct Domain {
     int32_t W = 0, H = 0;
+    int32_t row0 = 0, H_grid = 0;   // rows row0 .. row0 + H - 1 of an H_grid-row grid
     float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
     int32_t kind = TGP_TARGET_PAGIE;
     DevBuf<float> target;
@@ -753,6 +754,7 @@ int launch_tables(tgp_ctx* c, Plan* pl, const Domain* d, int32_t trig_rad, cudaS
         q.N = d->W;
         q.W = d->W;
         q.H = 1;
+        q.H_grid = 1;
         q.xlo = d->xlo;
         q.xhi = d->xhi;
         q.ylo = d->ylo;
@@ -782,6 +784,8 @@ int launch_tables(tgp_ctx* c, Plan* pl, const Domain* d, int32_t trig_rad, cudaS
         q.N = d->H;
         q.W = 1;
         q.H = d->H;
+        q.row0 = d->row0;
+        q.H_grid = d->H_grid;
         q.xlo = d->xlo;
         q.xhi = d->xlo;
         q.ylo = d->ylo;
@@ -816,6 +820,8 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     p.N = d->N();
     p.W = d->W;
     p.H = d->H;
+    p.row0 = d->row0;
+    p.H_grid = d->H_grid;
     p.xlo = d->xlo;
     p.xhi = d->xhi;
     p.ylo = d->ylo;
@@ -869,7 +875,8 @@ int launch_plan(tgp_ctx* c, Plan* pl, const Domain* d, bool pheno, float* out, c
     return TGP_OK;
 }
 
-int launch_fitness(tgp_ctx* c, Population* pop, Plan* pl, Domain* d, cudaStream_t s, double* rmse_dev) {
+int launch_fitness(tgp_ctx* c, Population* pop, Plan* pl, Domain* d, cudaStream_t s, double* rmse_dev,
+                   bool sse = false) {
     int rc = launch_plan(c, pl, d, false, nullptr, s);
     if (rc) return rc;
     FinalizeParams f{};
@@ -878,17 +885,19 @@ int launch_fitness(tgp_ctx* c, Population* pop, Plan* pl, Domain* d, cudaStream_
     f.n_trees = (int32_t)pop->ir.roots.size();
     f.n_points = (double)d->N();
     f.rmse = rmse_dev ? rmse_dev : pl->rmse.p;
+    f.sse = sse ? 1 : 0;
     CUDA_TRY(launch_finalize(f, s));
     c->stats.launches++;
     return TGP_OK;
 }
 
-int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out) {
+int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, double* rmse_dev, Plan** plan_out,
+                      bool sse = false) {
     Plan* pl = nullptr;
     CallCache cc;
     int rc = get_call_plan(c, pop, d, false, s, &pl, cc);
     if (rc) return rc;
-    rc = launch_fitness(c, pop, pl, d, s, rmse_dev);
+    rc = launch_fitness(c, pop, pl, d, s, rmse_dev, sse);
     if (rc) return rc;
     rc = finish_call(pl, cc, s);
     if (rc) return rc;
@@ -940,6 +949,7 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
     if (rc) return rc;
     v->ir = &p->ir;
     v->W = d->W; v->H = d->H;
+    v->row0 = d->row0; v->H_grid = d->H_grid;
     v->xlo = d->xlo; v->xhi = d->xhi; v->ylo = d->ylo; v->yhi = d->yhi;
     v->target = d->kind == TGP_TARGET_PAGIE ? nullptr : d->target.p;
     v->pagie_x = d->pagie_x.p;
@@ -952,10 +962,14 @@ int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::
 }
 
 int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi, int32_t target_kind,
-                const void* target, void* stream, bool sync, tgp_handle* domain_out) {
+                const void* target, void* stream, bool sync, tgp_handle* domain_out, int32_t row0, int32_t n_rows) {
     if (!ctx || !domain_out) return fail(TGP_E_INVALID, "ctx / domain_out is NULL");
     if (W < 1 || H < 1 || (int64_t)W * H > INT32_MAX)
         return fail(TGP_E_INVALID, "grid %d x %d: need W, H >= 1 and W*H <= 2^31-1", W, H);
+    if (n_rows < 0) n_rows = H;
+    if (row0 < 0 || n_rows < 1 || (int64_t)row0 + n_rows > H)
+        return fail(TGP_E_INVALID, "rows %d .. %d of a %d-row grid: need 0 <= row0 and 1 <= n_rows <= H - row0", row0,
+                    row0 + n_rows - 1, H);
     if (!std::isfinite(xlo) || !std::isfinite(xhi) || !std::isfinite(ylo) || !std::isfinite(yhi))
         return fail(TGP_E_INVALID, "domain bounds must be finite");
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -965,7 +979,9 @@ int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     auto d = std::make_unique<Domain>();
-    d->W = W; d->H = H; d->xlo = xlo; d->xhi = xhi; d->ylo = ylo; d->yhi = yhi;
+    // the domain holds the band's rows: H of the domain is the band's height
+    d->W = W; d->H = n_rows; d->row0 = row0; d->H_grid = H;
+    d->xlo = xlo; d->xhi = xhi; d->ylo = ylo; d->yhi = yhi;
     d->kind = target_kind;
     const int64_t N = d->N();
     if (target_kind == TGP_TARGET_PAGIE) {
@@ -1133,6 +1149,8 @@ int fitness_fused(tgp_ctx* ctx, const std::vector<FusedSegment>& segs, void* str
         sp.n_tiles = hp.n_tiles;
         sp.W = d->W;
         sp.H = d->H;
+        sp.row0 = d->row0;
+        sp.H_grid = d->H_grid;
         sp.xlo = d->xlo;
         sp.xhi = d->xhi;
         sp.ylo = d->ylo;
@@ -1276,6 +1294,14 @@ int tgp_load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, fl
     return internal::load_domain(ctx, W, H, xlo, xhi, ylo, yhi, target_kind, target, nullptr, true, domain_out);
 }
 
+int tgp_load_domain_rows(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi,
+                         int32_t row0, int32_t n_rows, int32_t target_kind, const void* target,
+                         tgp_handle* domain_out) {
+    if (n_rows < 1) return fail(TGP_E_INVALID, "n_rows must be >= 1 (got %d)", n_rows);
+    return internal::load_domain(ctx, W, H, xlo, xhi, ylo, yhi, target_kind, target, nullptr, true, domain_out, row0,
+                                 n_rows);
+}
+
 int tgp_release_domain(tgp_ctx* ctx, tgp_handle domain) {
     if (!ctx) return fail(TGP_E_INVALID, "ctx is NULL");
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -1398,6 +1424,18 @@ int tgp_fitness_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* strea
     int rc = set_device(ctx);
     if (rc) return rc;
     return fitness_to_device(ctx, p, d, (cudaStream_t)stream, rmse_dev, nullptr);
+}
+
+int tgp_fitness_sse_dev(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* sse_dev) {
+    if (!ctx || !sse_dev) return fail(TGP_E_INVALID, "ctx / sse_dev is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Population* p = find(ctx->pops, pop);
+    Domain* d = find(ctx->domains, domain);
+    if (!p || !d) return fail(TGP_E_INVALID, "unknown population or domain handle");
+    if (p->ir.roots.empty()) return TGP_OK;
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    return fitness_to_device(ctx, p, d, (cudaStream_t)stream, sse_dev, nullptr, true);
 }
 
 int tgp_fitness_graph(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, void* stream, double* rmse_dev) {

@@ -15,6 +15,7 @@ namespace internal {
 struct View {
     const PopIR* ir = nullptr;
     int32_t W = 0, H = 0;
+    int32_t row0 = 0, H_grid = 0;    // a band of rows of a larger grid (tgp_load_domain_rows)
     float xlo = 0, xhi = 0, ylo = 0, yhi = 0;
     const float* target = nullptr;   // device target tensor, nullptr for Pagie
     const float* pagie_x = nullptr;  // Pagie: the x part per column (nullptr: formed inline)
@@ -28,11 +29,13 @@ struct View {
 // Locks the context into `lk`, makes its device current and fills `v`.
 int view(tgp_ctx* ctx, tgp_handle pop, tgp_handle domain, std::unique_lock<std::mutex>& lk, View* v);
 
-// tgp_load_domain on `stream`.  sync: returns after a target tree has been
-// evaluated (as tgp_load_domain does); otherwise the evaluation is left in
-// flight and every later use of the domain, on any stream, waits for it.
+// tgp_load_domain_rows on `stream` (n_rows < 0: all rows from row0).  sync:
+// returns after a target tree has been evaluated (as tgp_load_domain does);
+// otherwise the evaluation is left in flight and every later use of the
+// domain, on any stream, waits for it.
 int load_domain(tgp_ctx* ctx, int32_t W, int32_t H, float xlo, float xhi, float ylo, float yhi, int32_t target_kind,
-                const void* target, void* stream, bool sync, tgp_handle* domain_out);
+                const void* target, void* stream, bool sync, tgp_handle* domain_out, int32_t row0 = 0,
+                int32_t n_rows = -1);
 
 // A copy of a population's IR (its DAG and roots).
 int population_copy(tgp_ctx* ctx, tgp_handle pop, PopIR* out);

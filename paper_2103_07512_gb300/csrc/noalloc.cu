@@ -132,6 +132,8 @@ extern "C" int tgp_fitness_noalloc(tgp_ctx* ctx, tgp_handle pop, tgp_handle doma
     p.N = (int64_t)v.W * v.H;
     p.W = v.W;
     p.H = v.H;
+    p.row0 = v.row0;
+    p.H_grid = v.H_grid;
     p.xlo = v.xlo;
     p.xhi = v.xhi;
     p.ylo = v.ylo;

@@ -188,6 +188,7 @@ struct SegParams {
     int64_t item0;
     int32_t n_tiles;
     int32_t W, H;
+    int32_t row0, H_grid;       // a band of rows of a larger grid (see EvalParams)
     float xlo, xhi, ylo, yhi;
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
     const float* pagie_x;       // Pagie: x^4/(1+x^4) per column (see EvalParams)
@@ -205,7 +206,9 @@ struct EvalParams {
     int32_t n_tiles;
     int32_t warps_per_tile;
     int64_t N;                  // points
-    int32_t W, H;
+    int32_t W, H;               // the launch's points: H rows of W
+    int32_t row0, H_grid;       // its rows are rows row0 .. row0 + H - 1 of an H_grid-row grid on
+                                // [ylo, yhi] (y = ylo + (row0 + row) * ((yhi - ylo) / (H_grid - 1)))
     float xlo, xhi, ylo, yhi;
     const float* target;        // [N] or nullptr for the inline Pagie polynomial
     const float* pagie_x;       // Pagie: its x part x^4/(1+x^4) at every column, padded to a
@@ -232,6 +235,7 @@ struct FinalizeParams {
     int32_t n_trees;
     double n_points;            // N
     double* rmse;               // [n_trees]
+    int32_t sse;                // nonzero: write the sums of squared residuals, not the RMSE
 };
 
 }  // namespace tgp

@@ -1012,8 +1012,10 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
 // `code`, appending each group's end offset (code.size() after it) to
 // `code_off`.  A store followed by the start of a new subexpression, or by a
 // table load, is one word.  A table load's word holds the offset of its entry
-// (entry * the table's stride).  Returns whether the interpreter variant with
-// the rest of Table 1 is needed.
+// (entry * the table's stride).  Roots are numbered in batches of
+// kRootBatch, each batch closed by a flush word and its trees (see
+// OPC_FLUSH).  Returns whether the interpreter variant with the rest of
+// Table 1 is needed.
 static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int n, int64_t col_stride,
                           int64_t row_stride, std::vector<Ins>& code, std::vector<int64_t>& code_off) {
     bool ext = false;
@@ -1023,9 +1025,26 @@ static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int 
         if (in.form == F_ROW) e.y = (uint32_t)((int64_t)in.aux * row_stride);
         return e;
     };
+    int pending = 0;
+    uint32_t batch[kRootBatch];
+    auto flush = [&]() {
+        if (!pending) return;
+        code.push_back(Ins{(uint32_t)OPC_FLUSH, (uint32_t)pending});
+        for (int i = 0; i < pending; i += 2) code.push_back(Ins{batch[i], i + 1 < pending ? batch[i + 1] : 0u});
+        pending = 0;
+    };
     for (int g = 0; g < n; ++g) {
         for (int64_t i = off[g]; i < off[g + 1]; ++i) {
             const IrIns& in = ir[i];
+            if (in.form == F_ROOT) {
+                Ins e = enc(in);
+                e.x |= (uint32_t)pending << kStoreSlotShift;
+                code.push_back(e);
+                batch[pending++] = (uint32_t)in.aux;
+                if (pending == kRootBatch) flush();
+                continue;
+            }
+            if (in.form == F_END) flush();
             const bool form_fn = in.form == F_AO || in.form == F_OA || in.form == F_TT || in.form == F_UA ||
                                  in.form == F_UT;
             if (in.form == F_SEL || (form_fn && in.fn >= T_TAN)) ext = true;
@@ -1050,6 +1069,7 @@ static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int 
             }
             code.push_back(enc(in));
         }
+        flush();   // (a group always ends in END; kept for a group that would not)
         code_off.push_back((int64_t)code.size());
     }
     return ext;
@@ -1247,7 +1267,9 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     const std::vector<int32_t>* rowp = row.empty() ? nullptr : &row;
 
     const int slot_bytes = shape.K * shape.threads * 4;
-    const int budget = std::max(4, smem_budget_per_cta(shape.K) / slot_bytes - 1);
+    // (less the target values and the root-sum area: kRootBatch floats per thread)
+    const int budget =
+        std::max(4, (smem_budget_per_cta(shape.K) - kRootBatch * 4 * shape.threads) / slot_bytes - 1);
     plan.group_off.push_back(0);
     if (par && *par && G > 1 && !(cv && cv->active())) {
         // contiguous runs of groups, one planner (and its per-node arrays)

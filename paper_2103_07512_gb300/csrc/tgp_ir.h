@@ -120,6 +120,17 @@ static_assert(OPC_ROW > kExitCosUniform && OPC_ROW <= kDispatchMask, "F_ROW code
 constexpr int OPC_STC = 253;
 constexpr int OPC_STR = 254;
 static_assert(OPC_STR <= kDispatchMask, "fused table codes");
+// Tree roots of a fitness launch.  A root word (OPC_ROOT, y = the tree) also
+// carries in x >> kStoreSlotShift its place j (0 .. kRootBatch - 1) in the
+// group's current batch of roots: the thread's sum of squared residuals of
+// the tree at its K points goes to element j of its root-sum area in shared
+// memory.  After every kRootBatch roots of a group, and before its END when
+// some are pending, a flush word (OPC_FLUSH, y = n, the batch's roots) is
+// followed by ceil(n / 2) data words holding the batch's trees (x, y: two
+// trees each; never dispatched): the flush adds each root's sums over the
+// lanes of each warp and stores one partial per (tree, tile, warp).
+constexpr int OPC_FLUSH = 255;
+constexpr int kRootBatch = 4;
 
 // One encoded instruction: x = opcode (low byte; a fused store's slot in the
 // high half), y = immediate bits, slot, or aux.

@@ -293,31 +293,46 @@ int32_t make_node(Dag& dag, int op, const int32_t (&k)[kMaxKids], uint32_t bits,
 
 // Drops DAG nodes no tree reaches (operands that simplification bypassed),
 // keeping ids in topological order.
-void compact(PopIR& pop) {
-    const size_t n = pop.dag.size();
-    std::vector<uint8_t> live(n, 0);
-    for (int32_t r : pop.roots) live[r] = 1;
-    for (size_t i = n; i-- > 0;)   // parents have larger ids than their operands
+// Nodes reachable from `roots` in `dag`: live[i] = 1.
+static void mark_live(const Dag& dag, const int32_t* roots, size_t n_roots, std::vector<uint8_t>& live) {
+    live.assign(dag.size(), 0);
+    for (size_t t = 0; t < n_roots; ++t) live[roots[t]] = 1;
+    for (size_t i = dag.size(); i-- > 0;)   // parents have larger ids than their operands
         if (live[i])
             for (int c = 0; c < kMaxKids; ++c)
-                if (pop.dag.nodes[i].kid[c] >= 0) live[pop.dag.nodes[i].kid[c]] = 1;
-    const size_t n_live = (size_t)std::count(live.begin(), live.end(), (uint8_t)1);
-    if (n_live == n) return;
-    // the live nodes keep their keys (operands renumbered) and their derived
-    // fields, which depend on the operands' only
-    std::vector<DagNode> kept;
-    kept.reserve(n_live);
+                if (dag.nodes[i].kid[c] >= 0) live[dag.nodes[i].kid[c]] = 1;
+}
+
+// Keeps the nodes marked live, in their order (operands renumbered; the
+// derived fields depend on the operands' only), with `par` in ranges.
+static void compact_live(PopIR& pop, const std::vector<uint8_t>& live, const ParallelFor* par) {
+    const size_t n = pop.dag.size();
     std::vector<int32_t> id(n, -1);
-    for (size_t i = 0; i < n; ++i) {
-        if (!live[i]) continue;
-        DagNode x = pop.dag.nodes[i];
-        for (int c = 0; c < kMaxKids; ++c)
-            if (x.kid[c] >= 0) x.kid[c] = id[x.kid[c]];
-        id[i] = (int32_t)kept.size();
-        kept.push_back(x);
-    }
+    int32_t n_live = 0;
+    for (size_t i = 0; i < n; ++i)
+        if (live[i]) id[i] = n_live++;
+    if ((size_t)n_live == n) return;
+    std::vector<DagNode> kept((size_t)n_live);
+    auto fill = [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+            if (!live[i]) continue;
+            DagNode x = pop.dag.nodes[i];
+            for (int c = 0; c < kMaxKids; ++c)
+                if (x.kid[c] >= 0) x.kid[c] = id[x.kid[c]];
+            kept[id[i]] = x;
+        }
+    };
+    const int P = (par && *par && n >= (1u << 16)) ? 16 : 1;
+    if (P > 1) (*par)(P, [&](int t) { fill(n * t / P, n * (t + 1) / P); });
+    else fill(0, n);
     for (auto& r : pop.roots) r = id[r];
     pop.dag.assign_nodes(std::move(kept));
+}
+
+void compact(PopIR& pop) {
+    std::vector<uint8_t> live;
+    mark_live(pop.dag, pop.roots.data(), pop.roots.size(), live);
+    compact_live(pop, live, nullptr);
 }
 
 void append_population(PopIR& dst, const PopIR& src) {
@@ -479,12 +494,17 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
         std::vector<int> rcs(n_chunks, 0);
         std::vector<std::string> errs(n_chunks);
         std::vector<int64_t> toks(n_chunks, 0);
+        // with simplification, each chunk also marks the nodes its own trees
+        // reach: the population's live nodes are their images (see below)
+        std::vector<std::vector<uint8_t>> clive(n_chunks);
         (*par)(n_chunks, [&](int c) {
             const int64_t n = tree_off[t_at[c + 1]] - tree_off[t_at[c]];
             dags[c].reserve((size_t)std::max<int64_t>(n, 1));
             rcs[c] = parse_trees(ops, imm, n_imm, tree_off, t_at[c], t_at[c + 1], imm_at[c], order, simplify, dags[c],
                                  out.roots.data() + t_at[c], out.tree_size.data() + t_at[c],
                                  out.tree_cost.data() + t_at[c], &toks[c], errs[c]);
+            if (!rcs[c] && simplify)
+                mark_live(dags[c], out.roots.data() + t_at[c], (size_t)(t_at[c + 1] - t_at[c]), clive[c]);
         });
         for (int c = 0; c < n_chunks; ++c) {   // the first failing tree's message, as a serial parse gives
             if (rcs[c]) {
@@ -495,9 +515,10 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
         size_t nodes = 0;
         for (const Dag& d : dags) nodes += d.size();
         out.dag.reserve(nodes);
-        std::vector<int32_t> id;
+        std::vector<std::vector<int32_t>> ids(n_chunks);
         for (int c = 0; c < n_chunks; ++c) {
             const Dag& d = dags[c];
+            std::vector<int32_t>& id = ids[c];
             id.assign(d.size(), -1);
             for (size_t i = 0; i < d.size(); ++i) {
                 const DagNode& x = d.nodes[i];
@@ -510,6 +531,24 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
             for (int32_t t = t_at[c]; t < t_at[c + 1]; ++t) out.roots[t] = id[out.roots[t]];
             out.tree_nodes += toks[c];
         }
+        if (n_trees > 0 && total != out.tree_nodes) { err = "internal: token count"; return -1; }
+        if (imm_at[n_chunks] != n_imm) {
+            fmt(err, "stream has %lld CONST tokens but n_imm = %lld", imm_at[n_chunks], n_imm);
+            return -2;
+        }
+        if (simplify) {
+            // a node of the population is reached from a root exactly when it
+            // is the image of a node its chunk's trees reach (the population's
+            // node has the images of the chunk node's operands): the same live
+            // set, hence the same nodes and ids, as compact() after a serial parse
+            std::vector<uint8_t> live(out.dag.size(), 0);
+            (*par)(n_chunks, [&](int c) {
+                for (size_t i = 0; i < clive[c].size(); ++i)
+                    if (clive[c][i]) __atomic_store_n(&live[ids[c][i]], (uint8_t)1, __ATOMIC_RELAXED);
+            });
+            compact_live(out, live, par);
+        }
+        return 0;
     }
     if (n_trees > 0 && total != out.tree_nodes) { err = "internal: token count"; return -1; }
     int64_t nconst_all = 0;

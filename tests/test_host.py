@@ -590,6 +590,16 @@ def test_parallel_parse_equals_serial(simplify, order):
                 c.compile_tokens(bad)
             msgs.append(str(e.value))
         assert msgs[0] == msgs[1] and "tree 3000" in msgs[0]
+    # one immediate too many: the constant count check of both parses
+    extra = I.Tokens(tok.ops, np.append(tok.imm, np.float32(1.0)), tok.tree_off, tok.order)
+    with tgp.Context(host_only=True, plan_threads=1) as a, tgp.Context(host_only=True) as b:
+        msgs = []
+        for c in (a, b):
+            with pytest.raises(tgp.TgpError) as e:
+                c.compile_tokens(extra)
+            assert e.value.code == tgp.E_TOKENS
+            msgs.append(str(e.value))
+        assert msgs[0] == msgs[1] and "CONST tokens" in msgs[0]
 
 
 def test_column_flag_is_accepted_and_debug_plans_have_no_column_loads():

@@ -14,10 +14,12 @@
 #include "compiler.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <numeric>
 
 namespace tgp {
@@ -89,6 +91,41 @@ void Dag::assign_nodes(std::vector<DagNode>&& v) {
     rehash(cap);
 }
 
+// The fields of node n that follow from its key and its operands' fields
+// (`nodes` holds the operands): Sethi-Ullman slots, depth, cost as a tree.
+static void derive_fields(DagNode& n, const DagNode* nodes) {
+    const int op = n.op;
+    const int ar = arity(op);
+    if (ar == 3) {
+        // planned order: operand 0 and 1 parked in slots, operand 2 into A
+        const DagNode& a = nodes[n.kid[0]];
+        const DagNode& b = nodes[n.kid[1]];
+        const DagNode& c = nodes[n.kid[2]];
+        n.su = std::max(a.su, std::max(b.su + 1, c.su + 2));
+        n.depth = std::max(a.depth, std::max(b.depth, c.depth)) + 1;
+        n.cost = op_cost(op) + a.cost + b.cost + c.cost;
+    } else if (ar == 0) {
+        n.su = 0;
+        n.depth = 0;
+        n.cost = 0.f;
+    } else if (ar == 1) {
+        const DagNode& c = nodes[n.kid[0]];
+        n.su = c.su;
+        n.depth = c.depth + 1;
+        n.cost = op_cost(op) + c.cost;
+    } else {
+        const DagNode& l = nodes[n.kid[0]];
+        const DagNode& r = nodes[n.kid[1]];
+        bool ll = is_leaf(l.op), rl = is_leaf(r.op);
+        if (ll && rl) n.su = 0;
+        else if (ll) n.su = r.su;
+        else if (rl) n.su = l.su;
+        else n.su = l.su == r.su ? l.su + 1 : std::max(l.su, r.su);
+        n.depth = std::max(l.depth, r.depth) + 1;
+        n.cost = op_cost(op) + l.cost + r.cost;
+    }
+}
+
 int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     if (table_.empty()) rehash(1024);
     size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
@@ -103,35 +140,7 @@ int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
     n.kid[1] = k1;
     n.kid[2] = k2;
     n.imm = imm;
-    int ar = arity(op);
-    if (ar == 3) {
-        // planned order: operand 0 and 1 parked in slots, operand 2 into A
-        const DagNode& a = nodes[k0];
-        const DagNode& b = nodes[k1];
-        const DagNode& c = nodes[k2];
-        n.su = std::max(a.su, std::max(b.su + 1, c.su + 2));
-        n.depth = std::max(a.depth, std::max(b.depth, c.depth)) + 1;
-        n.cost = op_cost(op) + a.cost + b.cost + c.cost;
-    } else if (ar == 0) {
-        n.su = 0;
-        n.depth = 0;
-        n.cost = 0.f;
-    } else if (ar == 1) {
-        const DagNode& c = nodes[k0];
-        n.su = c.su;
-        n.depth = c.depth + 1;
-        n.cost = op_cost(op) + c.cost;
-    } else {
-        const DagNode& l = nodes[k0];
-        const DagNode& r = nodes[k1];
-        bool ll = is_leaf(l.op), rl = is_leaf(r.op);
-        if (ll && rl) n.su = 0;
-        else if (ll) n.su = r.su;
-        else if (rl) n.su = l.su;
-        else n.su = l.su == r.su ? l.su + 1 : std::max(l.su, r.su);
-        n.depth = std::max(l.depth, r.depth) + 1;
-        n.cost = op_cost(op) + l.cost + r.cost;
-    }
+    derive_fields(n, nodes.data());
     int32_t id = (int32_t)nodes.size();
     nodes.push_back(n);
     table_[h] = id;
@@ -439,6 +448,81 @@ static int parse_trees(const int32_t* ops, const float* imm, int64_t n_imm, cons
 // planning workers.
 constexpr int64_t kParallelParseTokens = 1 << 16;
 
+namespace {
+
+// Insert-only hash set of node keys that the chunks of a parse add to
+// concurrently.  A node gets a provisional id when it is first added (in
+// whatever order the workers reach it); its key is written before the slot
+// that publishes it (release / acquire).  A worker that loses the race for a
+// slot leaves its reserved node unreferenced and compares with the winner's.
+class MergeTable {
+public:
+    // max_nodes: the nodes the workers add, at most; workers: how many add
+    MergeTable(size_t max_nodes, int workers, const ParallelFor* par)
+        : nodes_(max_nodes + (size_t)workers * kBlock) {
+        size_t cap = 1024;
+        while (cap < 2 * max_nodes + 2) cap *= 2;
+        mask_ = cap - 1;
+        slot_.reset(new std::atomic<int32_t>[cap]);
+        const int P = 16;
+        (*par)(P, [&](int t) {
+            for (size_t i = cap * t / P; i < cap * (t + 1) / P; ++i) slot_[i].store(-1, std::memory_order_relaxed);
+        });
+    }
+    // A worker's block of ids to hand out (taken kBlock at a time, so the
+    // workers do not contend for one counter).
+    struct Ids {
+        int32_t next = 0, end = 0;
+    };
+    static constexpr int32_t kBlock = 256;
+    int32_t find_or_add(Ids& ids, int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
+        size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
+        int32_t mine = -1;
+        for (;;) {
+            int32_t s = slot_[h].load(std::memory_order_acquire);
+            if (s < 0) {
+                if (mine < 0) {
+                    if (ids.next == ids.end) {
+                        ids.next = count_.fetch_add(kBlock, std::memory_order_relaxed);
+                        ids.end = ids.next + kBlock;
+                    }
+                    mine = ids.next++;
+                    DagNode& n = nodes_[mine];
+                    n.op = op;
+                    n.kid[0] = k0;
+                    n.kid[1] = k1;
+                    n.kid[2] = k2;
+                    n.imm = imm;
+                }
+                int32_t expected = -1;
+                if (slot_[h].compare_exchange_strong(expected, mine, std::memory_order_release,
+                                                     std::memory_order_acquire))
+                    return mine;
+                s = expected;
+            }
+            const DagNode& n = nodes_[s];
+            if (n.op == op && n.kid[0] == k0 && n.kid[1] == k1 && n.kid[2] == k2 && n.imm == imm) return s;
+            h = (h + 1) & mask_;
+        }
+    }
+    const DagNode& node(int32_t id) const { return nodes_[id]; }
+    // ids handed out so far (some, at the ends of blocks, unused)
+    int32_t size() const { return count_.load(std::memory_order_relaxed); }
+
+private:
+    std::vector<DagNode> nodes_;
+    std::unique_ptr<std::atomic<int32_t>[]> slot_;
+    size_t mask_ = 0;
+    std::atomic<int32_t> count_{0};
+};
+
+void atomic_min_u64(std::atomic<uint64_t>& a, uint64_t v) {
+    uint64_t cur = a.load(std::memory_order_relaxed);
+    while (v < cur && !a.compare_exchange_weak(cur, v, std::memory_order_relaxed)) {}
+}
+
+}  // namespace
+
 int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const int64_t* tree_off,
                      int32_t n_trees, int32_t order, PopIR& out, std::string& err, bool simplify,
                      const ParallelFor* par) {
@@ -512,42 +596,96 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                 return rcs[c];
             }
         }
-        size_t nodes = 0;
-        for (const Dag& d : dags) nodes += d.size();
-        out.dag.reserve(nodes);
-        std::vector<std::vector<int32_t>> ids(n_chunks);
-        for (int c = 0; c < n_chunks; ++c) {
-            const Dag& d = dags[c];
-            std::vector<int32_t>& id = ids[c];
-            id.assign(d.size(), -1);
-            for (size_t i = 0; i < d.size(); ++i) {
-                const DagNode& x = d.nodes[i];
-                int32_t k[kMaxKids];
-                for (int j = 0; j < kMaxKids; ++j) k[j] = x.kid[j] >= 0 ? id[x.kid[j]] : -1;
-                if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && k[1] < k[0])
-                    std::swap(k[0], k[1]);
-                id[i] = out.dag.intern(x.op, k[0], k[1], x.imm, k[2]);
-            }
-            for (int32_t t = t_at[c]; t < t_at[c + 1]; ++t) out.roots[t] = id[out.roots[t]];
-            out.tree_nodes += toks[c];
-        }
+        for (int c = 0; c < n_chunks; ++c) out.tree_nodes += toks[c];
         if (n_trees > 0 && total != out.tree_nodes) { err = "internal: token count"; return -1; }
         if (imm_at[n_chunks] != n_imm) {
             fmt(err, "stream has %lld CONST tokens but n_imm = %lld", imm_at[n_chunks], n_imm);
             return -2;
         }
-        if (simplify) {
-            // a node of the population is reached from a root exactly when it
-            // is the image of a node its chunk's trees reach (the population's
-            // node has the images of the chunk node's operands): the same live
-            // set, hence the same nodes and ids, as compact() after a serial parse
-            std::vector<uint8_t> live(out.dag.size(), 0);
-            (*par)(n_chunks, [&](int c) {
-                for (size_t i = 0; i < clive[c].size(); ++i)
-                    if (clive[c][i]) __atomic_store_n(&live[ids[c][i]], (uint8_t)1, __ATOMIC_RELAXED);
-            });
-            compact_live(out, live, par);
+        // The chunks' nodes go into one population DAG.  Its nodes and ids
+        // must be those of a serial parse: nodes in the order of their first
+        // occurrence (chunk, then place in the chunk's DAG), with
+        // simplification only those a tree reaches, the operands of
+        // commutative operators in the order of those ids.  The chunks add
+        // their nodes to a shared hash set concurrently (provisional ids),
+        // then the first occurrence of every node fixes its id.
+        size_t n_chunk_nodes = 0;
+        for (const Dag& d : dags) n_chunk_nodes += d.size();
+        MergeTable mt(n_chunk_nodes, n_chunks, par);
+        std::vector<std::vector<int32_t>> pid(n_chunks);
+        (*par)(n_chunks, [&](int c) {
+            const Dag& d = dags[c];
+            std::vector<int32_t>& id = pid[c];
+            id.assign(d.size(), -1);
+            MergeTable::Ids block;
+            for (size_t i = 0; i < d.size(); ++i) {
+                const DagNode& x = d.nodes[i];
+                int32_t k[kMaxKids];
+                for (int j = 0; j < kMaxKids; ++j) k[j] = x.kid[j] >= 0 ? id[x.kid[j]] : -1;
+                // commutative operands in provisional-id order, so that both
+                // orders of a pair meet (the final order is set below)
+                if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && k[1] < k[0])
+                    std::swap(k[0], k[1]);
+                id[i] = mt.find_or_add(block, x.op, k[0], k[1], x.imm, k[2]);
+            }
+        });
+        // first occurrence of each node, as chunk << 32 | place; with
+        // simplification a node is kept when it is the image of a node its
+        // chunk's trees reach (a serial parse's live nodes)
+        const int32_t n_prov = mt.size();
+        std::unique_ptr<std::atomic<uint64_t>[]> first(new std::atomic<uint64_t>[(size_t)std::max(n_prov, 1)]);
+        std::vector<uint8_t> keep((size_t)std::max(n_prov, 1), simplify ? 0 : 1);
+        (*par)(16, [&](int t) {
+            for (int64_t g = (int64_t)n_prov * t / 16; g < (int64_t)n_prov * (t + 1) / 16; ++g)
+                first[g].store(UINT64_MAX, std::memory_order_relaxed);
+        });
+        (*par)(n_chunks, [&](int c) {
+            for (size_t i = 0; i < pid[c].size(); ++i) {
+                atomic_min_u64(first[pid[c][i]], (uint64_t)c << 32 | (uint64_t)i);
+                if (simplify && clive[c][i]) __atomic_store_n(&keep[pid[c][i]], (uint8_t)1, __ATOMIC_RELAXED);
+            }
+        });
+        // final ids: kept nodes numbered in the order of their first occurrence
+        std::vector<int64_t> base(n_chunks + 1, 0);
+        (*par)(n_chunks, [&](int c) {
+            int64_t k = 0;
+            for (size_t i = 0; i < pid[c].size(); ++i) {
+                const int32_t g = pid[c][i];
+                k += keep[g] && first[g].load(std::memory_order_relaxed) == ((uint64_t)c << 32 | (uint64_t)i);
+            }
+            base[c + 1] = k;
+        });
+        for (int c = 0; c < n_chunks; ++c) base[c + 1] += base[c];
+        std::vector<int32_t> fin((size_t)std::max(n_prov, 1), -1);
+        (*par)(n_chunks, [&](int c) {
+            int64_t k = base[c];
+            for (size_t i = 0; i < pid[c].size(); ++i) {
+                const int32_t g = pid[c][i];
+                if (keep[g] && first[g].load(std::memory_order_relaxed) == ((uint64_t)c << 32 | (uint64_t)i))
+                    fin[g] = (int32_t)k++;
+            }
+        });
+        const size_t n_final = (size_t)base[n_chunks];
+        std::vector<DagNode> final_nodes(n_final);
+        (*par)(16, [&](int t) {
+            for (int64_t g = (int64_t)n_prov * t / 16; g < (int64_t)n_prov * (t + 1) / 16; ++g) {
+                if (fin[g] < 0) continue;
+                DagNode x = mt.node((int32_t)g);
+                for (int j = 0; j < kMaxKids; ++j)
+                    if (x.kid[j] >= 0) x.kid[j] = fin[x.kid[j]];
+                final_nodes[fin[g]] = x;
+            }
+        });
+        // operand order and derived fields, in id order (operands first)
+        for (size_t f = 0; f < n_final; ++f) {
+            DagNode& x = final_nodes[f];
+            if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && x.kid[1] < x.kid[0])
+                std::swap(x.kid[0], x.kid[1]);
+            derive_fields(x, final_nodes.data());
         }
+        for (int c = 0; c < n_chunks; ++c)
+            for (int32_t t = t_at[c]; t < t_at[c + 1]; ++t) out.roots[t] = fin[pid[c][out.roots[t]]];
+        out.dag.assign_nodes(std::move(final_nodes));
         return 0;
     }
     if (n_trees > 0 && total != out.tree_nodes) { err = "internal: token count"; return -1; }

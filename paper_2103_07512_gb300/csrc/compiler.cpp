@@ -1350,12 +1350,17 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     // nodes with no x below them: their value is the same at all K points of
     // a thread (the points share a row), operands are interned before users
     std::vector<uint8_t> xfree(pop.dag.size(), 0);
-    for (size_t n = 0; n < pop.dag.size(); ++n) {
-        const DagNode& d = pop.dag.nodes[n];
-        bool f = d.op != T_X;
-        for (int c = 0; c < kMaxKids; ++c)
-            if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
-        xfree[n] = f;
+    const int64_t W = shape.W > 0 ? shape.W : shape.N;
+    const int64_t H = W > 0 ? shape.N / W : 0;
+    const bool tables = columns && W > 1 && H > 1;
+    if (!tables) {   // (with tables, the pass below forms it too)
+        for (size_t n = 0; n < pop.dag.size(); ++n) {
+            const DagNode& d = pop.dag.nodes[n];
+            bool f = d.op != T_X;
+            for (int c = 0; c < kMaxKids; ++c)
+                if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
+            xfree[n] = f;
+        }
     }
     // Column and row tables (grids of at least two rows and two columns, no
     // cache view): the largest costly subtrees with x and no y below them
@@ -1365,27 +1370,28 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     // one column of H points.
     std::vector<int32_t> col, row;
     std::vector<std::function<void()>> table_builds;   // run beside the groups' planning
-    const int64_t W = shape.W > 0 ? shape.W : shape.N;
-    const int64_t H = W > 0 ? shape.N / W : 0;
-    if (columns && W > 1 && H > 1) {
+    if (tables) {
         const size_t nn = pop.dag.size();
         const bool cview = cv && cv->active();
+        // one pass in id order (operands first): no x, no y, a cache load or
+        // store below (such a subtree is evaluated in this plan), eligible
         std::vector<uint8_t> yfree(nn, 0), celig(nn, 0), relig(nn, 0), cneed(nn, 0), rneed(nn, 0), blocked(nn, 0);
         for (size_t n = 0; n < nn; ++n) {
             const DagNode& d = pop.dag.nodes[n];
-            bool f = d.op != T_Y;
-            // a subtree holding a cache load or store is evaluated in this plan
+            bool fx = d.op != T_X, fy = d.op != T_Y;
             bool b = cview && (cv->cached[n] >= 0 || cv->insert[n] >= 0);
             for (int c = 0; c < kMaxKids; ++c)
                 if (d.kid[c] >= 0) {
-                    f = f && yfree[d.kid[c]];
+                    fx = fx && xfree[d.kid[c]];
+                    fy = fy && yfree[d.kid[c]];
                     b = b || blocked[d.kid[c]];
                 }
-            yfree[n] = f;
+            xfree[n] = fx;
+            yfree[n] = fy;
             blocked[n] = b;
             const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost && !b;
-            celig[n] = costly && f && !xfree[n];
-            relig[n] = costly && xfree[n];
+            celig[n] = costly && fy && !fx;
+            relig[n] = costly && fx;
         }
         for (int32_t r : pop.roots) {
             cneed[r] = celig[r];

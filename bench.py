@@ -408,14 +408,55 @@ def run_ours(args):
     }
     if not args.no_extras and world == 1:
         line["other_configs"] = {
+            "small_population": bench_small_population(tgp.Context, dev, flush),
             "population_at_scale": bench_population_at_scale(tgp.Context, dev, flush, costs, peak_add, peak_fma),
             "evolution": bench_evolution(tgp.Context, dev),
             "serving": bench_serving(tgp, dev),
         }
+        # the oracle, one thread, on a bounded sample of the 1024x1024 population
+        tok2, g2 = I.population_at_scale(seed=1)
+        v2, info2 = cpu_oracle_rate(tok2, g2, target_seconds=4.0)
+        line["other_configs"]["population_at_scale"]["cpu_baseline"] = {
+            "value": v2, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{info2['rows']} of {g2.H} rows ({info2['points']} points), all {tok2.n_trees} trees, "
+                      f"{info2['seconds']:.1f} s, one thread"}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bench_small_population(ctx_cls, dev, flush, steps=50):
+    """50 RHH trees (depth 2-6) on 64x64 (the small configuration): direct
+    launches (tgp_fitness_dev) timed with CUDA events, and the oracle on the
+    whole grid, one thread."""
+    import torch
+    tok, g = I.small_population(seed=0)
+    ctx = ctx_cls(device=dev.index)
+    dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    pop = ctx.compile_tokens(tok)
+    rmse = torch.empty(tok.n_trees, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(5):
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        ctx.fitness_dev(pop, dom, rmse, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    units = int(tok.ops.size) * g.N
+    ctx.close()
+    cv, info = cpu_oracle_rate(tok, g, target_seconds=2.0)
+    return {"workload": "small_population: 50 RHH trees depth 2-6, 64x64 grid, Pagie target, seed 0",
+            "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "tree_nodes": int(tok.ops.size),
+            "l2": "flushed between steps", "note": "a launch-latency-bound size (4,096 points)",
+            "cpu_baseline": {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{info['rows']} of {g.H} rows ({info['points']} points), all "
+                                       f"{tok.n_trees} trees, {info['seconds']:.2f} s, one thread"}}
 
 
 def bench_population_at_scale(ctx_cls, dev, flush, costs, peak_add, peak_fma, steps=50):

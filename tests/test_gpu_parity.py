@@ -76,6 +76,34 @@ def test_odd_grids_and_ragged_tails(W, H, K):
         full_check(c, tok, I.Grid(W, H), f"{W}x{H} K={K}", budget=None)
 
 
+@pytest.mark.parametrize("K,threads", [(1, 32), (2, 64), (4, 128), (8, 128), (16, 128)])
+def test_residual_squares_beyond_binary32_and_root_batches(K, threads):
+    """Trees whose values stay finite in binary32 but whose squared residuals
+    do not (|v| up to 1e26, squares up to 1e52): the sums are formed from
+    residuals scaled by 2^-80, in warps that mix scaled and unscaled threads
+    (max(x, 0) is 0 on half the grid), next to ordinary trees, in batches of
+    roots that end at every place of the group (10 trees: two full batches and
+    one of two), on a grid with ragged chunks.  Every RMSE is the oracle's
+    binary64 one within 1e-5 (binary32 squares and sums: below 2^-19)."""
+    X, Y = I.leaf(I.X), I.leaf(I.Y)
+
+    def C(v):
+        return I.leaf(I.CONST, np.float32(v))
+    n = I.node
+    trees = [n(I.MUL, X, C(1e25)), n(I.ADD, X, Y), n(I.MUL, n(I.MAX, X, C(0.0)), C(3e25)),
+             n(I.MUL, n(I.MUL, X, Y), C(4e24)), n(I.SUB, X, C(0.25)), n(I.MUL, n(I.SIN, X), C(1e21)),
+             n(I.MUL, Y, C(2e19)), n(I.DIV, X, C(7.0)), n(I.MUL, n(I.MIN, Y, C(0.5)), C(-6e25)), Y]
+    tok = I.to_tokens(trees)
+    g = I.Grid(37, 29)
+    with tgp.Context(points_per_thread=K, threads_per_block=threads) as c:
+        dom = load(c, g)
+        pop = c.compile_tokens(tok)
+        fit = c.fitness(pop, dom, tok.n_trees)
+    r64, _, _ = oracle.fitness(tok.ops, tok.imm, tok.tree_off, tok.order, g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+    assert np.all(np.isfinite(fit)) and np.all(np.isfinite(r64))
+    np.testing.assert_allclose(fit, r64, rtol=1e-5, atol=0)
+
+
 def test_other_domain_bounds():
     tok, _ = I.small_population(seed=6)
     with tgp.Context() as c:

@@ -164,7 +164,14 @@ typedef struct tgp_config {
     int32_t plan_threads;        /* host threads that plan a population's tree groups
                                     concurrently (the calling thread included); 0 = up to 8,
                                     1 = serial.  The bytecode does not depend on it. */
-    int32_t reserved[3];
+    int32_t cache_ids_max;       /* with the cache on, cache entries are keyed by a context-wide
+                                    DAG of every subtree adopted so far (exact structural
+                                    identity).  Past this many nodes, and past twice what the
+                                    live populations held at its last rebuild, that DAG is
+                                    rebuilt from the live populations and the cache flushed:
+                                    host memory stays bounded in a long-running process.
+                                    0 = 2^23 (about 400 MB). */
+    int32_t reserved[2];
 } tgp_config;
 
 /* A target given as one expression tree (TGP_TARGET_TOKENS). */
@@ -198,7 +205,9 @@ typedef struct tgp_stats {
     int64_t eval_timed;       /* TGP_F_TIME_KERNELS: launches summed in eval_ms_sum */
     int64_t cache_reserved;   /* HBM reserved for the cache (slabs carved into entries; at most
                                  the budget, freed with the context) */
-    int64_t reserved[5];
+    int64_t cache_id_nodes;   /* nodes of the context-wide DAG that keys the cache */
+    int64_t cache_id_rebuilds;   /* its rebuilds (each a full flush of the cache) */
+    int64_t reserved[3];
 } tgp_stats;
 
 /* Creates a context on cfg->device (cfg may be NULL: device 0, defaults). */

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
                 ("cache_budget_bytes", ctypes.c_int64),
                 ("points_per_thread", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("n_groups", ctypes.c_int32), ("cache_min_cost", ctypes.c_int32),
-                ("plan_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("plan_threads", ctypes.c_int32), ("cache_ids_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TargetTokens(ctypes.Structure):
@@ -63,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("cache_hits", ctypes.c_int64), ("cache_inserts", ctypes.c_int64),
                 ("cache_evictions", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("eval_ms_sum", ctypes.c_double), ("eval_timed", ctypes.c_int64),
-                ("cache_reserved", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+                ("cache_reserved", ctypes.c_int64), ("cache_id_nodes", ctypes.c_int64),
+                ("cache_id_rebuilds", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -187,7 +189,7 @@ class Context:
 
     def __init__(self, device=0, host_only=False, cache_budget_bytes=0, points_per_thread=0,
                  threads_per_block=0, n_groups=0, dedup=True, time_kernels=False, cache_min_cost=0,
-                 simplify=True, trig="pi", plan_threads=0, columns=True):
+                 simplify=True, trig="pi", plan_threads=0, columns=True, cache_ids_max=0):
         """trig: "pi" (sin(a) = sin(pi a), Sec. 3.2) or "rad" (radians, the
         footnote of Table 1), for sin, cos and tan."""
         if trig not in ("pi", "rad"):
@@ -204,6 +206,7 @@ class Context:
         cfg.n_groups = n_groups
         cfg.cache_min_cost = cache_min_cost
         cfg.plan_threads = plan_threads
+        cfg.cache_ids_max = cache_ids_max
         h = ctypes.c_void_p()
         self._h = None
         self._check(self._L.tgp_create(ctypes.byref(h), ctypes.byref(cfg)))

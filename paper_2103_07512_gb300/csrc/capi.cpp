@@ -207,6 +207,7 @@ struct tgp_ctx {
     std::map<std::tuple<int, int, int, size_t>, int> occ;   // (K, pheno*2+ext, threads, smem) -> blocks/SM
     std::map<TuneKey, TuneChoice> tuned;                     // tgp_autotune results
     Dag gdag;                                                // context-wide DAG (cache on)
+    size_t gdag_live = 0;                                    // its nodes after the last rebuild
     int64_t epoch = 0;                                       // calls that used the cache
     int64_t cache_bytes = 0;                                 // held by live entries
     int64_t cache_reserved = 0;                              // device memory of the slabs (<= budget)
@@ -905,21 +906,59 @@ int fitness_to_device(tgp_ctx* c, Population* pop, Domain* d, cudaStream_t s, do
     return TGP_OK;
 }
 
+// Context-wide ids of a population's nodes (its nodes interned into the
+// context-wide DAG, kids first).
+void intern_gids(tgp_ctx* ctx, Population* pop) {
+    const auto& nodes = pop->ir.dag.nodes;
+    pop->gid.resize(nodes.size());
+    for (size_t n = 0; n < nodes.size(); ++n) {
+        const DagNode& dn = nodes[n];
+        int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
+        int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
+        int32_t k2 = dn.kid[2] >= 0 ? pop->gid[dn.kid[2]] : -1;
+        pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm, k2);
+    }
+}
+
+// The context-wide DAG keeps every subtree of every population adopted with
+// the cache on.  Past cfg.cache_ids_max nodes, and past twice the nodes the
+// live populations held at the last rebuild, it is rebuilt from the live
+// populations; the cache entries, keyed by its ids, are flushed first (their
+// blocks return to the free list with their fences, as an eviction's do),
+// and so are the domains' admission sets.  The cache is an optimisation:
+// results are bitwise those without it either way.
+void bound_gids(tgp_ctx* ctx, const Population* adopting) {
+    const size_t cap = ctx->cfg.cache_ids_max > 0 ? (size_t)ctx->cfg.cache_ids_max : ((size_t)1 << 23);
+    if (ctx->gdag.size() <= cap || ctx->gdag.size() <= 2 * ctx->gdag_live) return;
+    for (auto& dk : ctx->domains) {
+        Domain& d = *dk.second;
+        for (auto& kv : d.cache) {
+            ctx->stats.cache_evictions++;
+            ctx->cache_bytes -= (int64_t)kv.second->cap * (int64_t)sizeof(float);
+            const size_t vcap = kv.second->cap;
+            ctx->cache_free.emplace(vcap, std::move(kv.second));
+        }
+        d.cache.clear();
+        d.seen.clear();
+    }
+    ctx->gdag = Dag();
+    for (auto& pk : ctx->pops) {
+        Population* p = pk.second.get();
+        if (p != adopting && !p->gid.empty()) intern_gids(ctx, p);
+    }
+    ctx->gdag_live = ctx->gdag.size();
+    ctx->stats.cache_id_rebuilds++;
+}
+
 // Registers a population's IR with the context (lock held): context-wide
 // subtree ids when the cache is on (the cache key of a subtree across
 // populations), and the population counters.
 void adopt_ir(tgp_ctx* ctx, Population* pop) {
     pop->gid.clear();
     if (cache_on(ctx)) {
-        const auto& nodes = pop->ir.dag.nodes;
-        pop->gid.resize(nodes.size());
-        for (size_t n = 0; n < nodes.size(); ++n) {   // kids precede parents
-            const DagNode& dn = nodes[n];
-            int32_t k0 = dn.kid[0] >= 0 ? pop->gid[dn.kid[0]] : -1;
-            int32_t k1 = dn.kid[1] >= 0 ? pop->gid[dn.kid[1]] : -1;
-            int32_t k2 = dn.kid[2] >= 0 ? pop->gid[dn.kid[2]] : -1;
-            pop->gid[n] = ctx->gdag.intern(dn.op, k0, k1, dn.imm, k2);
-        }
+        bound_gids(ctx, pop);
+        intern_gids(ctx, pop);
+        ctx->stats.cache_id_nodes = (int64_t)ctx->gdag.size();
     }
     ctx->stats.tree_nodes = pop->ir.tree_nodes;
     ctx->stats.dag_nodes = (int64_t)pop->ir.dag.size();

@@ -142,3 +142,38 @@ def test_tabled_subtrees_are_not_stored(columns):
         assert st["cache_inserts"] == 2 and st["cache_hits"] == 2, st
     else:
         assert st["cache_inserts"] == 9 and st["cache_hits"] == 9, st
+
+
+def test_cache_ids_stay_bounded_and_the_cache_keeps_working():
+    """The context-wide DAG that keys the cache is rebuilt from the live
+    populations (a full flush of the cache) once it passes cache_ids_max:
+    many populations adopted one after the other, two alive at a time, each
+    evaluated three times (its subtrees are seen, then stored, then loaded).
+    Every result is bitwise that of a context without the cache, the DAG
+    stays near its bound, and loads keep happening after the rebuilds."""
+    g = I.Grid(128, 96)
+    cap = 1000   # about two populations' nodes
+    with tgp.Context(cache_budget_bytes=256 * g.N * 4, cache_min_cost=4, cache_ids_max=cap) as a, \
+            tgp.Context() as b:
+        da = a.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+        db = b.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
+        live = []
+        hits_after = None
+        for seed in range(14):
+            tok, _ = I.small_population(seed=100 + seed)
+            pa, pb = a.compile_tokens(tok), b.compile_tokens(tok)
+            ref = b.fitness(pb, db, tok.n_trees)
+            for call in range(3):
+                got = a.fitness(pa, da, tok.n_trees)
+                assert np.array_equal(got.view(np.int64), ref.view(np.int64)), f"population {seed} call {call}"
+            b.release_population(pb)
+            live.append(pa)
+            if len(live) > 2:
+                a.release_population(live.pop(0))
+            st = a.stats()
+            assert st["cache_id_nodes"] <= 2 * cap + 8 * tok.ops.size
+            if st["cache_id_rebuilds"] >= 1 and hits_after is None:
+                hits_after = st["cache_hits"]
+        st = a.stats()
+        assert st["cache_id_rebuilds"] >= 2
+        assert hits_after is not None and st["cache_hits"] > hits_after

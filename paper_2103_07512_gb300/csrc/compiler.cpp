@@ -703,14 +703,41 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
 
 namespace {
 
+// Per-node arrays of a planner, sized to the DAG and at their initial values
+// between planners (a planner puts back every entry it changes).  One set per
+// host thread, reused by the next planner on that thread: planning the groups
+// and tables of a population then neither allocates nor clears them again.
+struct GenScratch {
+    std::vector<int32_t> uses, where, first_pos, last_pos;
+    std::vector<uint8_t> keep, stored, mark;
+    bool in_use = false;
+    void fit(size_t n) {
+        if (uses.size() >= n) return;
+        uses.resize(n, 0);
+        where.resize(n, -1);
+        first_pos.resize(n, -1);
+        last_pos.resize(n, -1);
+        keep.resize(n, 0);
+        stored.resize(n, 0);
+        mark.resize(n, 0);
+    }
+};
+thread_local GenScratch tls_scratch;
+
 class GroupGen {
 public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
              const std::vector<uint8_t>* xfree, const std::vector<int32_t>* col, const std::vector<int32_t>* row)
-        : d_(dag), out_(out), uses_(dag.size(), 0), where_(dag.size(), -1), keep_(dag.size(), 0),
-          first_pos_(dag.size(), -1), last_pos_(dag.size(), -1), dedup_(dedup), kept_cap_(kept_cap),
-          cv_(cv && cv->active() ? cv : nullptr), stored_(dag.size(), 0), mark_(dag.size(), 0), xfree_(xfree),
+        : sc_(take_scratch(dag.size())), d_(dag), out_(out), uses_(sc_->uses), where_(sc_->where), keep_(sc_->keep),
+          first_pos_(sc_->first_pos), last_pos_(sc_->last_pos), dedup_(dedup), kept_cap_(kept_cap),
+          cv_(cv && cv->active() ? cv : nullptr), stored_(sc_->stored), mark_(sc_->mark), xfree_(xfree),
           col_(col), row_(row) {}
+    ~GroupGen() {
+        for (int32_t n : stored_all_) stored_[n] = 0;
+        if (sc_ == &tls_scratch) tls_scratch.in_use = false;
+    }
+    GroupGen(const GroupGen&) = delete;
+    GroupGen& operator=(const GroupGen&) = delete;
 
     int slot_high = 0;                    // slots used by the last run
     void set_kept_cap(int c) { kept_cap_ = c; }
@@ -742,6 +769,21 @@ public:
     }
 
 private:
+    // The thread's scratch, or a fresh set when the thread's is held (a
+    // planner inside a planner on one thread).
+    std::unique_ptr<GenScratch> own_;
+    GenScratch* take_scratch(size_t n) {
+        GenScratch* g = &tls_scratch;
+        if (g->in_use) {
+            own_ = std::make_unique<GenScratch>();
+            g = own_.get();
+        }
+        g->in_use = true;
+        g->fit(n);
+        return g;
+    }
+    GenScratch* sc_;
+
     // A shared node is kept (evaluated once, held in a slot until its last
     // use) when its subtree costs at least this much per point and its uses
     // lie in at most kKeepSpan + 1 consecutive trees of the group; otherwise
@@ -752,20 +794,22 @@ private:
 
     const Dag& d_;
     std::vector<IrIns>& out_;
-    std::vector<int32_t> uses_;    // evaluations of the node still to be consumed
-    std::vector<int32_t> where_;   // slot holding the node, or -1
-    std::vector<uint8_t> keep_;    // evaluated once and held
-    std::vector<int32_t> first_pos_, last_pos_;   // tree positions of first / last use
+    std::vector<int32_t>& uses_;    // evaluations of the node still to be consumed
+    std::vector<int32_t>& where_;   // slot holding the node, or -1
+    std::vector<uint8_t>& keep_;    // evaluated once and held
+    std::vector<int32_t>& first_pos_;   // tree positions of first / last use
+    std::vector<int32_t>& last_pos_;
     std::vector<int32_t> span_touched_;
     std::vector<int32_t> touched_;
     bool dedup_;
     int kept_cap_;                 // slots a kept node may use; temporaries may go beyond
     const CacheView* cv_;          // cross-call cache, or nullptr
-    std::vector<uint8_t> stored_;  // cache store already emitted (this plan)
+    std::vector<uint8_t>& stored_;  // cache store already emitted (this plan)
     std::vector<int32_t> stored_log_;   // stores of the current group attempt
+    std::vector<int32_t> stored_all_;   // every store emitted (put back to 0 at the end)
     std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
-    std::vector<uint8_t> mark_;    // scratch of sort_touched_descending, all zero between calls
+    std::vector<uint8_t>& mark_;    // scratch of sort_touched_descending, all zero between calls
     const std::vector<uint8_t>* xfree_;   // node has no x below it (or nullptr)
     const std::vector<int32_t>* col_;     // column-table entry of a node, -1 (or nullptr: none)
     const std::vector<int32_t>* row_;     // row-table entry of a node, -1 (or nullptr: none)
@@ -933,6 +977,7 @@ private:
                 emit(F_CST, 0, 0, 0, cv_->insert[n], 0);
                 stored_[n] = 1;
                 stored_log_.push_back(n);
+                stored_all_.push_back(n);
             }
         }
         // a kept node is held for the uses that remain after the current one

@@ -734,7 +734,11 @@ public:
           col_(col), row_(row) {}
     ~GroupGen() {
         for (int32_t n : stored_all_) stored_[n] = 0;
-        if (sc_ == &tls_scratch) tls_scratch.in_use = false;
+        if (sc_ == &tls_scratch) {
+            // a very large DAG's arrays are not kept (19 bytes per node per thread)
+            if (tls_scratch.uses.size() > ((size_t)1 << 22)) tls_scratch = GenScratch();
+            tls_scratch.in_use = false;
+        }
     }
     GroupGen(const GroupGen&) = delete;
     GroupGen& operator=(const GroupGen&) = delete;

@@ -1232,7 +1232,8 @@ constexpr float kColMinCost = 4.f;
 constexpr size_t kColMaxEntries = 16384;
 
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns, bool table_plan);
+                            const ParallelFor* par, bool columns, bool table_plan,
+                            const std::vector<uint8_t>* xfree_given = nullptr);
 
 // Encodes groups [0, n) of `ir` (group g at [off[g], off[g + 1])) onto
 // `code`, appending each group's end offset (code.size() after it) to
@@ -1310,7 +1311,8 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
 // table_plan: the plan of column or row tables (their subtrees in id order:
 // the ordering pass would cost more than it saves on these small launches).
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns, bool table_plan) {
+                            const ParallelFor* par, bool columns, bool table_plan,
+                            const std::vector<uint8_t>* xfree_given) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -1398,17 +1400,20 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     // Sethi-Ullman number).
     // nodes with no x below them: their value is the same at all K points of
     // a thread (the points share a row), operands are interned before users
-    std::vector<uint8_t> xfree(pop.dag.size(), 0);
+    // (a table's plan takes its population's: the same DAG)
+    std::vector<uint8_t> xfree_own;
+    if (!xfree_given) xfree_own.assign(pop.dag.size(), 0);
+    const std::vector<uint8_t>& xfree = xfree_given ? *xfree_given : xfree_own;
     const int64_t W = shape.W > 0 ? shape.W : shape.N;
     const int64_t H = W > 0 ? shape.N / W : 0;
-    const bool tables = columns && W > 1 && H > 1;
-    if (!tables) {   // (with tables, the pass below forms it too)
+    const bool tables = columns && W > 1 && H > 1 && !xfree_given;   // (a table's plan has none)
+    if (!tables && !xfree_given) {   // (with tables, the pass below forms it too)
         for (size_t n = 0; n < pop.dag.size(); ++n) {
             const DagNode& d = pop.dag.nodes[n];
             bool f = d.op != T_X;
             for (int c = 0; c < kMaxKids; ++c)
-                if (d.kid[c] >= 0) f = f && xfree[d.kid[c]];
-            xfree[n] = f;
+                if (d.kid[c] >= 0) f = f && xfree_own[d.kid[c]];
+            xfree_own[n] = f;
         }
     }
     // Column and row tables (grids of at least two rows and two columns, no
@@ -1431,11 +1436,11 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             bool b = cview && (cv->cached[n] >= 0 || cv->insert[n] >= 0);
             for (int c = 0; c < kMaxKids; ++c)
                 if (d.kid[c] >= 0) {
-                    fx = fx && xfree[d.kid[c]];
+                    fx = fx && xfree_own[d.kid[c]];
                     fy = fy && yfree[d.kid[c]];
                     b = b || blocked[d.kid[c]];
                 }
-            xfree[n] = fx;
+            xfree_own[n] = fx;
             yfree[n] = fy;
             blocked[n] = b;
             const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost && !b;
@@ -1488,8 +1493,9 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             tplan = std::make_shared<HostPlan>();
             HostPlan* tp = tplan.get();
             const bool big = R >= 256;
-            table_builds.push_back([&pop, &roots, costs, ts, tp, par, big]() {
-                build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tp, nullptr, big ? par : nullptr, false, true);
+            table_builds.push_back([&pop, &roots, &xfree, costs, ts, tp, par, big]() {
+                build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tp, nullptr, big ? par : nullptr, false, true,
+                                &xfree);
             });
         };
         make_tables(cneed, col, plan.col_roots, plan.col_plan, plan.col_stride, W, W);

@@ -410,6 +410,7 @@ def run_ours(args):
         line["other_configs"] = {
             "small_population": bench_small_population(tgp.Context, dev, flush),
             "population_at_scale": bench_population_at_scale(tgp.Context, dev, flush, costs, peak_add, peak_fma),
+            "all_operators": bench_all_operators(tgp.Context, dev, flush, costs, peak_add, peak_fma),
             "evolution": bench_evolution(tgp.Context, dev),
             "serving": bench_serving(tgp, dev),
         }
@@ -463,8 +464,28 @@ def bench_population_at_scale(ctx_cls, dev, flush, costs, peak_add, peak_fma, st
     """100 RHH trees (depth 2-8) on 1024x1024, population-wide DAG: direct
     launches (tgp_fitness_dev) timed with CUDA events; the interpreter's own
     time from the library's kernel events; phenotypes to HBM."""
-    import torch
     tok, g = I.population_at_scale(seed=1)
+    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, WORKLOAD_C2, PROFILE_C2,
+                          steps, phenotypes=True)
+
+
+def bench_all_operators(ctx_cls, dev, flush, costs, peak_add, peak_fma, steps=50):
+    """100 RHH trees (depth 2-8) over every function of Table 1 (the 21 of
+    the extended set: tan, exp, log, pow, mod and the rest beside the
+    benchmark's ten) on 1024x1024, Pagie target: the interpreter variant with
+    the rest of Table 1, timed as the 1024x1024 population."""
+    tok = I.to_tokens(I.ramped_half_and_half(100, 2, 8, np.random.default_rng(7), I.ALL_FUNCTIONS))
+    g = I.Grid(1024, 1024)
+    workload = ("all_operators: 100 RHH trees depth 2-8 over all 21 functions of Table 1, 1024x1024 grid, "
+                "Pagie target, seed 7")
+    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, None, steps)
+
+
+def fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, profile, steps,
+                   phenotypes=False):
+    """Direct fitness launches of one population, timed with CUDA events,
+    with the roofline of the work they evaluate as planned."""
+    import torch
     ctx = ctx_cls(device=dev.index, time_kernels=True)
     dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     pop = ctx.compile_tokens(tok)
@@ -486,16 +507,17 @@ def bench_population_at_scale(ctx_cls, dev, flush, costs, peak_add, peak_fma, st
     kern_ms = (s1["eval_ms_sum"] - s0["eval_ms_sum"]) / max(1, s1["eval_timed"] - s0["eval_timed"])
     units = int(tok.ops.size) * g.N
     work, w_ops, _ = executed_work(ctx, pop, dom, costs)
-    out = {"workload": WORKLOAD_C2, "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    out = {"workload": workload, "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
            "tree_nodes": int(tok.ops.size), "dag_internal_nodes": int(s1["dag_internal"]),
            "points_per_thread": int(s1["points_per_thread"]), "threads_per_block": int(s1["threads_per_block"]),
            "groups": int(s1["n_groups"]),
            "roofline": roofline(work, tree_work(tok, costs) * g.N, units, kern_ms, peak_add, peak_fma,
-                                profile_traffic(PROFILE_C2), costs, w_ops),
+                                profile_traffic(profile) if profile else None, costs, w_ops),
            "l2": "flushed between steps"}
     out["roofline"]["kernel_ms_note"] = ("interpreter and table launches, CUDA events the library records "
                                          "around them on the stream (TGP_F_TIME_KERNELS)")
-    out["phenotype"] = bench_phenotype(ctx, pop, dom, tok, g, dev, flush)
+    if phenotypes:
+        out["phenotype"] = bench_phenotype(ctx, pop, dom, tok, g, dev, flush)
     ctx.close()
     return out
 
@@ -788,7 +810,7 @@ def main():
                     help="skip the other configurations (1024x1024 population, evolution, serving)")
     ap.add_argument("--sharded", action="store_true",
                     help="the 1024x1024 population with its rows split over the ranks (strong scaling)")
-    ap.add_argument("--only", choices=["population_at_scale"],
+    ap.add_argument("--only", choices=["population_at_scale", "all_operators"],
                     help="measure one other configuration alone and print its line (for profiling it)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -805,7 +827,8 @@ def main():
             costs = c.calibrate_op_costs()
             pa, pf = c.calibrate_peak()
         torch.cuda.nvtx.range_push("timed")
-        r = bench_population_at_scale(tgp.Context, dev, flush, costs, pa, pf, steps=args.steps)
+        leg = bench_population_at_scale if args.only == "population_at_scale" else bench_all_operators
+        r = leg(tgp.Context, dev, flush, costs, pa, pf, steps=args.steps)
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"config": args.only, **r}))
         return 0

@@ -162,8 +162,9 @@ typedef struct tgp_config {
                                     a subtree with no x or no y below it is never stored and counts
                                     as one add in the cost of the subtrees above it. */
     int32_t plan_threads;        /* host threads that plan a population's tree groups
-                                    concurrently (the calling thread included); 0 = up to 8,
-                                    1 = serial.  The bytecode does not depend on it. */
+                                    concurrently (the calling thread included); 0 = up to 16
+                                    (at most the host's hardware threads), 1 = serial.  The
+                                    bytecode does not depend on it. */
     int32_t cache_ids_max;       /* with the cache on, cache entries are keyed by a context-wide
                                     DAG of every subtree adopted so far (exact structural
                                     identity).  Past this many nodes, and past twice what the

@@ -1285,7 +1285,7 @@ int tgp_create(tgp_ctx** out, const tgp_config* cfg) {
     {
         // planning workers besides the calling thread
         const unsigned hw = std::thread::hardware_concurrency();
-        const int want = c->cfg.plan_threads > 0 ? c->cfg.plan_threads : 8;
+        const int want = c->cfg.plan_threads > 0 ? c->cfg.plan_threads : 16;
         const int workers = (int)std::min<unsigned>((unsigned)(want - 1), hw > 1 ? hw - 1 : 0);
         c->pool = std::make_unique<WorkerPool>(workers);
         WorkerPool* pool = c->pool.get();

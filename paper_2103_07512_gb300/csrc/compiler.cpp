@@ -1512,7 +1512,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     if (par && *par && G > 1 && !(cv && cv->active())) {
         // contiguous runs of groups, one planner (and its per-node arrays)
         // each, and the tables' plans as tasks of their own
-        const int P = std::min(G, 16);
+        const int P = std::min(G, 32);
         const int NT = (int)table_builds.size();
         // each run is planned and encoded on its own; the runs are then
         // placed back to back (offsets shifted)

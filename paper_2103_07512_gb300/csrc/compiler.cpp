@@ -86,9 +86,10 @@ void Dag::reserve(size_t n) {
 void Dag::assign_nodes(std::vector<DagNode>&& v) {
     nodes = std::move(v);
     used_ = nodes.size();
-    size_t cap = 1024;
-    while (cap < 2 * used_ + 2) cap *= 2;
-    rehash(cap);
+    // the index is rebuilt by the first intern, if any comes (a parsed
+    // population is mostly only planned)
+    table_.clear();
+    table_.shrink_to_fit();
 }
 
 // The fields of node n that follow from its key and its operands' fields
@@ -127,7 +128,11 @@ static void derive_fields(DagNode& n, const DagNode* nodes) {
 }
 
 int32_t Dag::intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
-    if (table_.empty()) rehash(1024);
+    if (table_.empty()) {
+        size_t cap = 1024;
+        while (cap < 2 * nodes.size() + 2) cap *= 2;
+        rehash(cap);
+    }
     size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
     while (table_[h] >= 0) {
         const DagNode& n = nodes[table_[h]];

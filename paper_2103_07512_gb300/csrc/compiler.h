@@ -31,7 +31,7 @@ public:
     // Room for n nodes without growing the node array or the hash table.
     void reserve(size_t n);
     // Takes `v` as the node array (distinct keys, operands before their
-    // users) and rebuilds the hash index over it.
+    // users); the hash index over it is rebuilt by the next intern.
     void assign_nodes(std::vector<DagNode>&& v);
 
 private:

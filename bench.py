@@ -48,6 +48,7 @@ WORKLOAD = ("batched_uneven: 4096 trees of U{3..255} nodes, depth <= 12, ~30% du
 WORKLOAD_C2 = "population_at_scale: 100 RHH trees depth 2-8, 1024x1024 grid, Pagie target, seed 1"
 PROFILE = os.path.join(HERE, "profiles", "eval_kernel_batched_uneven.md")
 PROFILE_C2 = os.path.join(HERE, "profiles", "eval_kernel_population_at_scale.md")
+PROFILE_OPS = os.path.join(HERE, "profiles", "eval_kernel_all_operators.md")
 KERNEL_SRCS = [os.path.join(HERE, "paper_2103_07512_gb300", "csrc", f)
                for f in ("kernels.cu", "gen_fastloop.py", "tgp_ir.h")]
 
@@ -478,7 +479,7 @@ def bench_all_operators(ctx_cls, dev, flush, costs, peak_add, peak_fma, steps=50
     g = I.Grid(1024, 1024)
     workload = ("all_operators: 100 RHH trees depth 2-8 over all 21 functions of Table 1, 1024x1024 grid, "
                 "Pagie target, seed 7")
-    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, None, steps)
+    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, PROFILE_OPS, steps)
 
 
 def fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, profile, steps,

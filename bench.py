@@ -764,6 +764,8 @@ def _serve_run(tgp, ctx, jobs, rate, seconds, rng, streams, clients=4):
             "drain_s": (last - last_sub) * 1e-9,
             "worker_busy_frac": st["worker_busy_ns"] * 1e-9 / span,
             "domain_load_frac": st["domain_load_ns"] * 1e-9 / span,
+            "adopt_frac": st["adopt_ns"] * 1e-9 / span,
+            "fitness_call_frac": st["fitness_ns"] * 1e-9 / span,
             "kernel_busy_frac": (k1["eval_ms_sum"] - k0["eval_ms_sum"]) * 1e-3 / span}
 
 

@@ -562,7 +562,10 @@ typedef struct tgp_server_stats {
     int64_t worker_busy_ns;      /* host time the worker spent preparing and enqueueing launches */
     int64_t domain_load_ns;      /* part of it spent loading domains */
     int64_t max_batch_domains;   /* most domains fused into one launch */
-    int64_t reserved[2];
+    int64_t adopt_ns;            /* part of it registering the launches' populations with the
+                                    context (their context-wide ids when the cache is on) */
+    int64_t fitness_ns;          /* part of it in the fitness calls (cache view, plan, upload,
+                                    launches) */
 } tgp_server_stats;
 
 /* Starts a server on ctx (a device context; the server uses it from its

@@ -97,7 +97,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "submitted", "completed", "failed", "batches", "max_batch_jobs", "max_in_flight", "domains_resident",
         "domains_loaded", "domains_released", "bytes_in_use", "max_bytes_in_use", "hbm_budget_bytes", "queued",
-        "worker_busy_ns", "domain_load_ns", "max_batch_domains")] + [("reserved", ctypes.c_int64 * 2)]
+        "worker_busy_ns", "domain_load_ns", "max_batch_domains", "adopt_ns", "fitness_ns")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

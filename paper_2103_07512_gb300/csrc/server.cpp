@@ -242,6 +242,7 @@ int launch(tgp_server* srv, Slot* s, std::vector<Segment>& segs) {
     }
     std::vector<internal::FusedSegment> fused;
     size_t off = 0;
+    const int64_t t_adopt = now_ns();
     for (size_t i = 0; i < segs.size(); ++i) {
         Segment& sg = segs[i];
         PopIR ir;
@@ -269,6 +270,11 @@ int launch(tgp_server* srv, Slot* s, std::vector<Segment>& segs) {
         for (Job* j : sg.jobs) j->info.launch_ns = t;
     int rc = segs.size() == 1 ? tgp_fitness_dev(ctx, fused[0].pop, fused[0].domain, s->stream, s->d_rmse)
                               : internal::fitness_fused(ctx, fused, s->stream, s->d_segs, s->d_counter);
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->st.adopt_ns += t - t_adopt;
+        srv->st.fitness_ns += now_ns() - t;
+    }
     if (rc) return rc;
     SRV_TRY(cudaMemcpyAsync(s->h_rmse, s->d_rmse, T * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SRV_TRY(cudaLaunchHostFunc(s->stream, on_launch_done, s));

@@ -8,7 +8,7 @@ div sin cos neg abs min max, terminals x, y, const ~ U[-1,1], seed 2) over a
 shape chosen by the library's autotuner; one step = one replay of the captured
 CUDA graph (column- and row-table launches, interpreter, finalize).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--sharded]
 
 Prints ONE JSON line.  `value` times the device-resident path (bytecode
 uploaded, CUDA events around each step, L2 flushed between steps); `e2e`
@@ -16,9 +16,11 @@ times the public API from host tokens (compile -> upload -> kernels -> fitness
 on the host) per step.  The roofline counts the work the step's launches
 evaluate as planned (tgp_plan_work) at the calibrated issue cost of each
 operator, against the measured straight-line binary32 issue peak.  The other
-configurations (100 trees on 1024x1024, phenotypes, the generational run, the
-serving loop) are under `other_configs`.  --impl reference times the CPU
-oracle on the host cores on a bounded sample of the same workload.
+configurations (50 trees on 64x64, 100 trees on 1024x1024 with its phenotypes,
+100 trees over all of Table 1, the generational run, the serving loop) are
+under `other_configs`.  --impl reference times the CPU oracle on the host
+cores on a bounded sample of the same workload.  --sharded times the 1024x1024
+population with its grid rows split over the ranks (strong scaling).
 """
 from __future__ import annotations
 

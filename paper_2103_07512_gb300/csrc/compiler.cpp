@@ -83,7 +83,7 @@ void Dag::reserve(size_t n) {
     if (cap > table_.size()) rehash(cap);
 }
 
-void Dag::assign_nodes(std::vector<DagNode>&& v) {
+void Dag::assign_nodes(NodeVec&& v) {
     nodes = std::move(v);
     used_ = nodes.size();
     // the index is rebuilt by the first intern, if any comes (a parsed
@@ -93,10 +93,15 @@ void Dag::assign_nodes(std::vector<DagNode>&& v) {
 }
 
 // The fields of node n that follow from its key and its operands' fields
-// (`nodes` holds the operands): Sethi-Ullman slots, depth, cost as a tree.
+// (`nodes` holds the operands): Sethi-Ullman slots, depth, cost as a tree,
+// the coordinates below it.  They are functions of the subtree, and for a
+// binary node they do not depend on the order of its operands.
 static void derive_fields(DagNode& n, const DagNode* nodes) {
     const int op = n.op;
     const int ar = arity(op);
+    n.spare_ = 0;
+    n.vars = op == T_X ? 1 : op == T_Y ? 2 : 0;
+    for (int c = 0; c < ar; ++c) n.vars |= nodes[n.kid[c]].vars;
     if (ar == 3) {
         // planned order: operand 0 and 1 parked in slots, operand 2 into A
         const DagNode& a = nodes[n.kid[0]];
@@ -123,7 +128,7 @@ static void derive_fields(DagNode& n, const DagNode* nodes) {
         else if (rl) n.su = l.su;
         else n.su = l.su == r.su ? l.su + 1 : std::max(l.su, r.su);
         n.depth = std::max(l.depth, r.depth) + 1;
-        n.cost = op_cost(op) + l.cost + r.cost;
+        n.cost = op_cost(op) + (l.cost + r.cost);   // (the same bits in either operand order)
     }
 }
 
@@ -326,7 +331,7 @@ static void compact_live(PopIR& pop, const std::vector<uint8_t>& live, const Par
     for (size_t i = 0; i < n; ++i)
         if (live[i]) id[i] = n_live++;
     if ((size_t)n_live == n) return;
-    std::vector<DagNode> kept((size_t)n_live);
+    NodeVec kept((size_t)n_live);
     auto fill = [&](size_t lo, size_t hi) {
         for (size_t i = lo; i < hi; ++i) {
             if (!live[i]) continue;
@@ -464,7 +469,7 @@ class MergeTable {
 public:
     // max_nodes: the nodes the workers add, at most; workers: how many add
     MergeTable(size_t max_nodes, int workers, const ParallelFor* par)
-        : nodes_(max_nodes + (size_t)workers * kBlock) {
+        : nodes_(new DagNode[max_nodes + (size_t)workers * kBlock]) {   // (written when handed out)
         size_t cap = 1024;
         while (cap < 2 * max_nodes + 2) cap *= 2;
         mask_ = cap - 1;
@@ -480,7 +485,9 @@ public:
         int32_t next = 0, end = 0;
     };
     static constexpr int32_t kBlock = 256;
-    int32_t find_or_add(Ids& ids, int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
+    // `src`: the node as its chunk holds it (operands in the chunk's ids),
+    // whose derived fields a new node takes.
+    int32_t find_or_add(Ids& ids, const DagNode& src, int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2) {
         size_t h = key_hash(op, k0, k1, imm, k2) & mask_;
         int32_t mine = -1;
         for (;;) {
@@ -493,6 +500,7 @@ public:
                     }
                     mine = ids.next++;
                     DagNode& n = nodes_[mine];
+                    n = src;
                     n.op = op;
                     n.kid[0] = k0;
                     n.kid[1] = k1;
@@ -515,7 +523,7 @@ public:
     int32_t size() const { return count_.load(std::memory_order_relaxed); }
 
 private:
-    std::vector<DagNode> nodes_;
+    std::unique_ptr<DagNode[]> nodes_;
     std::unique_ptr<std::atomic<int32_t>[]> slot_;
     size_t mask_ = 0;
     std::atomic<int32_t> count_{0};
@@ -631,7 +639,7 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
                 // orders of a pair meet (the final order is set below)
                 if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && k[1] < k[0])
                     std::swap(k[0], k[1]);
-                id[i] = mt.find_or_add(block, x.op, k[0], k[1], x.imm, k[2]);
+                id[i] = mt.find_or_add(block, x, x.op, k[0], k[1], x.imm, k[2]);
             }
         });
         // first occurrence of each node, as chunk << 32 | place; with
@@ -671,23 +679,20 @@ int parse_population(const int32_t* ops, const float* imm, int64_t n_imm, const 
             }
         });
         const size_t n_final = (size_t)base[n_chunks];
-        std::vector<DagNode> final_nodes(n_final);
+        NodeVec final_nodes(n_final);
         (*par)(16, [&](int t) {
             for (int64_t g = (int64_t)n_prov * t / 16; g < (int64_t)n_prov * (t + 1) / 16; ++g) {
                 if (fin[g] < 0) continue;
                 DagNode x = mt.node((int32_t)g);
                 for (int j = 0; j < kMaxKids; ++j)
                     if (x.kid[j] >= 0) x.kid[j] = fin[x.kid[j]];
+                // commutative operands in the order of the final ids (the
+                // derived fields, taken from a chunk, do not depend on it)
+                if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && x.kid[1] < x.kid[0])
+                    std::swap(x.kid[0], x.kid[1]);
                 final_nodes[fin[g]] = x;
             }
         });
-        // operand order and derived fields, in id order (operands first)
-        for (size_t f = 0; f < n_final; ++f) {
-            DagNode& x = final_nodes[f];
-            if (simplify && (x.op == T_ADD || x.op == T_MUL || x.op == T_MDIST) && x.kid[1] < x.kid[0])
-                std::swap(x.kid[0], x.kid[1]);
-            derive_fields(x, final_nodes.data());
-        }
         for (int c = 0; c < n_chunks; ++c)
             for (int32_t t = t_at[c]; t < t_at[c + 1]; ++t) out.roots[t] = fin[pid[c][out.roots[t]]];
         out.dag.assign_nodes(std::move(final_nodes));
@@ -732,11 +737,11 @@ thread_local GenScratch tls_scratch;
 class GroupGen {
 public:
     GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
-             const std::vector<uint8_t>* xfree, const std::vector<int32_t>* col, const std::vector<int32_t>* row)
+             const std::vector<int32_t>* col, const std::vector<int32_t>* row)
         : sc_(take_scratch(dag.size())), d_(dag), out_(out), uses_(sc_->uses), where_(sc_->where), keep_(sc_->keep),
           first_pos_(sc_->first_pos), last_pos_(sc_->last_pos), dedup_(dedup), kept_cap_(kept_cap),
-          cv_(cv && cv->active() ? cv : nullptr), stored_(sc_->stored), mark_(sc_->mark), xfree_(xfree),
-          col_(col), row_(row) {}
+          cv_(cv && cv->active() ? cv : nullptr), stored_(sc_->stored), mark_(sc_->mark), col_(col),
+          row_(row) {}
     ~GroupGen() {
         for (int32_t n : stored_all_) stored_[n] = 0;
         if (sc_ == &tls_scratch) {
@@ -819,7 +824,6 @@ private:
     std::vector<bool> busy_;
     std::vector<int32_t> dfs_;
     std::vector<uint8_t>& mark_;    // scratch of sort_touched_descending, all zero between calls
-    const std::vector<uint8_t>* xfree_;   // node has no x below it (or nullptr)
     const std::vector<int32_t>* col_;     // column-table entry of a node, -1 (or nullptr: none)
     const std::vector<int32_t>* row_;     // row-table entry of a node, -1 (or nullptr: none)
 
@@ -981,7 +985,9 @@ private:
             emit(F_ROW, 0, 0, 0, (*row_)[n], 0);
         } else {
             compute(n);
-            if (xfree_ && (*xfree_)[n]) out_.back().uni = 1;   // the instruction that computed n
+            // no x below n: the same value at all K points of a thread (they
+            // share a row); the instruction that computed n says so
+            if (!(N(n).vars & 1)) out_.back().uni = 1;
             if (cv_ && cv_->insert[n] >= 0 && !stored_[n]) {
                 emit(F_CST, 0, 0, 0, cv_->insert[n], 0);
                 stored_[n] = 1;
@@ -1237,8 +1243,7 @@ constexpr float kColMinCost = 4.f;
 constexpr size_t kColMaxEntries = 16384;
 
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns, bool table_plan,
-                            const std::vector<uint8_t>* xfree_given = nullptr);
+                            const ParallelFor* par, bool columns, bool table_plan);
 
 // Encodes groups [0, n) of `ir` (group g at [off[g], off[g + 1])) onto
 // `code`, appending each group's end offset (code.size() after it) to
@@ -1316,8 +1321,7 @@ void build_plan(const PopIR& pop, const PlanShape& shape, HostPlan& plan, const 
 // table_plan: the plan of column or row tables (their subtrees in id order:
 // the ordering pass would cost more than it saves on these small launches).
 static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan& plan, const CacheView* cv,
-                            const ParallelFor* par, bool columns, bool table_plan,
-                            const std::vector<uint8_t>* xfree_given) {
+                            const ParallelFor* par, bool columns, bool table_plan) {
     plan = HostPlan();
     plan.shape = shape;
     const int64_t T = (int64_t)pop.roots.size();
@@ -1371,10 +1375,15 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                 }
             }
         };
-        if (C > 1) (*par)(C, walk);
-        else walk(0);
-        for (const auto& v : nodes_of)
-            for (int32_t n : v) tree_uses[n]++;
+        if (C > 1) {
+            (*par)(C, walk);
+            (*par)(C, [&](int c) {
+                for (int32_t n : nodes_of[c]) __atomic_fetch_add(&tree_uses[n], 1, __ATOMIC_RELAXED);
+            });
+        } else {
+            walk(0);
+            for (int32_t n : nodes_of[0]) tree_uses[n]++;
+        }
         if (C > 1) (*par)(C, keys);
         else keys(0);
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -1399,71 +1408,65 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         }
     }
 
-    // Slot cap for kept nodes: keep a CTA's dynamic shared memory (target
-    // values + slots) within the SM's share for the interpreter's resident
-    // CTAs at this K.  Temporaries may exceed it (a tree needs as many as its
-    // Sethi-Ullman number).
-    // nodes with no x below them: their value is the same at all K points of
-    // a thread (the points share a row), operands are interned before users
-    // (a table's plan takes its population's: the same DAG)
-    std::vector<uint8_t> xfree_own;
-    if (!xfree_given) xfree_own.assign(pop.dag.size(), 0);
-    const std::vector<uint8_t>& xfree = xfree_given ? *xfree_given : xfree_own;
     const int64_t W = shape.W > 0 ? shape.W : shape.N;
     const int64_t H = W > 0 ? shape.N / W : 0;
-    const bool tables = columns && W > 1 && H > 1 && !xfree_given;   // (a table's plan has none)
-    if (!tables && !xfree_given) {   // (with tables, the pass below forms it too)
-        for (size_t n = 0; n < pop.dag.size(); ++n) {
-            const DagNode& d = pop.dag.nodes[n];
-            bool f = d.op != T_X;
-            for (int c = 0; c < kMaxKids; ++c)
-                if (d.kid[c] >= 0) f = f && xfree_own[d.kid[c]];
-            xfree_own[n] = f;
-        }
-    }
-    // Column and row tables (grids of at least two rows and two columns, no
-    // cache view): the largest costly subtrees with x and no y below them
-    // (one value per column) and with no x below them (one value per row),
-    // i.e. those used by a node evaluated in this plan, or tree roots.  The
-    // tables' own plans are phenotype launches on one row of W points and on
-    // one column of H points.
+    const bool tables = columns && W > 1 && H > 1 && !table_plan;   // (a table's plan has none)
+    // Column and row tables (grids of at least two rows and two columns): the
+    // largest costly subtrees with x and no y below them (one value per
+    // column) and with no x below them (one value per row), i.e. those used
+    // by a node evaluated in this plan, or tree roots.  The tables' own plans
+    // are phenotype launches on one row of W points and on one column of H
+    // points.
     std::vector<int32_t> col, row;
     std::vector<std::function<void()>> table_builds;   // run beside the groups' planning
     if (tables) {
         const size_t nn = pop.dag.size();
         const bool cview = cv && cv->active();
-        // one pass in id order (operands first): no x, no y, a cache load or
-        // store below (such a subtree is evaluated in this plan), eligible
-        std::vector<uint8_t> yfree(nn, 0), celig(nn, 0), relig(nn, 0), cneed(nn, 0), rneed(nn, 0), blocked(nn, 0);
-        for (size_t n = 0; n < nn; ++n) {
-            const DagNode& d = pop.dag.nodes[n];
-            bool fx = d.op != T_X, fy = d.op != T_Y;
-            bool b = cview && (cv->cached[n] >= 0 || cv->insert[n] >= 0);
-            for (int c = 0; c < kMaxKids; ++c)
-                if (d.kid[c] >= 0) {
-                    fx = fx && xfree_own[d.kid[c]];
-                    fy = fy && yfree[d.kid[c]];
-                    b = b || blocked[d.kid[c]];
-                }
-            xfree_own[n] = fx;
-            yfree[n] = fy;
-            blocked[n] = b;
-            const bool costly = !is_leaf(d.op) && d.cost >= kColMinCost && !b;
-            celig[n] = costly && fy && !fx;
-            relig[n] = costly && fx;
-        }
-        for (int32_t r : pop.roots) {
-            cneed[r] = celig[r];
-            rneed[r] = relig[r];
-        }
-        for (size_t n = 0; n < nn; ++n) {
-            if (celig[n] || relig[n]) continue;   // inside a table's subtree (or one)
-            for (int c = 0; c < kMaxKids; ++c) {
-                const int32_t k = pop.dag.nodes[n].kid[c];
-                if (k < 0) continue;
-                if (celig[k]) cneed[k] = 1;
-                if (relig[k]) rneed[k] = 1;
+        // a cache load or store at or below a node (such a subtree is
+        // evaluated in this plan): one pass in id order, operands first
+        std::vector<uint8_t> blocked;
+        if (cview) {
+            blocked.assign(nn, 0);
+            for (size_t n = 0; n < nn; ++n) {
+                const DagNode& d = pop.dag.nodes[n];
+                bool b = cv->cached[n] >= 0 || cv->insert[n] >= 0;
+                for (int c = 0; c < kMaxKids; ++c)
+                    if (d.kid[c] >= 0) b = b || blocked[d.kid[c]];
+                blocked[n] = b;
             }
+        }
+        // 1: may be a column table's subtree (x and no y below it), 2: a row
+        // table's (no x below it), 0: neither
+        const auto elig = [&](size_t n) -> int {
+            const DagNode& d = pop.dag.nodes[n];
+            if (is_leaf(d.op) || d.cost < kColMinCost || (cview && blocked[n])) return 0;
+            return d.vars == 1 ? 1 : (d.vars & 1) ? 0 : 2;
+        };
+        std::vector<uint8_t> cneed(nn, 0), rneed(nn, 0);
+        for (int32_t r : pop.roots) {
+            const int e = elig(r);
+            cneed[r] = e == 1;
+            rneed[r] = e == 2;
+        }
+        // the eligible operands of nodes that are not inside a table's
+        // subtree (nor one); the marks are idempotent stores, so node ranges
+        // run on the workers
+        const auto mark = [&](size_t n0, size_t n1) {
+            for (size_t n = n0; n < n1; ++n) {
+                if (elig(n)) continue;
+                const DagNode& d = pop.dag.nodes[n];
+                for (int c = 0; c < kMaxKids; ++c) {
+                    if (d.kid[c] < 0) continue;
+                    const int e = elig(d.kid[c]);
+                    if (e) __atomic_store_n(&(e == 1 ? cneed : rneed)[d.kid[c]], (uint8_t)1, __ATOMIC_RELAXED);
+                }
+            }
+        };
+        if (par && *par && nn >= (1u << 16)) {
+            const int C = 16;
+            (*par)(C, [&](int c) { mark(nn * c / C, nn * (c + 1) / C); });
+        } else {
+            mark(0, nn);
         }
         auto make_tables = [&](const std::vector<uint8_t>& need, std::vector<int32_t>& view,
                                std::vector<int32_t>& roots, std::shared_ptr<HostPlan>& tplan, int64_t& stride,
@@ -1498,9 +1501,8 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             tplan = std::make_shared<HostPlan>();
             HostPlan* tp = tplan.get();
             const bool big = R >= 256;
-            table_builds.push_back([&pop, &roots, &xfree, costs, ts, tp, par, big]() {
-                build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tp, nullptr, big ? par : nullptr, false, true,
-                                &xfree);
+            table_builds.push_back([&pop, &roots, costs, ts, tp, par, big]() {
+                build_plan_impl(PlanPop{pop.dag, roots, costs, 0}, ts, *tp, nullptr, big ? par : nullptr, false, true);
             });
         };
         make_tables(cneed, col, plan.col_roots, plan.col_plan, plan.col_stride, W, W);
@@ -1509,6 +1511,10 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     const std::vector<int32_t>* colp = col.empty() ? nullptr : &col;
     const std::vector<int32_t>* rowp = row.empty() ? nullptr : &row;
 
+    // Slot cap for kept nodes: keep a CTA's dynamic shared memory (target
+    // values + slots) within the SM's share for the interpreter's resident
+    // CTAs at this K.  Temporaries may exceed it (a tree needs as many as its
+    // Sethi-Ullman number).
     const int slot_bytes = shape.K * shape.threads * 4;
     // (less the target values and the root-sum area: kRootBatch floats per thread)
     const int budget =
@@ -1533,7 +1539,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             }
             t -= NT;
             const int g0 = (int)((int64_t)G * t / P), g1 = (int)((int64_t)G * (t + 1) / P);
-            GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, &xfree, colp, rowp);
+            GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, colp, rowp);
             ends[t].push_back(0);
             for (int g = g0; g < g1; ++g) {
                 slots[t] = std::max(slots[t], plan_group(gen, part[t], pop, groups[g], budget));
@@ -1562,7 +1568,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         }
     } else {
         for (auto& b : table_builds) b();
-        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, &xfree, colp, rowp);
+        GroupGen gen(pop.dag, plan.ir, shape.dedup, budget, cv, colp, rowp);
         for (int g = 0; g < G; ++g) {
             plan.n_slots = std::max(plan.n_slots, plan_group(gen, plan.ir, pop, groups[g], budget));
             plan.group_off.push_back((int64_t)plan.ir.size());

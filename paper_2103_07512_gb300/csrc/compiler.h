@@ -5,6 +5,8 @@
 #include <functional>
 #include <memory>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "tgp_ir.h"
@@ -15,7 +17,9 @@ namespace tgp {
 // (op, kid0, kid1, imm bits) *is* the node, so two equal subtrees always map
 // to the same id (Handley's DAG, Sec. 2 of TensorGP).
 struct DagNode {
-    int32_t op;
+    int16_t op;
+    uint8_t vars;       // bit 0: x is the node or below it; bit 1: y likewise
+    uint8_t spare_;
     int32_t kid[kMaxKids];   // operands in order, -1 when absent
     uint32_t imm;       // binary32 bits of a CONST
     int32_t su;         // register slots needed to evaluate it (Sethi-Ullman)
@@ -23,16 +27,39 @@ struct DagNode {
     float cost;         // issue cost of evaluating it as a tree, per point
 };
 
+// Node arrays: an allocator that leaves a new element of a trivial type
+// uninitialised, so that sizing an array that is filled right after (by
+// several workers) does not first zero it on one thread.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new ((void*)p) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+using NodeVec = std::vector<DagNode, NoInitAlloc<DagNode>>;
+
 class Dag {
 public:
-    std::vector<DagNode> nodes;
+    NodeVec nodes;
     int32_t intern(int op, int32_t k0, int32_t k1, uint32_t imm, int32_t k2 = -1);
     size_t size() const { return nodes.size(); }
     // Room for n nodes without growing the node array or the hash table.
     void reserve(size_t n);
     // Takes `v` as the node array (distinct keys, operands before their
     // users); the hash index over it is rebuilt by the next intern.
-    void assign_nodes(std::vector<DagNode>&& v);
+    void assign_nodes(NodeVec&& v);
 
 private:
     std::vector<int32_t> table_;   // open addressing, -1 = empty

@@ -736,7 +736,7 @@ thread_local GenScratch tls_scratch;
 
 class GroupGen {
 public:
-    GroupGen(const Dag& dag, std::vector<IrIns>& out, bool dedup, int kept_cap, const CacheView* cv,
+    GroupGen(const Dag& dag, IrVec& out, bool dedup, int kept_cap, const CacheView* cv,
              const std::vector<int32_t>* col, const std::vector<int32_t>* row)
         : sc_(take_scratch(dag.size())), d_(dag), out_(out), uses_(sc_->uses), where_(sc_->where), keep_(sc_->keep),
           first_pos_(sc_->first_pos), last_pos_(sc_->last_pos), dedup_(dedup), kept_cap_(kept_cap),
@@ -807,7 +807,7 @@ private:
     static constexpr int kKeepSpan = 1;
 
     const Dag& d_;
-    std::vector<IrIns>& out_;
+    IrVec& out_;
     std::vector<int32_t>& uses_;    // evaluations of the node still to be consumed
     std::vector<int32_t>& where_;   // slot holding the node, or -1
     std::vector<uint8_t>& keep_;    // evaluated once and held
@@ -836,7 +836,7 @@ private:
 
     void emit(int form, int fn, int o1, int o2, int aux, uint32_t imm) {
         IrIns in;
-        in.form = form; in.fn = fn; in.o1 = o1; in.o2 = o2; in.aux = aux; in.imm = imm;
+        in.form = form; in.fn = fn; in.o1 = o1; in.o2 = o2; in.aux = aux; in.imm = imm; in.uni = 0;
         out_.push_back(in);
     }
 
@@ -1215,7 +1215,7 @@ struct PlanPop {
 
 // One group's bytecode (appended to gen's output), with the kept-slot cap
 // that the group's temporaries leave of `budget`.  Returns the slots used.
-static int plan_group(GroupGen& gen, std::vector<IrIns>& ir, const PlanPop& pop, const std::vector<int32_t>& trees,
+static int plan_group(GroupGen& gen, IrVec& ir, const PlanPop& pop, const std::vector<int32_t>& trees,
                       int budget) {
     // kept nodes get what the group's temporaries leave of the budget (a
     // tree's evaluation parks up to its Sethi-Ullman number of values)
@@ -1253,8 +1253,8 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
 // kRootBatch, each batch closed by a flush word and its trees (see
 // OPC_FLUSH).  Returns whether the interpreter variant with the rest of
 // Table 1 is needed.
-static bool encode_groups(const std::vector<IrIns>& ir, const int64_t* off, int n, int64_t col_stride,
-                          int64_t row_stride, std::vector<Ins>& code, std::vector<int64_t>& code_off) {
+static bool encode_groups(const IrVec& ir, const int64_t* off, int n, int64_t col_stride, int64_t row_stride,
+                          CodeVec& code, std::vector<int64_t>& code_off) {
     bool ext = false;
     auto enc = [&](const IrIns& in) {
         Ins e = encode(in);
@@ -1527,9 +1527,9 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
         const int NT = (int)table_builds.size();
         // each run is planned and encoded on its own; the runs are then
         // placed back to back (offsets shifted)
-        std::vector<std::vector<IrIns>> part(P);
+        std::vector<IrVec> part(P);
         std::vector<std::vector<int64_t>> ends(P), cends(P);
-        std::vector<std::vector<Ins>> pcode(P);
+        std::vector<CodeVec> pcode(P);
         std::vector<int> slots(P, 0);
         std::vector<uint8_t> pext(P, 0);
         (*par)(P + NT, [&](int t) {
@@ -1539,6 +1539,11 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             }
             t -= NT;
             const int g0 = (int)((int64_t)G * t / P), g1 = (int)((int64_t)G * (t + 1) / P);
+            // room for about the run's instructions (its trees' costs bound
+            // their nodes), so that the output is not moved as it grows
+            double est = 0;
+            for (int g = g0; g < g1; ++g) est += plan.group_cost[g];
+            part[t].reserve((size_t)(std::min(est, 2.0 * (double)pop.tree_nodes) + 64.0));
             GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, colp, rowp);
             ends[t].push_back(0);
             for (int g = g0; g < g1; ++g) {
@@ -1549,22 +1554,25 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             pext[t] = encode_groups(part[t], ends[t].data(), g1 - g0, plan.col_stride, plan.row_stride, pcode[t],
                                     cends[t]);
         });
-        size_t total_ins = 0, total_code = 1;
+        // the runs' places, then their copies on the workers
+        std::vector<int64_t> base(P + 1, 0), cbase(P + 1, 0);
         for (int t = 0; t < P; ++t) {
-            total_ins += part[t].size();
-            total_code += pcode[t].size();
+            base[t + 1] = base[t] + (int64_t)part[t].size();
+            cbase[t + 1] = cbase[t] + (int64_t)pcode[t].size();
         }
-        plan.ir.reserve(total_ins);
-        plan.code.reserve(total_code);
+        plan.ir.resize((size_t)base[P]);
+        plan.code.reserve((size_t)cbase[P] + 1);
+        plan.code.resize((size_t)cbase[P]);
+        (*par)(P, [&](int t) {
+            std::copy(part[t].begin(), part[t].end(), plan.ir.begin() + base[t]);
+            std::copy(pcode[t].begin(), pcode[t].end(), plan.code.begin() + cbase[t]);
+        });
         plan.code_off.assign(1, 0);
         for (int t = 0; t < P; ++t) {
-            const int64_t base = (int64_t)plan.ir.size(), cbase = (int64_t)plan.code.size();
-            plan.ir.insert(plan.ir.end(), part[t].begin(), part[t].end());
-            plan.code.insert(plan.code.end(), pcode[t].begin(), pcode[t].end());
             plan.n_slots = std::max(plan.n_slots, slots[t]);
             plan.ext = plan.ext || pext[t];
-            for (size_t i = 1; i < ends[t].size(); ++i) plan.group_off.push_back(base + ends[t][i]);
-            for (int64_t e : cends[t]) plan.code_off.push_back(cbase + e);
+            for (size_t i = 1; i < ends[t].size(); ++i) plan.group_off.push_back(base[t] + ends[t][i]);
+            for (int64_t e : cends[t]) plan.code_off.push_back(cbase[t] + e);
         }
     } else {
         for (auto& b : table_builds) b();

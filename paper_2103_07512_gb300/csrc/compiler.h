@@ -49,6 +49,8 @@ struct NoInitAlloc : std::allocator<T> {
     }
 };
 using NodeVec = std::vector<DagNode, NoInitAlloc<DagNode>>;
+using IrVec = std::vector<IrIns, NoInitAlloc<IrIns>>;
+using CodeVec = std::vector<Ins, NoInitAlloc<Ins>>;
 
 class Dag {
 public:
@@ -127,8 +129,8 @@ inline int64_t plan_chunks(const PlanShape& s) {
 
 struct HostPlan {
     PlanShape shape;
-    std::vector<IrIns> ir;              // decoded, all groups back to back
-    std::vector<Ins> code;              // encoded, plus one trailing END
+    IrVec ir;                           // decoded, all groups back to back
+    CodeVec code;                       // encoded, plus one trailing END
     std::vector<int64_t> group_off;     // [n_groups + 1] offsets into ir
     std::vector<int64_t> code_off;      // [n_groups + 1] offsets into code (fused pairs are one word)
     std::vector<int32_t> group_order;   // groups by descending estimated cost

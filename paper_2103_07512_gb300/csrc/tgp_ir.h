@@ -144,7 +144,7 @@ struct IrIns {
     int32_t form, fn, o1, o2;
     int32_t aux;
     uint32_t imm;   // binary32 bits of the immediate operand
-    int32_t uni = 0;   // computes a value with no x below it: the same at all of a thread's points
+    int32_t uni;   // computes a value with no x below it: the same at all of a thread's points
 };
 
 // Resident CTAs per SM the interpreter is built for, by points per thread K

@@ -866,27 +866,14 @@ private:
                 }
             }
         }
+        // the group's internal nodes (those the walk above reached, each
+        // once) and the uses of the roots
+        touched_.assign(span_touched_.begin(), span_touched_.end());
         for (int32_t t : trees) {
             int32_t r = roots[t];
-            if (is_leaf(N(r).op)) continue;
-            if (uses_[r]++ > 0) continue;
-            touched_.push_back(r);
-            dfs_.assign(1, r);
-            while (!dfs_.empty()) {
-                int32_t n = dfs_.back();
-                dfs_.pop_back();
-                if (is_loaded(n)) continue;
-                for (int c = 0; c < kMaxKids; ++c) {
-                    int32_t k = N(n).kid[c];
-                    if (k < 0 || is_leaf(N(k).op) || where_[k] == -2) continue;
-                    where_[k] = -2;   // visited mark, reset below
-                    touched_.push_back(k);
-                    dfs_.push_back(k);
-                }
-            }
+            if (!is_leaf(N(r).op)) uses_[r]++;
         }
         sort_touched_descending();
-        for (int32_t n : touched_) where_[n] = -1;
         for (int32_t n : forbid) where_[n] = -3;   // mark: never keep (reset below)
         // uses_ holds the root counts so far; push evaluations down
         for (int32_t n : touched_) {
@@ -1337,14 +1324,17 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
     std::iota(order.begin(), order.end(), 0);
     if (!table_plan) {
         // distinct internal nodes of each tree (contiguous chunks of trees
-        // on the workers), then the number of trees using each node
+        // on the workers), then whether two trees or more use each node: a
+        // node seen by two trees of one chunk, or by two chunks
         const bool many = par && *par && T >= 512;
         const int C = many ? (int)std::min<int64_t>(16, T / 256) : 1;
-        std::vector<int32_t> tree_uses(pop.dag.size(), 0);
-        std::vector<std::vector<int32_t>> nodes_of(C), at_of(C);
+        const size_t nn = pop.dag.size();
+        std::vector<std::vector<int32_t>> nodes_of(C), at_of(C), seen_of(C), dup_of(C);
         auto walk = [&](int c) {
             const int64_t t0 = T * c / C, t1 = T * (c + 1) / C;
-            std::vector<int32_t> seen(pop.dag.size(), -1), stack;
+            std::vector<int32_t>& seen = seen_of[c];   // last tree of the chunk using the node
+            seen.assign(nn, -1);
+            std::vector<int32_t> stack;
             std::vector<int32_t>& tree_nodes = nodes_of[c];
             std::vector<int32_t>& tree_at = at_of[c];
             for (int64_t t = t0; t < t1; ++t) {
@@ -1354,6 +1344,7 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                     int32_t n = stack.back();
                     stack.pop_back();
                     if (seen[n] == (int32_t)t || is_leaf(pop.dag.nodes[n].op)) continue;
+                    if (seen[n] >= 0) dup_of[c].push_back(n);
                     seen[n] = (int32_t)t;
                     tree_nodes.push_back(n);
                     for (int k = 0; k < kMaxKids; ++k)
@@ -1361,6 +1352,14 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                 }
             }
             tree_at.push_back((int32_t)tree_nodes.size());
+        };
+        std::vector<uint8_t> multi(nn, 0);
+        const auto merge = [&](size_t n0, size_t n1) {
+            for (size_t n = n0; n < n1; ++n) {
+                int k = 0;
+                for (int c = 0; c < C && k < 2; ++c) k += seen_of[c][n] >= 0;
+                if (k >= 2) multi[n] = 1;
+            }
         };
         // the costliest node of each tree that another tree also uses
         std::vector<int32_t> key(T, -1);
@@ -1371,21 +1370,23 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
                 for (int32_t i = at_of[c][t - t0]; i < at_of[c][t - t0 + 1]; ++i) {
                     const int32_t n = nodes_of[c][i];
                     const float cost = pop.dag.nodes[n].cost;
-                    if (tree_uses[n] >= 2 && cost > key_cost) { key_cost = cost; key[t] = n; }
+                    if (multi[n] && cost > key_cost) { key_cost = cost; key[t] = n; }
                 }
             }
         };
         if (C > 1) {
             (*par)(C, walk);
+            const int R = 16;
+            (*par)(R, [&](int r) { merge(nn * r / R, nn * (r + 1) / R); });
             (*par)(C, [&](int c) {
-                for (int32_t n : nodes_of[c]) __atomic_fetch_add(&tree_uses[n], 1, __ATOMIC_RELAXED);
+                for (int32_t n : dup_of[c]) __atomic_store_n(&multi[n], (uint8_t)1, __ATOMIC_RELAXED);
             });
+            (*par)(C, keys);
         } else {
             walk(0);
-            for (int32_t n : nodes_of[0]) tree_uses[n]++;
+            for (int32_t n : dup_of[0]) multi[n] = 1;
+            keys(0);
         }
-        if (C > 1) (*par)(C, keys);
-        else keys(0);
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
             if (key[a] != key[b]) return key[a] > key[b];
             return a < b;

@@ -1157,7 +1157,8 @@ PlanShape default_shape(const PopIR& pop, int64_t N, int sms) {
     PlanShape s;
     s.N = N;
     s.threads = 128;
-    s.K = N >= (1 << 18) ? 8 : N >= (1 << 14) ? 4 : N >= (1 << 12) ? 2 : 1;
+    // (measured on GB300: K = 8 is the fastest from 256 x 256 points up)
+    s.K = N >= (1 << 16) ? 8 : N >= (1 << 14) ? 4 : N >= (1 << 12) ? 2 : 1;
     // Enough (group, tile) work items for ~64 per SM: the atomic queue then
     // balances uneven groups, and smaller groups cost nothing extra.
     int64_t tile = (int64_t)s.K * s.threads;

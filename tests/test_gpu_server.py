@@ -50,10 +50,13 @@ def test_alone_equals_in_mix():
 
 def test_fused_domains_alone_equals_in_mix():
     """Jobs on many different grids of one launch shape (K = 8: 2^18 points
-    and more) and both target kinds, queued at once: fused across domains
-    into few launches, each result bitwise that of the job alone."""
+    and more) and both target kinds, queued at once behind a long first job
+    (2,000 trees on 2048 x 2048 points, so that the others are all queued
+    when it ends): fused across domains into few launches, each result
+    bitwise that of the job alone."""
     rng = np.random.default_rng(47)
-    jobs = []
+    jobs = [{"tok": I.to_tokens(I.ramped_half_and_half(2000, 2, 10, rng)), "W": 2048, "H": 2048,
+             "target_tokens": None}]
     for k in range(12):
         side = int(rng.integers(512, 800))
         tok = I.to_tokens(I.ramped_half_and_half(int(rng.integers(10, 40)), 2, 6, rng))

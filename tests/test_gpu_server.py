@@ -26,8 +26,9 @@ def test_alone_equals_in_mix():
     jobs = small_jobs(14, seed=40)
     # repeat some domains so that queued jobs share a launch
     jobs += [dict(j, tok=k["tok"]) for j, k in zip(jobs[:6], jobs[6:12])]
-    # four heavier jobs first keep every stream busy while the rest queue
-    heavy, _ = I.population_at_scale(seed=46)
+    # four heavy jobs first (1,000 trees on 2048 x 2048 points each) keep every
+    # stream busy while the rest queue
+    heavy = I.to_tokens(I.ramped_half_and_half(1000, 2, 8, np.random.default_rng(46)))
     jobs = [{"tok": heavy, "W": 2048, "H": 2048 - 8 * k, "target_tokens": None} for k in range(4)] + jobs
     with tgp.Context() as ctx:
         with tgp.Server(ctx, streams=1) as srv:      # alone: one job at a time

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "compiler.cpp", "capi.cpp", "noalloc.cu", "server.cpp", "evolve.cpp"]
-HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h", "gen_fastloop.py"]
+HEADERS = ["tgp_ir.h", "compiler.h", "kernels.h", "internal.h", "pool.h", "gen_fastloop.py"]
 
 
 def nvcc() -> str:

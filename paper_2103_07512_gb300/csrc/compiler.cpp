@@ -1541,11 +1541,13 @@ static void build_plan_impl(const PlanPop& pop, const PlanShape& shape, HostPlan
             }
             t -= NT;
             const int g0 = (int)((int64_t)G * t / P), g1 = (int)((int64_t)G * (t + 1) / P);
-            // room for about the run's instructions (its trees' costs bound
-            // their nodes), so that the output is not moved as it grows
+            // room for about the run's instructions, so that the output is
+            // not moved as it grows: at most two for each of its trees'
+            // tokens, its share of the population's tokens taken as its
+            // share of the cost
             double est = 0;
             for (int g = g0; g < g1; ++g) est += plan.group_cost[g];
-            part[t].reserve((size_t)(std::min(est, 2.0 * (double)pop.tree_nodes) + 64.0));
+            part[t].reserve((size_t)(2.0 * (double)pop.tree_nodes * est / std::max(total, 1.0) + 64.0));
             GroupGen gen(pop.dag, part[t], shape.dedup, budget, nullptr, colp, rowp);
             ends[t].push_back(0);
             for (int g = g0; g < g1; ++g) {

@@ -476,24 +476,32 @@ def bench_all_operators(ctx_cls, dev, flush, costs, peak_add, peak_fma, steps=50
     """100 RHH trees (depth 2-8) over every function of Table 1 (the 21 of
     the extended set: tan, exp, log, pow, mod and the rest beside the
     benchmark's ten) on 1024x1024, Pagie target: the interpreter variant with
-    the rest of Table 1, timed as the 1024x1024 population."""
+    the rest of Table 1, timed as the 1024x1024 population, in the launch
+    shape the autotuner picks."""
     tok = I.to_tokens(I.ramped_half_and_half(100, 2, 8, np.random.default_rng(7), I.ALL_FUNCTIONS))
     g = I.Grid(1024, 1024)
     workload = ("all_operators: 100 RHH trees depth 2-8 over all 21 functions of Table 1, 1024x1024 grid, "
                 "Pagie target, seed 7")
-    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, PROFILE_OPS, steps)
+    return fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, PROFILE_OPS, steps,
+                          tune=True)
 
 
 def fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workload, profile, steps,
-                   phenotypes=False):
+                   phenotypes=False, tune=False):
     """Direct fitness launches of one population, timed with CUDA events,
-    with the roofline of the work they evaluate as planned."""
+    with the roofline of the work they evaluate as planned; with `tune`, in
+    the launch shape the autotuner picks first.  The warm-up and timed
+    launches (and the phenotype measurement) run in the NVTX range "timed",
+    which profilers can select."""
     import torch
     ctx = ctx_cls(device=dev.index, time_kernels=True)
     dom = ctx.load_domain(g.W, g.H, g.xlo, g.xhi, g.ylo, g.yhi)
     pop = ctx.compile_tokens(tok)
     rmse = torch.empty(tok.n_trees, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuned = ctx.autotune(pop, dom, stream=stream) if tune else None
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(5):
         ctx.fitness_dev(pop, dom, rmse, stream=stream)
     torch.cuda.synchronize()
@@ -519,8 +527,11 @@ def fitness_record(ctx_cls, dev, flush, costs, peak_add, peak_fma, tok, g, workl
            "l2": "flushed between steps"}
     out["roofline"]["kernel_ms_note"] = ("interpreter and table launches, CUDA events the library records "
                                          "around them on the stream (TGP_F_TIME_KERNELS)")
+    if tuned:
+        out["autotuned"] = {"points_per_thread": int(tuned[0]), "groups": int(tuned[1]), "kernel_ms": float(tuned[2])}
     if phenotypes:
         out["phenotype"] = bench_phenotype(ctx, pop, dom, tok, g, dev, flush)
+    torch.cuda.nvtx.range_pop()
     ctx.close()
     return out
 
@@ -831,10 +842,8 @@ def main():
         with tgp.Context(device=0) as c:
             costs = c.calibrate_op_costs()
             pa, pf = c.calibrate_peak()
-        torch.cuda.nvtx.range_push("timed")
         leg = bench_population_at_scale if args.only == "population_at_scale" else bench_all_operators
         r = leg(tgp.Context, dev, flush, costs, pa, pf, steps=args.steps)
-        torch.cuda.nvtx.range_pop()
         print(json.dumps({"config": args.only, **r}))
         return 0
     return run_ours(args)
